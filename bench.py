@@ -1,0 +1,368 @@
+"""Benchmark of the Bragg-spot sum on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Workload: the large shot (3072x3072 pixels, oversample 2, 2 sensor layers,
+100 sources on a 0.5 % Gaussian spectrum at 9.5 keV, 50 mosaic domains,
+Na=Nb=Nc=25 Gaussian shape, tricubic F_cell on hkl in [-60,60]^3, Kahn
+0.99): 3.77e11 pixel-steps per image.  One step = one image: the per-shot
+host set-up (rotated axes, source tables) and the whole per-pixel sum with
+the fused double accumulate, in the FP32-mixed form.  The JSON line also
+carries the plain FP64 form (timed on a strided pixel subset of the same
+shot, its rate scaled by nothing: pixel-steps it did / time it took).
+
+Timing: W untimed warm-up steps, then K steps, each bracketed by CUDA
+events on the library's stream; a 512 MB buffer is rewritten between timed
+steps (outside the events) to flush the 129 MB L2.  Multi-GPU (torchrun):
+independent replicas, one shot per rank, no data-path collective; the
+slowest rank's time sets the rate.
+
+--impl reference times the FP64 CPU oracle (the only reference this method
+has: the paper ships no code) on the host cores, on a strided row sample of
+the same shot per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("pixel-steps/s (FP32-mixed vs FP64 form); served shots/s with "
+          "p99 latency")
+UNIT = "pixel-steps/s"
+WORKLOAD = ("large shot 3072x3072, oversample 2, 2 layers (0.5 mm, atten "
+            "0.3 mm), 100 sources (0.5% Gaussian at 9.5 keV), 50 mosaic "
+            "domains, cell 79x79x38 A, N=25 Gaussian, tricubic F on "
+            "[-60,60]^3, Kahn 0.99")
+SM_COUNT_GB300 = 152
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--f64-rows-every", type=int, default=96)
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------- clocks
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples every 200 ms while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,"
+         "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}",
+                 f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                 "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() in ("active", "0x1", "1"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        # samples under load: the upper half of the observed clocks
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------- helpers
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+        pg = dist
+    return world, rank, local, pg
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+def max_over_ranks(pg, x: float) -> float:
+    if pg is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_baseline(shot, every: int, threads: int = 0):
+    import oracle
+    from paper_2205_07976_gb300 import workloads as W
+    pix = W.strided_rows(shot, every)
+    oracle.build()
+    t0 = time.perf_counter()
+    oracle.image(shot, pix, nthreads=threads)
+    dt = time.perf_counter() - t0
+    steps = len(pix) * shot.steps_per_pixel
+    return {"value": steps / dt, "unit": UNIT,
+            "cores": threads or oracle.max_threads(), "kind": "oracle",
+            "sample": f"every {every}th row of the large shot "
+                      f"({len(pix)} pixels, {steps:.3e} pixel-steps, "
+                      f"{dt:.1f} s)"}
+
+
+# ------------------------------------------------------------ our arm
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    from paper_2205_07976_gb300 import nbgb
+    from paper_2205_07976_gb300 import workloads as W
+
+    world, rank, local, pg = dist_setup(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    shot = W.large_shot(seed=1 + rank)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32,
+                        device=dev)
+    sim = nbgb.Sim("mixed", device=local, stream=stream).set_shot(shot)
+
+    kernel_times = []
+
+    def step(record=False):
+        # per-shot host set-up (a1) + the whole per-pixel sum (a2..a8)
+        sim.set_crystal(shot, with_F=False)
+        if record:
+            k0 = torch.cuda.Event(enable_timing=True)
+            k1 = torch.cuda.Event(enable_timing=True)
+            k0.record(stream)
+            sim.add_spots()
+            k1.record(stream)
+            kernel_times.append((k0, k1))
+        else:
+            sim.add_spots()
+
+    def timed(fn, k):
+        times = []
+        for _ in range(k):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            fn(record=True)
+            ev1.record(stream)
+            stream.synchronize()
+            times.append(ev0.elapsed_time(ev1) / 1e3)
+        return times
+
+    for _ in range(args.warmup):
+        step()
+    stream.synchronize()
+    barrier(pg)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        times = timed(step, args.steps)
+    torch.cuda.synchronize()
+    barrier(pg)
+    t_step = max_over_ranks(pg, sum(times) / len(times))
+    units = shot.pixel_steps * world
+    value = units / t_step
+    clocks = clk.summary()
+
+    # end to end through the C ABI with host buffers
+    img_host = torch.empty(shot.npix, dtype=torch.float32).pin_memory()
+    F_host = torch.from_numpy(np.ascontiguousarray(shot.F)).pin_memory()
+
+    def step_e2e():
+        s2 = shot.copy()
+        s2.F = F_host.numpy()
+        sim.set_crystal(s2, with_F=True)
+        sim.set_beam(s2)
+        sim.set_detector(s2)
+        sim.add_spots()
+        code = nbgb.NB_DTYPE_F32
+        nbgb._check(sim.lib.nb_get_image(sim.h, nbgb._vp(img_host.data_ptr()),
+                                         shot.npix, code, 0), sim.h)
+
+    step_e2e()
+    torch.cuda.synchronize()
+    barrier(pg)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step_e2e()
+    torch.cuda.synchronize()
+    barrier(pg)
+    t_e2e = max_over_ranks(pg, (time.perf_counter() - t0) / args.steps)
+    h2d = (shot.F.nbytes + shot.umats.nbytes + shot.axes.nbytes
+           + shot.dirs.nbytes + shot.lambdas.nbytes + shot.weights.nbytes)
+    d2h = shot.npix * 4
+
+    # plain FP64 form on a strided pixel subset of the same shot
+    rows = W.strided_rows(shot, args.f64_rows_every)
+    sim64 = nbgb.Sim("f64", device=local, stream=stream).set_shot(shot)
+    sim64.add_spots(rows)
+    stream.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    sim64.add_spots(rows)
+    ev1.record(stream)
+    stream.synchronize()
+    t64 = ev0.elapsed_time(ev1) / 1e3
+    f64_rate = len(rows) * shot.steps_per_pixel / t64
+
+    if rank != 0:
+        return
+    from paper_2205_07976_gb300 import flops
+    evaluated, _ = sim.stats()  # terms evaluated by the last timed launch
+    t_kernel = sum(a.elapsed_time(b) for a, b in kernel_times) / 1e3 / len(
+        kernel_times)
+    alg = flops.algorithmic_flops(shot, evaluated)
+    achieved = alg / t_kernel / 1e12
+    peak_fp32 = flops.fp32_peak_tflops(152, 2070.0)
+    sm_mhz = clocks["sm_mhz"] if clocks else None
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_step * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+ff",
+        "data": "synthetic (seeded)",
+        "config": {"workload": WORKLOAD, "pixels": shot.npix,
+                   "steps_per_pixel": shot.steps_per_pixel,
+                   "pixel_steps_per_image": shot.pixel_steps,
+                   "precision": "FP32-mixed", "parallelism": "replicas",
+                   "l2": "512 MB buffer rewritten between timed steps"},
+        "e2e": {"value": shot.pixel_steps * world / t_e2e, "unit": UNIT,
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": d2h},
+        "f64": {"value": f64_rate, "unit": UNIT,
+                "sample": f"every {args.f64_rows_every}th row "
+                          f"({len(rows)} pixels)", "ms": t64 * 1e3},
+        "gpu_launches": args.steps,
+        "roofline": {"bound": "alu", "achieved": achieved,
+                     "peak": peak_fp32, "unit": "TFLOP/s",
+                     "frac": achieved / peak_fp32, "traffic": None,
+                     "kernel": "spots_mixed", "kernel_ms": t_kernel * 1e3,
+                     "algorithmic_tflop_per_launch": alg / 1e12,
+                     "evaluated_terms": evaluated,
+                     "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x "
+                                    "2070 MHz (derived from unit counts; "
+                                    "FP32 is not in MEASURED_PEAKS)",
+                     "frac_at_measured_clock": (
+                         achieved / flops.fp32_peak_tflops(152, sm_mhz)
+                         if sm_mhz else None)},
+        "clocks": clocks,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(shot, 192)
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------- reference arm
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    from paper_2205_07976_gb300 import workloads as W
+    shot = W.large_shot(seed=1)
+    oracle.build()
+    every = 384
+    pix = W.strided_rows(shot, every)
+    for _ in range(args.warmup):
+        oracle.image(shot, pix[:3072])
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.image(shot, pix)
+    dt = (time.perf_counter() - t0) / args.steps
+    rate = len(pix) * shot.steps_per_pixel / dt
+    cores = oracle.max_threads()
+    sample = (f"every {every}th row of the large shot per step "
+              f"({len(pix)} pixels, {len(pix) * shot.steps_per_pixel:.3e} "
+              f"pixel-steps)")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded)",
+        "config": {"workload": WORKLOAD, "precision": "FP64 CPU oracle"},
+        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores,
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,193 @@
+/*
+ * nbgb.h -- C ABI of the GB300 Bragg-spot library (libnbgb.so).
+ *
+ * The library computes the per-pixel Bragg-spot image of one crystal shot:
+ * the nanoBraggSpots sum of Sec. III-B (every detector pixel independent;
+ * the sum runs over crystal orientation, mosaic domains and photon energy,
+ * with one structure factor per Bragg spot, Sec. II), here over
+ * subpixels x sensor layers x sources x phi steps x mosaic domains:
+ *
+ *   I_p += r_e^2 fluence scale / (os^2 M Phi)
+ *          * sum_{sub, layer, k, phi, m} F_cell(hkl)^2 F_latt(hkl)^2
+ *                                       * w_k cap pol omega,
+ *   hkl = (a, b, c)_{phi,m} . (d - i_k) / lambda_k,
+ *   (a, b, c)_{phi,m} = U_m R_phi (a, b, c)_lab.
+ *
+ * and accumulates it into a resident double image, the fused form of the
+ * addArray kernel of Sec. III-B (Listing 1: lhs[j] += (double) rhs[j]).
+ *
+ * Conventions
+ *   - Every function returns an nb_status and never aborts or throws.
+ *   - Every host array argument is copied before the call returns; the
+ *     caller keeps ownership.  Device tables and the image belong to the
+ *     handle until nb_free().
+ *   - Lengths: Angstrom for crystal axes and wavelengths, metres for the
+ *     detector.  The sample is at the origin.
+ *   - Global pixel index: panel-major, then slow, then fast.
+ *   - Work is queued on the handle's CUDA stream; nb_get_image() waits for it.
+ *   - Calls on one handle must not overlap (one host thread at a time).
+ */
+#ifndef NBGB_H
+#define NBGB_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nb_sim nb_sim; /* opaque, owned by the library */
+
+typedef enum {
+    NB_OK = 0,
+    NB_EINVAL = -1,   /* a bad argument (size, pointer, value)          */
+    NB_ENOMEM = -2,   /* a device or host allocation failed             */
+    NB_ECUDA = -3,    /* a CUDA call failed; nb_last_error() has text   */
+    NB_ESTATE = -4,   /* called out of order (e.g. spots before setup)  */
+    NB_ETIMEOUT = -5  /* a bounded device-side wait ran out             */
+} nb_status;
+
+typedef enum {
+    NB_F64 = 0,   /* plain FP64 throughout                                  */
+    NB_MIXED = 1, /* FP32 bulk; double-float scattering-vector.axis dots and
+                     fractional offsets; compensated FP32 accumulation     */
+    NB_F32 = 2    /* everything in FP32 (the precision sweep's lower arm)   */
+} nb_precision;
+
+enum { NB_SHAPE_SINC = 0, NB_SHAPE_GAUSS = 1 };
+enum { NB_INTERP_NEAREST = 0, NB_INTERP_TRICUBIC = 1 };
+enum { NB_DTYPE_F32 = 0, NB_DTYPE_F64 = 1 };
+
+/* One flat detector panel.  Pixel (s, f), subpixel (i, j) of an oversample
+ * os sits at origin + (f + (i+1/2)/os) pixel fdir + (s + (j+1/2)/os) pixel
+ * sdir; sensor layer t adds t * thickness / n_layers * ndir. */
+typedef struct {
+    double origin[3]; /* m, outer corner of pixel (0, 0)                  */
+    double fdir[3];   /* unit fast axis                                   */
+    double sdir[3];   /* unit slow axis                                   */
+    double ndir[3];   /* unit normal pointing away from the sample        */
+    double pixel_m;   /* square pixel size, m                             */
+    int nfast;
+    int nslow;
+} nb_panel;
+
+/* Create a handle on CUDA device `device` computing in `precision`, with
+ * its work queued on `cuda_stream` (a cudaStream_t; NULL: the legacy
+ * default stream).  *out receives the handle; on failure *out is NULL.
+ * Errors: NB_EINVAL (out NULL, bad precision), NB_ECUDA (bad device). */
+int nb_sim_create(nb_sim **out, int device, int precision, void *cuda_stream);
+
+/* Crystal (Sec. III-B: orientation and mosaicity; Sec. II: one structure
+ * factor per spot).
+ *   axes      9 doubles, rows a, b, c (Angstrom), lab frame, orientation
+ *             included.
+ *   umats     n_mosaic 3x3 row-major rotations U_m (mosaic domains).
+ *   n_phi, phi0_deg, phistep_deg, spindle
+ *             phi step j rotates the axes by phi0 + j*phistep degrees about
+ *             the spindle (any non-zero vector) before U_m applies.
+ *   Na, Nb, Nc  unit cells per mosaic block; integers for NB_SHAPE_SINC.
+ *   shape     NB_SHAPE_SINC: F_latt = prod sin(pi N h)/sin(pi h);
+ *             NB_SHAPE_GAUSS: F_latt = Na Nb Nc exp(-sum N^2 (h-h0)^2/0.63).
+ *   F         structure-factor amplitudes, float, hkl_n[0] x hkl_n[1] x
+ *             hkl_n[2], l fastest, for h in [hkl_min[0], hkl_min[0] +
+ *             hkl_n[0]) and so on.  NULL keeps the table of the previous
+ *             call (hkl_min, hkl_n, interp and default_F must then match or
+ *             are ignored when they are NULL / negative).
+ *   interp    NB_INTERP_NEAREST (F at the nearest node, default_F outside
+ *             the table) or NB_INTERP_TRICUBIC (4-point Lagrange per axis;
+ *             nearest where the 4x4x4 stencil leaves the table).
+ * Errors: NB_EINVAL for n_mosaic < 1, n_phi < 1, non-positive or (sinc)
+ * non-integral N, a zero spindle with n_phi > 1, empty table, NULL axes or
+ * umats, or F NULL before any table was set. */
+int nb_set_crystal(nb_sim *sim, const double axes[9], const double *umats,
+                   int n_mosaic, int n_phi, double phi0_deg,
+                   double phistep_deg, const double spindle[3], double Na,
+                   double Nb, double Nc, int shape, const float *F,
+                   const int hkl_min[3], const int hkl_n[3], int interp,
+                   double default_F);
+
+/* Overall intensity scale of the crystal (default 1). */
+int nb_set_scale(nb_sim *sim, double scale);
+
+/* Beam (Sec. III-B: photon energy; Sec. II: shot-to-shot spectrum).
+ *   dirs      n_src x 3 unit propagation directions.
+ *   lambda_A  n_src wavelengths (Angstrom, > 0).
+ *   weights   n_src weights w_k, used as given (pass weights summing to 1
+ *             for `fluence` to be the total fluence).
+ *   fluence   photons per m^2.
+ *   kahn_K    polarization factor K in [0, 1]; e_vec the E-vector of the
+ *             polarized part (not parallel to any source direction when
+ *             K != 0).
+ * Errors: NB_EINVAL for n_src < 1, NULL arrays, non-unit directions,
+ * lambda <= 0, K outside [0, 1], or e_vec parallel to a direction. */
+int nb_set_beam(nb_sim *sim, const double *dirs, const double *lambda_A,
+                const double *weights, int n_src, double fluence,
+                double kahn_K, const double e_vec[3]);
+
+/* Detector: n_panels panels (copied), oversample os >= 1 per axis,
+ * n_layers >= 1 sensor layers of a sensor `thickness_m` thick with
+ * attenuation length `atten_m`.  thickness 0 means a surface detector (the
+ * capture fraction is 1; n_layers must then be 1).  Resets the image to 0.
+ * Errors: NB_EINVAL for empty panels, non-positive sizes, layers with no
+ * thickness, atten_m <= 0 with thickness > 0. */
+int nb_set_detector(nb_sim *sim, int n_panels, const nb_panel *panels,
+                    int oversample, int n_layers, double thickness_m,
+                    double atten_m);
+
+/* Number of pixels of the detector (0 before nb_set_detector). */
+long long nb_num_pixels(const nb_sim *sim);
+
+/* Queue the Bragg-spot sum of every pixel and add it to the image (the
+ * fused addArray: image[p] += (double) I_p).  Asynchronous on the handle's
+ * stream.  Errors: NB_ESTATE before crystal, beam and detector are set;
+ * NB_ECUDA if the launch fails. */
+int nb_add_spots(nb_sim *sim);
+
+/* As nb_add_spots for the listed global pixel indices only (a host array
+ * of n_pix int64 values, copied; duplicates are added twice).  Errors:
+ * NB_EINVAL for an index outside [0, nb_num_pixels). */
+int nb_add_spots_pixels(nb_sim *sim, const long long *pixels, long long n_pix);
+
+/* Set every pixel of the image to 0 (asynchronous). */
+int nb_zero_image(nb_sim *sim);
+
+/* Copy the image (n_elems must equal nb_num_pixels) to dst, converted to
+ * dtype (NB_DTYPE_F32 / NB_DTYPE_F64); dst is device memory of the
+ * handle's device if on_device, else host memory.  Blocks until the
+ * handle's queued work and the copy are done.  Errors: NB_EINVAL for a
+ * mis-sized n_elems, NULL dst or a bad dtype. */
+int nb_get_image(nb_sim *sim, void *dst, size_t n_elems, int dtype,
+                 int on_device);
+
+/* Device pointer of the resident double image (for zero-copy readers on
+ * the same stream); NULL before nb_set_detector. */
+const double *nb_image_device_ptr(const nb_sim *sim);
+
+/* Work counts of the last nb_add_spots* call: *pixel_steps = pixels x
+ * subpixels x layers x sources x phi steps x mosaic domains; and
+ * *evaluated_terms = the steps whose term was evaluated (NB_MIXED and
+ * NB_F32 skip Gaussian terms whose F_latt^2 / (Na Nb Nc)^2 = exp(-2 sum
+ * N^2 f^2 / 0.63) lies below exp(-88) < FLT_MIN, i.e. terms that vanish in
+ * FP32; NB_F64 evaluates every step and reports 0 here).  Blocks until the
+ * launch is done.  Errors: NB_EINVAL for NULL outputs. */
+int nb_get_stats(nb_sim *sim, long long *evaluated_terms,
+                 long long *pixel_steps);
+
+/* Wait for the handle's queued work. */
+int nb_synchronize(nb_sim *sim);
+
+/* Free the handle and everything it owns; NULL is a no-op. */
+int nb_free(nb_sim *sim);
+
+/* Text of the last error on this handle ("" if none; a static string for a
+ * NULL handle).  Valid until the next call on the handle. */
+const char *nb_last_error(const nb_sim *sim);
+
+/* Library version string. */
+const char *nb_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NBGB_H */

@@ -1,0 +1,698 @@
+// nbgb_api.cu -- the C ABI of libnbgb (declared in include/nbgb.h): the
+// handle, argument checks, the per-shot host set-up (rotated axes per phi
+// step and mosaic domain, source tables, panel offsets) and the launches.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/nbgb.h"
+#include "nbgb_internal.cuh"
+
+using nbgb::DevPanel;
+using nbgb::SpotArgs;
+
+namespace {
+
+struct DevBuf {
+  void *p = nullptr;
+  size_t n = 0;
+  cudaError_t ensure(size_t bytes) {
+    if (bytes <= n && p) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+    if (bytes == 0) return cudaSuccess;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e == cudaSuccess) n = bytes;
+    return e;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+};
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+}  // namespace
+
+struct nb_sim {
+  int device = 0;
+  int precision = NB_MIXED;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  // state flags
+  bool have_crystal = false, have_F = false, have_beam = false,
+       have_det = false;
+  // crystal (host copies)
+  double axes[9] = {0};
+  std::vector<double> umats;
+  int n_mosaic = 0, n_phi = 1;
+  double phi0 = 0, phistep = 0, spindle[3] = {0, 1, 0};
+  double N[3] = {1, 1, 1};
+  int shape = NB_SHAPE_SINC;
+  double scale = 1.0;
+  int hmin[3] = {0, 0, 0}, hn[3] = {0, 0, 0};
+  int interp = NB_INTERP_NEAREST;
+  double defF = 0.0;
+  // beam
+  std::vector<double> dirs, lam, w;
+  int n_src = 0;
+  double fluence = 0, kahn = 0, evec[3] = {1, 0, 0};
+  // detector
+  std::vector<nb_panel> panels;
+  std::vector<long long> pix0;
+  long long npix = 0;
+  int n_tiles = 0;
+  int os = 1, T = 1;
+  double thick = 0, atten = 0;
+  // device
+  DevBuf d_panels, d_ax64, d_axh, d_axl, d_src64, d_src32, d_divh, d_divl,
+      d_F, d_image, d_list, d_tmp, d_stats;
+  long long last_pixel_steps = 0;
+  int has_div = 0;
+  double u0 = 0;
+  bool tables_dirty = true;
+};
+
+static int fail(nb_sim *s, int code, const std::string &msg) {
+  if (s) s->err = msg;
+  return code;
+}
+
+static int cuda_fail(nb_sim *s, cudaError_t e, const char *what) {
+  return fail(s, NB_ECUDA,
+              std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+static bool finite3(const double *v) {
+  return std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]);
+}
+
+static double norm3(const double *v) {
+  return std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+}
+
+// ------------------------------------------------------------ host set-up
+
+// Rotation by `ang` radians about the unit axis k, as a 3x3 matrix:
+// R = I + sin(ang) K + (1 - cos(ang)) K^2 with K the cross-product matrix.
+static void axis_rotation(const double *k, double ang, double *R) {
+  double K[9] = {0, -k[2], k[1], k[2], 0, -k[0], -k[1], k[0], 0};
+  double K2[9];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double v = 0;
+      for (int l = 0; l < 3; ++l) v += K[3 * i + l] * K[3 * l + j];
+      K2[3 * i + j] = v;
+    }
+  double sn = std::sin(ang), cs = 1.0 - std::cos(ang);
+  for (int i = 0; i < 9; ++i)
+    R[i] = (i % 4 == 0 ? 1.0 : 0.0) + sn * K[i] + cs * K2[i];
+}
+
+// rows (a, b, c) of U_m R_phi(j) (a, b, c)_lab for all (j, m): ax[pm][9]
+static void build_axes(const nb_sim *s, std::vector<double> &ax) {
+  int PM = s->n_phi * s->n_mosaic;
+  ax.assign((size_t)PM * 9, 0.0);
+  double k[3] = {0, 1, 0};
+  double nk = norm3(s->spindle);
+  if (nk > 0)
+    for (int i = 0; i < 3; ++i) k[i] = s->spindle[i] / nk;
+  for (int j = 0; j < s->n_phi; ++j) {
+    double R[9];
+    axis_rotation(k, (s->phi0 + j * s->phistep) * (M_PI / 180.0), R);
+    for (int m = 0; m < s->n_mosaic; ++m) {
+      const double *U = s->umats.data() + 9 * m;
+      double UR[9];
+      for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c)
+          UR[3 * r + c] = U[3 * r] * R[c] + U[3 * r + 1] * R[3 + c] +
+                          U[3 * r + 2] * R[6 + c];
+      double *out = ax.data() + ((size_t)j * s->n_mosaic + m) * 9;
+      for (int v = 0; v < 3; ++v)
+        for (int r = 0; r < 3; ++r)
+          out[3 * v + r] = UR[3 * r] * s->axes[3 * v] +
+                           UR[3 * r + 1] * s->axes[3 * v + 1] +
+                           UR[3 * r + 2] * s->axes[3 * v + 2];
+    }
+  }
+}
+
+// transverse polarization basis of source direction dir: E' = unit part of
+// e normal to dir, B' = dir x E'
+static void pol_basis(const double *dir, const double *e, double *ep,
+                      double *bp) {
+  double de = dir[0] * e[0] + dir[1] * e[1] + dir[2] * e[2];
+  for (int i = 0; i < 3; ++i) ep[i] = e[i] - de * dir[i];
+  double n = norm3(ep);
+  for (int i = 0; i < 3; ++i) ep[i] /= n;
+  bp[0] = dir[1] * ep[2] - dir[2] * ep[1];
+  bp[1] = dir[2] * ep[0] - dir[0] * ep[2];
+  bp[2] = dir[0] * ep[1] - dir[1] * ep[0];
+}
+
+static void split_ff(double v, float &hi, float &lo) {
+  hi = (float)v;
+  lo = (float)(v - (double)hi);
+}
+
+// Uploads the crystal x beam tables (they depend on both).
+static int upload_tables(nb_sim *s) {
+  if (!s->tables_dirty) return NB_OK;
+  int PM = s->n_phi * s->n_mosaic, S = s->n_src;
+  std::vector<double> ax;
+  build_axes(s, ax);
+  std::vector<float> axh(ax.size()), axl(ax.size());
+  for (size_t i = 0; i < ax.size(); ++i) split_ff(ax[i], axh[i], axl[i]);
+  // sources: u = 1/lambda, u0 the centre of the range
+  double umin = 1e300, umax = -1e300;
+  for (int k = 0; k < S; ++k) {
+    double u = 1.0 / s->lam[k];
+    umin = std::fmin(umin, u);
+    umax = std::fmax(umax, u);
+  }
+  s->u0 = 0.5 * (umin + umax);
+  std::vector<double> src64((size_t)S * nbgb::SRC64_STRIDE);
+  std::vector<float> src32((size_t)S * nbgb::SRC32_STRIDE);
+  s->has_div = 0;
+  for (int k = 0; k < S; ++k) {
+    const double *dir = s->dirs.data() + 3 * k;
+    for (int c = 0; c < 3; ++c)
+      if (dir[c] != s->dirs[c]) s->has_div = 1;
+  }
+  for (int k = 0; k < S; ++k) {
+    const double *dir = s->dirs.data() + 3 * k;
+    double u = 1.0 / s->lam[k], ep[3], bp[3];
+    pol_basis(dir, s->evec, ep, bp);
+    double *r = src64.data() + (size_t)k * nbgb::SRC64_STRIDE;
+    r[nbgb::SRC64_LAM] = s->lam[k];
+    r[nbgb::SRC64_W] = s->w[k];
+    float *q = src32.data() + (size_t)k * nbgb::SRC32_STRIDE;
+    if (s->precision == NB_F32) {
+      q[nbgb::SRC32_DH] = 0.f;
+      q[nbgb::SRC32_DL] = (float)u;  // plain FP32 arm reads u_k here
+    } else {
+      split_ff(u - s->u0, q[nbgb::SRC32_DH], q[nbgb::SRC32_DL]);
+    }
+    q[nbgb::SRC32_W] = (float)s->w[k];
+    for (int c = 0; c < 3; ++c) {
+      r[nbgb::SRC64_DIR + c] = dir[c];
+      r[nbgb::SRC64_E + c] = ep[c];
+      r[nbgb::SRC64_B + c] = bp[c];
+      q[nbgb::SRC32_DIR + c] = (float)dir[c];
+      q[nbgb::SRC32_E + c] = (float)ep[c];
+      q[nbgb::SRC32_B + c] = (float)bp[c];
+    }
+  }
+  // divergence term E[pm][k][x] = A_pm,x . (i_k - i_0) u_k
+  std::vector<float> divh, divl;
+  if (s->has_div) {
+    divh.resize((size_t)PM * S * 3);
+    divl.resize(divh.size());
+    for (int pm = 0; pm < PM; ++pm)
+      for (int k = 0; k < S; ++k) {
+        double di[3], u = 1.0 / s->lam[k];
+        for (int c = 0; c < 3; ++c) di[c] = s->dirs[3 * k + c] - s->dirs[c];
+        for (int x = 0; x < 3; ++x) {
+          const double *A = ax.data() + (size_t)pm * 9 + 3 * x;
+          double E = (A[0] * di[0] + A[1] * di[1] + A[2] * di[2]) * u;
+          size_t e = ((size_t)pm * S + k) * 3 + x;
+          split_ff(E, divh[e], divl[e]);
+        }
+      }
+  }
+  cudaError_t e;
+  if ((e = s->d_ax64.ensure(ax.size() * 8)) != cudaSuccess ||
+      (e = s->d_axh.ensure(axh.size() * 4)) != cudaSuccess ||
+      (e = s->d_axl.ensure(axl.size() * 4)) != cudaSuccess ||
+      (e = s->d_src64.ensure(src64.size() * 8)) != cudaSuccess ||
+      (e = s->d_src32.ensure(src32.size() * 4)) != cudaSuccess)
+    return fail(s, NB_ENOMEM, std::string("device tables: ") +
+                                  cudaGetErrorString(e));
+  cudaMemcpyAsync(s->d_ax64.p, ax.data(), ax.size() * 8,
+                  cudaMemcpyHostToDevice, s->stream);
+  cudaMemcpyAsync(s->d_axh.p, axh.data(), axh.size() * 4,
+                  cudaMemcpyHostToDevice, s->stream);
+  cudaMemcpyAsync(s->d_axl.p, axl.data(), axl.size() * 4,
+                  cudaMemcpyHostToDevice, s->stream);
+  cudaMemcpyAsync(s->d_src64.p, src64.data(), src64.size() * 8,
+                  cudaMemcpyHostToDevice, s->stream);
+  cudaMemcpyAsync(s->d_src32.p, src32.data(), src32.size() * 4,
+                  cudaMemcpyHostToDevice, s->stream);
+  if (s->has_div) {
+    if ((e = s->d_divh.ensure(divh.size() * 4)) != cudaSuccess ||
+        (e = s->d_divl.ensure(divl.size() * 4)) != cudaSuccess)
+      return fail(s, NB_ENOMEM, "divergence table");
+    cudaMemcpyAsync(s->d_divh.p, divh.data(), divh.size() * 4,
+                    cudaMemcpyHostToDevice, s->stream);
+    cudaMemcpyAsync(s->d_divl.p, divl.data(), divl.size() * 4,
+                    cudaMemcpyHostToDevice, s->stream);
+  }
+  // pageable copies are staged before return; check the queue is healthy
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(s, e, "table upload");
+  s->tables_dirty = false;
+  return NB_OK;
+}
+
+static void fill_args(const nb_sim *s, SpotArgs &a) {
+  std::memset(&a, 0, sizeof a);
+  a.panels = (const DevPanel *)s->d_panels.p;
+  a.n_panels = (int)s->panels.size();
+  a.n_tiles = s->n_tiles;
+  a.npix = s->npix;
+  a.os = s->os;
+  a.T = s->T;
+  a.dt = s->thick > 0 ? s->thick / s->T : 0.0;
+  a.thickness = s->thick;
+  a.atten = s->atten;
+  a.PM = s->n_phi * s->n_mosaic;
+  a.ax64 = (const double *)s->d_ax64.p;
+  a.axh = (const float *)s->d_axh.p;
+  a.axl = (const float *)s->d_axl.p;
+  for (int i = 0; i < 3; ++i) {
+    a.N64[i] = s->N[i];
+    a.N[i] = (float)s->N[i];
+    a.hmin[i] = s->hmin[i];
+    a.hn[i] = s->hn[i];
+    a.i0[i] = s->dirs[i];
+  }
+  double nn = s->N[0] * s->N[1] * s->N[2];
+  a.N6 = (float)(nn * nn);
+  a.shape = s->shape;
+  a.interp = s->interp;
+  a.F = (const float *)s->d_F.p;
+  a.defF = (float)s->defF;
+  a.defF64 = s->defF;
+  a.S = s->n_src;
+  a.src64 = (const double *)s->d_src64.p;
+  a.src32 = (const float *)s->d_src32.p;
+  a.u0 = s->u0;
+  split_ff(s->u0, a.u0h, a.u0l);
+  pol_basis(s->dirs.data(), s->evec, a.e0, a.b0);
+  a.kahn = (float)s->kahn;
+  a.kahn64 = s->kahn;
+  a.has_div = s->has_div;
+  a.divh = (const float *)s->d_divh.p;
+  a.divl = (const float *)s->d_divl.p;
+  a.prefactor = nbgb::kElectronRadius * nbgb::kElectronRadius * s->fluence *
+                s->scale / ((double)s->os * s->os * s->n_mosaic * s->n_phi);
+  a.image = (double *)s->d_image.p;
+}
+
+// ------------------------------------------------------------------- ABI
+
+extern "C" {
+
+const char *nb_version(void) { return "nbgb 0.1 (sm_103a)"; }
+
+const char *nb_last_error(const nb_sim *sim) {
+  if (!sim) return "null handle";
+  return sim->err.c_str();
+}
+
+int nb_sim_create(nb_sim **out, int device, int precision,
+                  void *cuda_stream) {
+  if (!out) return NB_EINVAL;
+  *out = nullptr;
+  if (precision < NB_F64 || precision > NB_F32) return NB_EINVAL;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 ||
+      device >= ndev) {
+    cudaGetLastError();
+    return NB_ECUDA;
+  }
+  nb_sim *s = new (std::nothrow) nb_sim();
+  if (!s) return NB_ENOMEM;
+  s->device = device;
+  s->precision = precision;
+  s->stream = (cudaStream_t)cuda_stream;
+  *out = s;
+  return NB_OK;
+}
+
+int nb_free(nb_sim *sim) {
+  if (!sim) return NB_OK;
+  {
+    DeviceGuard g(sim->device);
+    cudaStreamSynchronize(sim->stream);
+    DevBuf *bufs[] = {&sim->d_panels, &sim->d_ax64, &sim->d_axh,
+                      &sim->d_axl,    &sim->d_src64, &sim->d_src32,
+                      &sim->d_divh,   &sim->d_divl,  &sim->d_F,
+                      &sim->d_image,  &sim->d_list,  &sim->d_tmp,
+                      &sim->d_stats};
+    for (DevBuf *b : bufs) b->release();
+  }
+  delete sim;
+  return NB_OK;
+}
+
+int nb_set_crystal(nb_sim *s, const double axes[9], const double *umats,
+                   int n_mosaic, int n_phi, double phi0_deg,
+                   double phistep_deg, const double spindle[3], double Na,
+                   double Nb, double Nc, int shape, const float *F,
+                   const int hkl_min[3], const int hkl_n[3], int interp,
+                   double default_F) {
+  if (!s) return NB_EINVAL;
+  if (!axes || !umats) return fail(s, NB_EINVAL, "axes/umats NULL");
+  if (n_mosaic < 1 || n_phi < 1 || (long long)n_mosaic * n_phi > nbgb::kMaxPM)
+    return fail(s, NB_EINVAL, "need 1 <= n_mosaic*n_phi <= 2048");
+  if (shape != NB_SHAPE_SINC && shape != NB_SHAPE_GAUSS)
+    return fail(s, NB_EINVAL, "bad shape");
+  double N[3] = {Na, Nb, Nc};
+  for (int i = 0; i < 3; ++i) {
+    if (!(N[i] > 0) || !std::isfinite(N[i]))
+      return fail(s, NB_EINVAL, "N must be positive");
+    if (shape == NB_SHAPE_SINC && N[i] != std::floor(N[i]))
+      return fail(s, NB_EINVAL, "sinc shape needs integral N");
+  }
+  for (int i = 0; i < 9; ++i)
+    if (!std::isfinite(axes[i])) return fail(s, NB_EINVAL, "axes not finite");
+  double sp[3] = {0, 1, 0};
+  if (spindle) std::memcpy(sp, spindle, sizeof sp);
+  if (n_phi > 1 && !(norm3(sp) > 0))
+    return fail(s, NB_EINVAL, "zero spindle with n_phi > 1");
+  if (F) {
+    if (!hkl_min || !hkl_n) return fail(s, NB_EINVAL, "hkl_min/hkl_n NULL");
+    for (int i = 0; i < 3; ++i)
+      if (hkl_n[i] < 1) return fail(s, NB_EINVAL, "empty structure-factor table");
+    if (interp != NB_INTERP_NEAREST && interp != NB_INTERP_TRICUBIC)
+      return fail(s, NB_EINVAL, "bad interp");
+  } else if (!s->have_F) {
+    return fail(s, NB_EINVAL, "no structure-factor table yet");
+  }
+  DeviceGuard g(s->device);
+  std::memcpy(s->axes, axes, sizeof s->axes);
+  s->umats.assign(umats, umats + 9 * (size_t)n_mosaic);
+  s->n_mosaic = n_mosaic;
+  s->n_phi = n_phi;
+  s->phi0 = phi0_deg;
+  s->phistep = phistep_deg;
+  std::memcpy(s->spindle, sp, sizeof sp);
+  std::memcpy(s->N, N, sizeof N);
+  s->shape = shape;
+  if (F) {
+    size_t nF = (size_t)hkl_n[0] * hkl_n[1] * hkl_n[2];
+    cudaError_t e = s->d_F.ensure(nF * sizeof(float));
+    if (e != cudaSuccess) return fail(s, NB_ENOMEM, "F table");
+    e = cudaMemcpyAsync(s->d_F.p, F, nF * sizeof(float),
+                        cudaMemcpyHostToDevice, s->stream);
+    // the caller's array may be pinned: finish the copy before returning
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "F upload");
+    for (int i = 0; i < 3; ++i) {
+      s->hmin[i] = hkl_min[i];
+      s->hn[i] = hkl_n[i];
+    }
+    s->interp = interp;
+    s->defF = default_F;
+    s->have_F = true;
+  } else {
+    if (interp == NB_INTERP_NEAREST || interp == NB_INTERP_TRICUBIC)
+      s->interp = interp;
+    if (std::isfinite(default_F)) s->defF = default_F;
+  }
+  s->have_crystal = true;
+  s->tables_dirty = true;
+  return NB_OK;
+}
+
+int nb_set_scale(nb_sim *s, double scale) {
+  if (!s) return NB_EINVAL;
+  if (!std::isfinite(scale)) return fail(s, NB_EINVAL, "scale not finite");
+  s->scale = scale;
+  return NB_OK;
+}
+
+int nb_set_beam(nb_sim *s, const double *dirs, const double *lambda_A,
+                const double *weights, int n_src, double fluence,
+                double kahn_K, const double e_vec[3]) {
+  if (!s) return NB_EINVAL;
+  if (n_src < 1 || n_src > nbgb::kMaxSrc)
+    return fail(s, NB_EINVAL, "need 1 <= n_src <= 1024");
+  if (!dirs || !lambda_A || !weights)
+    return fail(s, NB_EINVAL, "beam arrays NULL");
+  if (!(kahn_K >= 0 && kahn_K <= 1))
+    return fail(s, NB_EINVAL, "kahn_K outside [0, 1]");
+  if (!std::isfinite(fluence)) return fail(s, NB_EINVAL, "fluence");
+  double e[3] = {1, 0, 0};
+  if (e_vec) std::memcpy(e, e_vec, sizeof e);
+  for (int k = 0; k < n_src; ++k) {
+    const double *d = dirs + 3 * k;
+    if (!finite3(d) || std::fabs(norm3(d) - 1.0) > 1e-9)
+      return fail(s, NB_EINVAL, "source direction not unit");
+    if (!(lambda_A[k] > 0) || !std::isfinite(lambda_A[k]))
+      return fail(s, NB_EINVAL, "wavelength must be positive");
+    if (!std::isfinite(weights[k])) return fail(s, NB_EINVAL, "weight");
+    double de = d[0] * e[0] + d[1] * e[1] + d[2] * e[2];
+    double t[3] = {e[0] - de * d[0], e[1] - de * d[1], e[2] - de * d[2]};
+    if (!(norm3(t) > 1e-6 * norm3(e)))
+      return fail(s, NB_EINVAL, "e_vec parallel to a source direction");
+  }
+  s->dirs.assign(dirs, dirs + 3 * (size_t)n_src);
+  s->lam.assign(lambda_A, lambda_A + n_src);
+  s->w.assign(weights, weights + n_src);
+  s->n_src = n_src;
+  s->fluence = fluence;
+  s->kahn = kahn_K;
+  std::memcpy(s->evec, e, sizeof e);
+  s->have_beam = true;
+  s->tables_dirty = true;
+  return NB_OK;
+}
+
+long long nb_num_pixels(const nb_sim *s) { return s ? s->npix : 0; }
+
+int nb_set_detector(nb_sim *s, int n_panels, const nb_panel *panels,
+                    int oversample, int n_layers, double thickness_m,
+                    double atten_m) {
+  if (!s) return NB_EINVAL;
+  if (n_panels < 1 || !panels) return fail(s, NB_EINVAL, "no panels");
+  if (oversample < 1 || oversample > 64 || n_layers < 1 || n_layers > 64)
+    return fail(s, NB_EINVAL, "oversample / n_layers out of range");
+  if (!(thickness_m >= 0) || !std::isfinite(thickness_m))
+    return fail(s, NB_EINVAL, "thickness");
+  if (thickness_m == 0 && n_layers != 1)
+    return fail(s, NB_EINVAL, "layers need a sensor thickness");
+  if (thickness_m > 0 && !(atten_m > 0))
+    return fail(s, NB_EINVAL, "attenuation length must be positive");
+  std::vector<DevPanel> dp(n_panels);
+  std::vector<long long> pix0(n_panels);
+  long long npix = 0;
+  int tiles = 0;
+  for (int q = 0; q < n_panels; ++q) {
+    const nb_panel &p = panels[q];
+    if (p.nfast < 1 || p.nslow < 1 || !(p.pixel_m > 0))
+      return fail(s, NB_EINVAL, "panel size");
+    if (!finite3(p.origin) || !finite3(p.fdir) || !finite3(p.sdir) ||
+        !finite3(p.ndir))
+      return fail(s, NB_EINVAL, "panel vectors not finite");
+    DevPanel &d = dp[q];
+    std::memset(&d, 0, sizeof d);
+    for (int c = 0; c < 3; ++c) {
+      d.origin[c] = p.origin[c];
+      d.fdir[c] = p.fdir[c];
+      d.sdir[c] = p.sdir[c];
+      d.ndir[c] = p.ndir[c];
+    }
+    d.px = p.pixel_m;
+    d.nfast = p.nfast;
+    d.nslow = p.nslow;
+    d.pix0 = npix;
+    d.tile0 = tiles;
+    d.tiles_f = (p.nfast + nbgb::kTileF - 1) / nbgb::kTileF;
+    d.tiles = d.tiles_f * ((p.nslow + nbgb::kTileS - 1) / nbgb::kTileS);
+    pix0[q] = npix;
+    npix += (long long)p.nfast * p.nslow;
+    if ((long long)tiles + d.tiles > 2000000000LL)
+      return fail(s, NB_EINVAL, "detector too large");
+    tiles += d.tiles;
+  }
+  DeviceGuard g(s->device);
+  cudaError_t e = s->d_panels.ensure(dp.size() * sizeof(DevPanel));
+  if (e != cudaSuccess) return fail(s, NB_ENOMEM, "panel table");
+  e = cudaMemcpyAsync(s->d_panels.p, dp.data(), dp.size() * sizeof(DevPanel),
+                      cudaMemcpyHostToDevice, s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e, "panel upload");
+  e = s->d_image.ensure((size_t)npix * sizeof(double));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(s, NB_ENOMEM, "image");
+  }
+  e = cudaMemsetAsync(s->d_image.p, 0, (size_t)npix * sizeof(double),
+                      s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e, "image clear");
+  s->panels.assign(panels, panels + n_panels);
+  s->pix0 = pix0;
+  s->npix = npix;
+  s->n_tiles = tiles;
+  s->os = oversample;
+  s->T = n_layers;
+  s->thick = thickness_m;
+  s->atten = atten_m;
+  s->have_det = true;
+  return NB_OK;
+}
+
+static int launch(nb_sim *s, const long long *dev_list, long long n_list) {
+  if (!s->have_crystal || !s->have_beam || !s->have_det || !s->have_F)
+    return fail(s, NB_ESTATE, "crystal, beam and detector must be set first");
+  int rc = upload_tables(s);
+  if (rc != NB_OK) return rc;
+  SpotArgs a;
+  fill_args(s, a);
+  a.pixlist = dev_list;
+  a.n_list = n_list;
+  size_t smem_need =
+      s->precision == NB_F64
+          ? (size_t)(a.PM * 9 + a.S * nbgb::SRC64_STRIDE) * sizeof(double)
+          : (size_t)(2 * a.PM * 9 + a.S * nbgb::SRC32_STRIDE) * sizeof(float);
+  if (smem_need > 200 * 1024)
+    return fail(s, NB_EINVAL,
+                "phi x mosaic and source tables exceed 200 KB of shared "
+                "memory");
+  cudaError_t e = s->d_stats.ensure(sizeof(unsigned long long));
+  if (e != cudaSuccess) return fail(s, NB_ENOMEM, "statistics counter");
+  e = cudaMemsetAsync(s->d_stats.p, 0, sizeof(unsigned long long), s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e, "statistics reset");
+  a.stats = (unsigned long long *)s->d_stats.p;
+  long long pix = dev_list ? n_list : s->npix;
+  s->last_pixel_steps = pix * (long long)s->os * s->os * s->T * s->n_src *
+                        s->n_mosaic * s->n_phi;
+  e = s->precision == NB_F64
+          ? nbgb::launch_spots_f64(a, s->stream)
+          : nbgb::launch_spots_mixed(a, s->precision, s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e, "spots launch");
+  return NB_OK;
+}
+
+int nb_add_spots(nb_sim *s) {
+  if (!s) return NB_EINVAL;
+  DeviceGuard g(s->device);
+  return launch(s, nullptr, 0);
+}
+
+int nb_add_spots_pixels(nb_sim *s, const long long *pixels,
+                        long long n_pix) {
+  if (!s) return NB_EINVAL;
+  if (n_pix < 0 || (n_pix > 0 && !pixels))
+    return fail(s, NB_EINVAL, "pixel list");
+  if (!s->have_det) return fail(s, NB_ESTATE, "detector not set");
+  for (long long i = 0; i < n_pix; ++i)
+    if (pixels[i] < 0 || pixels[i] >= s->npix)
+      return fail(s, NB_EINVAL, "pixel index out of range");
+  if (n_pix == 0) return NB_OK;
+  DeviceGuard g(s->device);
+  // the list buffer may still be read by an earlier launch on the stream
+  cudaError_t e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e, "stream sync");
+  e = s->d_list.ensure((size_t)n_pix * sizeof(long long));
+  if (e != cudaSuccess) return fail(s, NB_ENOMEM, "pixel list");
+  e = cudaMemcpyAsync(s->d_list.p, pixels, (size_t)n_pix * sizeof(long long),
+                      cudaMemcpyHostToDevice, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e, "pixel list upload");
+  return launch(s, (const long long *)s->d_list.p, n_pix);
+}
+
+int nb_zero_image(nb_sim *s) {
+  if (!s) return NB_EINVAL;
+  if (!s->have_det) return fail(s, NB_ESTATE, "detector not set");
+  DeviceGuard g(s->device);
+  cudaError_t e = cudaMemsetAsync(s->d_image.p, 0,
+                                  (size_t)s->npix * sizeof(double), s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e, "image clear");
+  return NB_OK;
+}
+
+__global__ void nb_to_f32_kernel(const double *src, float *dst, long long n) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  long long stride = (long long)gridDim.x * blockDim.x;
+  for (; i < n; i += stride) dst[i] = (float)src[i];
+}
+
+int nb_get_image(nb_sim *s, void *dst, size_t n_elems, int dtype,
+                 int on_device) {
+  if (!s) return NB_EINVAL;
+  if (!dst) return fail(s, NB_EINVAL, "dst NULL");
+  if (!s->have_det) return fail(s, NB_ESTATE, "detector not set");
+  if ((long long)n_elems != s->npix)
+    return fail(s, NB_EINVAL, "n_elems differs from the pixel count");
+  if (dtype != NB_DTYPE_F32 && dtype != NB_DTYPE_F64)
+    return fail(s, NB_EINVAL, "bad dtype");
+  DeviceGuard g(s->device);
+  cudaError_t e;
+  size_t n = n_elems;
+  if (dtype == NB_DTYPE_F64) {
+    e = cudaMemcpyAsync(dst, s->d_image.p, n * 8,
+                        on_device ? cudaMemcpyDeviceToDevice
+                                  : cudaMemcpyDeviceToHost,
+                        s->stream);
+  } else {
+    float *target = (float *)dst;
+    if (!on_device) {
+      e = s->d_tmp.ensure(n * 4);
+      if (e != cudaSuccess) return fail(s, NB_ENOMEM, "conversion buffer");
+      target = (float *)s->d_tmp.p;
+    }
+    nb_to_f32_kernel<<<1216, 256, 0, s->stream>>>((const double *)s->d_image.p,
+                                                  target, (long long)n);
+    e = cudaGetLastError();
+    if (e == cudaSuccess && !on_device)
+      e = cudaMemcpyAsync(dst, s->d_tmp.p, n * 4, cudaMemcpyDeviceToHost,
+                          s->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(s, e, "image copy");
+  e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e, "image copy sync");
+  return NB_OK;
+}
+
+const double *nb_image_device_ptr(const nb_sim *s) {
+  return (s && s->have_det) ? (const double *)s->d_image.p : nullptr;
+}
+
+int nb_get_stats(nb_sim *s, long long *evaluated_terms,
+                 long long *pixel_steps) {
+  if (!s) return NB_EINVAL;
+  if (!evaluated_terms || !pixel_steps)
+    return fail(s, NB_EINVAL, "NULL output");
+  *evaluated_terms = 0;
+  *pixel_steps = s->last_pixel_steps;
+  if (!s->d_stats.p) return NB_OK;
+  DeviceGuard g(s->device);
+  unsigned long long v = 0;
+  cudaError_t e = cudaMemcpyAsync(&v, s->d_stats.p, sizeof v,
+                                  cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e, "statistics read");
+  *evaluated_terms = (long long)v;
+  return NB_OK;
+}
+
+int nb_synchronize(nb_sim *s) {
+  if (!s) return NB_EINVAL;
+  DeviceGuard g(s->device);
+  cudaError_t e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e, "synchronize");
+  return NB_OK;
+}
+
+}  // extern "C"

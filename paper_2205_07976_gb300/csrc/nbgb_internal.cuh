@@ -1,0 +1,216 @@
+// nbgb_internal.cuh -- kernel-side data layout and helpers of libnbgb.
+//
+// Layout in HBM (all device buffers owned by one nb_sim handle):
+//   panels   DevPanel[n_panels]            geometry + pixel/tile offsets
+//   ax64     double[PM][9]                 U_m R_phi (a,b,c)_lab, PM = Phi*M
+//   axh/axl  float[PM][9]                  double-float split of ax64
+//   src64    double[S][SRC64_STRIDE]       lambda, w, dir, E', B'
+//   src32    float [S][SRC32_STRIDE]       delta_hi, delta_lo, w, dir, E', B'
+//   divh/l   float[PM][S][3]               divergence term (only if sources
+//                                           do not share one direction)
+//   F        float[nh][nk][nl]             structure factors, l fastest
+//   image    double[npix]                  resident accumulator
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace nbgb {
+
+constexpr double kElectronRadius = 2.8179403262e-15;  // m, CODATA 2018
+constexpr int kTileF = 16;                            // pixels per tile, fast
+constexpr int kTileS = 8;                             // pixels per tile, slow
+constexpr int kTileThreads = kTileF * kTileS;
+constexpr int kMaxPM = 2048;
+constexpr int kMaxSrc = 1024;
+// Gaussian terms with sum N^2 f^2 / 0.63 above this are skipped: their
+// F_latt^2 / (Na Nb Nc)^2 = exp(-2 * 44) < FLT_MIN, i.e. they vanish in the
+// FP32 evaluation anyway.
+constexpr float kGaussCut = 44.0f;
+
+enum { SRC64_LAM = 0, SRC64_W = 1, SRC64_DIR = 2, SRC64_E = 5, SRC64_B = 8,
+       SRC64_STRIDE = 11 };
+enum { SRC32_DH = 0, SRC32_DL = 1, SRC32_W = 2, SRC32_DIR = 3, SRC32_E = 6,
+       SRC32_B = 9, SRC32_STRIDE = 12 };
+
+struct DevPanel {
+  double origin[3];
+  double fdir[3];
+  double sdir[3];
+  double ndir[3];
+  double px;
+  long long pix0;  // global index of pixel (0, 0)
+  int nfast, nslow;
+  int tile0;       // first tile of this panel in the tiled launch
+  int tiles_f;     // tiles along fast
+  int tiles;       // tiles of this panel
+  int pad;
+};
+
+struct SpotArgs {
+  // detector
+  const DevPanel *panels;
+  int n_panels;
+  int n_tiles;
+  long long npix;
+  const long long *pixlist;  // non-null: launch over this pixel list
+  long long n_list;
+  int os, T;
+  double dt, thickness, atten;
+  // crystal
+  int PM;
+  const double *ax64;
+  const float *axh, *axl;
+  double N64[3];
+  float N[3];
+  float N6;  // (Na Nb Nc)^2
+  int shape, interp;
+  const float *F;
+  int hmin[3], hn[3];
+  float defF;
+  double defF64;
+  // beam
+  int S;
+  const double *src64;
+  const float *src32;
+  double u0;
+  float u0h, u0l;
+  double i0[3];  // direction of source 0 (all sources, unless has_div)
+  double e0[3], b0[3];
+  float kahn;
+  double kahn64;
+  int has_div;
+  const float *divh, *divl;
+  double prefactor;  // r_e^2 fluence scale / (os^2 M Phi)
+  double *image;
+  // statistics of the launch: [0] terms evaluated (the FP32 forms skip
+  // Gaussian terms that underflow); null to skip counting
+  unsigned long long *stats;
+};
+
+// adds v of every active lane to *ctr with one atomic per converged group
+__device__ __forceinline__ void warp_count(unsigned long long *ctr,
+                                           unsigned v) {
+  unsigned mask = __activemask();
+  unsigned tot = __reduce_add_sync(mask, v);
+  if ((threadIdx.x & 31) == __ffs(mask) - 1)
+    atomicAdd(ctr, (unsigned long long)tot);
+}
+
+// ---------------------------------------------------------------- mapping
+
+__device__ __forceinline__ int panel_of_tile(const SpotArgs &a, int tile) {
+  int lo = 0, hi = a.n_panels - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (a.panels[mid].tile0 <= tile) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ int panel_of_pixel(const SpotArgs &a,
+                                              long long g) {
+  int lo = 0, hi = a.n_panels - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (a.panels[mid].pix0 <= g) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Pixel handled by (block, thread): a 16x8 tile per block, or one entry of
+// the pixel list.  Returns false for threads past the panel edge.
+__device__ __forceinline__ bool map_pixel(const SpotArgs &a, long long item,
+                                          int lane_in_tile, long long &gp,
+                                          int &q, int &s, int &f) {
+  if (a.pixlist) {
+    if (item >= a.n_list) return false;
+    gp = a.pixlist[item];
+    q = panel_of_pixel(a, gp);
+    long long local = gp - a.panels[q].pix0;
+    int nf = a.panels[q].nfast;
+    s = (int)(local / nf);
+    f = (int)(local - (long long)s * nf);
+    return true;
+  }
+  int tile = (int)item;
+  if (tile >= a.n_tiles) return false;
+  q = panel_of_tile(a, tile);
+  const DevPanel &P = a.panels[q];
+  int t = tile - P.tile0;
+  int ts = t / P.tiles_f, tf = t - ts * P.tiles_f;
+  s = ts * kTileS + lane_in_tile / kTileF;
+  f = tf * kTileF + lane_in_tile % kTileF;
+  if (s >= P.nslow || f >= P.nfast) return false;
+  gp = P.pix0 + (long long)s * P.nfast + f;
+  return true;
+}
+
+// ------------------------------------------------- error-free FP32 steps
+// (Dekker / Knuth transformations; the _rn intrinsics keep the compiler
+// from contracting them into FMAs)
+
+__device__ __forceinline__ void two_sum(float a, float b, float &s,
+                                        float &e) {
+  s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__device__ __forceinline__ void fast_two_sum(float a, float b, float &s,
+                                             float &e) {
+  s = __fadd_rn(a, b);
+  e = __fsub_rn(b, __fsub_rn(s, a));
+}
+
+__device__ __forceinline__ void two_prod(float a, float b, float &p,
+                                         float &e) {
+  p = __fmul_rn(a, b);
+  e = __fmaf_rn(a, b, -p);
+}
+
+// Kahan-compensated FP32 accumulation
+struct Kahan {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    float y = __fsub_rn(x, c);
+    float t = __fadd_rn(s, y);
+    c = __fsub_rn(__fsub_rn(t, s), y);
+    s = t;
+  }
+  __device__ __forceinline__ double value() const {
+    return (double)s - (double)c;
+  }
+};
+
+// sin(pi x) for |x| <= ~0.55: x * p(x^2), p the degree-5 least-squares fit
+// of sin(pi x)/x in x^2 at 400 Chebyshev nodes of [0, 0.56] (max relative
+// error 1e-10 in exact arithmetic, ~2 ulp evaluated in FP32).
+__device__ __forceinline__ float sinpi_reduced(float x) {
+  float t = x * x;
+  float p = -6.941131045e-03f;
+  p = fmaf(p, t, 8.199509639e-02f);
+  p = fmaf(p, t, -5.992401060e-01f);
+  p = fmaf(p, t, 2.550162271e+00f);
+  p = fmaf(p, t, -5.167712735e+00f);
+  p = fmaf(p, t, 3.141592653e+00f);
+  return x * p;
+}
+
+// 4-point Lagrange weights for nodes -1, 0, 1, 2 at x in [0, 1]
+template <typename T>
+__device__ __forceinline__ void lagrange4(T x, T w[4]) {
+  T xm1 = x - T(1), xm2 = x - T(2), xp1 = x + T(1);
+  T a = x * xm1;      // x (x-1)
+  T b = xp1 * xm2;    // (x+1)(x-2)
+  w[0] = -a * xm2 * T(1.0 / 6.0);
+  w[1] = b * xm1 * T(0.5);
+  w[2] = -b * x * T(0.5);
+  w[3] = a * xp1 * T(1.0 / 6.0);
+}
+
+cudaError_t launch_spots_f64(const SpotArgs &a, cudaStream_t st);
+cudaError_t launch_spots_mixed(const SpotArgs &a, int precision,
+                               cudaStream_t st);
+
+}  // namespace nbgb

@@ -1,0 +1,179 @@
+// spots_f64.cu -- the plain FP64 form of the per-pixel Bragg-spot sum
+// (nanoBraggSpots, Sec. III-B), one thread per pixel, with the fused
+// double accumulate of addArray (Listing 1).
+//
+// Loop nest per pixel: subpixel x sensor layer -> source -> phi x mosaic.
+// Everything is FP64, evaluated in the order the definition is written
+// (this file is compiled without FMA contraction), so that the result
+// differs from any other faithful FP64 evaluation only by the rounding of
+// the transcendental functions.  Only loop invariants are hoisted (pixel
+// position, solid angle, capture fraction per subpixel/layer; scattering
+// vector and polarization per source).  The rotated axes and the source
+// table are staged in shared memory per block.
+#include "nbgb_internal.cuh"
+
+namespace nbgb {
+
+__device__ __forceinline__ double dot3d(const double *a, const double *b) {
+  return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+
+template <int SHAPE>
+__device__ __forceinline__ double flatt_f64(const SpotArgs &a,
+                                            const double h[3], double n[3]) {
+  double r = 1.0, rad2 = 0.0;
+#pragma unroll
+  for (int x = 0; x < 3; ++x) {
+    n[x] = ceil(h[x] - 0.5);  // nearest integer, ties down
+    double fr = h[x] - n[x];
+    if (SHAPE == 0) {
+      // sin(pi N h)/sin(pi h) = +-sin(pi N f)/sin(pi f); the sign drops out
+      r *= (fr == 0.0) ? a.N64[x]
+                       : sin(M_PI * a.N64[x] * fr) / sin(M_PI * fr);
+    } else {
+      rad2 += a.N64[x] * a.N64[x] * fr * fr;
+    }
+  }
+  if (SHAPE == 1) r = a.N64[0] * a.N64[1] * a.N64[2] * exp(-rad2 / 0.63);
+  return r;
+}
+
+__device__ __forceinline__ bool in_table(const SpotArgs &a, long long i,
+                                         long long j, long long k) {
+  return (unsigned long long)i < (unsigned long long)a.hn[0] &&
+         (unsigned long long)j < (unsigned long long)a.hn[1] &&
+         (unsigned long long)k < (unsigned long long)a.hn[2];
+}
+
+template <int INTERP>
+__device__ __forceinline__ double fcell_f64(const SpotArgs &a,
+                                            const double h[3],
+                                            const double n[3]) {
+  if (INTERP == 1) {
+    long long fl[3];
+    double x[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      double f = floor(h[c]);
+      fl[c] = (long long)f - a.hmin[c];
+      x[c] = h[c] - f;
+    }
+    if (in_table(a, fl[0] - 1, fl[1] - 1, fl[2] - 1) &&
+        in_table(a, fl[0] + 2, fl[1] + 2, fl[2] + 2)) {
+      // 4-point Lagrange weights on nodes -1, 0, 1, 2
+      double w[3][4];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        double t = x[c];
+        w[c][0] = -t * (t - 1.0) * (t - 2.0) / 6.0;
+        w[c][1] = (t + 1.0) * (t - 1.0) * (t - 2.0) / 2.0;
+        w[c][2] = -(t + 1.0) * t * (t - 2.0) / 2.0;
+        w[c][3] = (t + 1.0) * t * (t - 1.0) / 6.0;
+      }
+      double sum = 0.0;
+      for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) {
+          const float *row =
+              a.F + ((fl[0] - 1 + i) * a.hn[1] + (fl[1] - 1 + j)) * a.hn[2] +
+              (fl[2] - 1);
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+            sum += w[0][i] * w[1][j] * w[2][k] * (double)__ldg(row + k);
+        }
+      return sum;
+    }
+  }
+  long long i = (long long)n[0] - a.hmin[0], j = (long long)n[1] - a.hmin[1],
+            k = (long long)n[2] - a.hmin[2];
+  if (in_table(a, i, j, k))
+    return (double)__ldg(a.F + (i * a.hn[1] + j) * a.hn[2] + k);
+  return a.defF64;
+}
+
+template <int SHAPE, int INTERP>
+__global__ void __launch_bounds__(kTileThreads, 4)
+    spots_f64_kernel(SpotArgs a) {
+  extern __shared__ double sm[];
+  double *s_ax = sm;
+  double *s_src = sm + a.PM * 9;
+  for (int i = threadIdx.x; i < a.PM * 9; i += blockDim.x) s_ax[i] = a.ax64[i];
+  for (int i = threadIdx.x; i < a.S * SRC64_STRIDE; i += blockDim.x)
+    s_src[i] = a.src64[i];
+  __syncthreads();
+
+  long long item = a.pixlist ? (long long)blockIdx.x * blockDim.x + threadIdx.x
+                             : (long long)blockIdx.x;
+  long long gp;
+  int q, s, f;
+  if (!map_pixel(a, item, threadIdx.x, gp, q, s, f)) return;
+  const DevPanel &P = a.panels[q];
+  const double px = P.px;
+  const int os = a.os;
+  double acc = 0.0;
+  for (int i = 0; i < os; ++i) {
+    for (int j = 0; j < os; ++j) {
+      for (int t = 0; t < a.T; ++t) {
+        double cf = (f + (i + 0.5) / os) * px, cs = (s + (j + 0.5) / os) * px,
+               cn = t * a.dt;
+        double pos[3], d[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          pos[c] = P.origin[c] + cf * P.fdir[c] + cs * P.sdir[c] +
+                   cn * P.ndir[c];
+        double R = sqrt(dot3d(pos, pos));
+#pragma unroll
+        for (int c = 0; c < 3; ++c) d[c] = pos[c] / R;
+        double omega = px * px * dot3d(P.ndir, pos) / (R * R * R);
+        double cap = 1.0;
+        if (a.thickness > 0.0) {
+          double L = a.atten * dot3d(d, P.ndir);
+          cap = exp(-t * a.dt / L) - exp(-(t + 1) * a.dt / L);
+        }
+        for (int k = 0; k < a.S; ++k) {
+          const double *src = s_src + k * SRC64_STRIDE;
+          const double lam = src[SRC64_LAM];
+          const double *dir = src + SRC64_DIR;
+          double Sv[3];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) Sv[c] = (d[c] - dir[c]) / lam;
+          // Kahn: cos 2psi sin^2 2theta = (d.E')^2 - (d.B')^2 for unit d
+          double c2 = dot3d(d, dir), x = dot3d(d, src + SRC64_E),
+                 y = dot3d(d, src + SRC64_B);
+          double pol = 0.5 * (1.0 + c2 * c2 - a.kahn64 * (x * x - y * y));
+          double wfac = src[SRC64_W];
+          for (int pm = 0; pm < a.PM; ++pm) {
+            const double *A = s_ax + pm * 9;
+            double h[3] = {dot3d(A, Sv), dot3d(A + 3, Sv), dot3d(A + 6, Sv)};
+            double n[3];
+            double fl = flatt_f64<SHAPE>(a, h, n);
+            double fc = fcell_f64<INTERP>(a, h, n);
+            acc += fc * fc * fl * fl * wfac * cap * pol * omega;
+          }
+        }
+      }
+    }
+  }
+  a.image[gp] += a.prefactor * acc;
+}
+
+cudaError_t launch_spots_f64(const SpotArgs &a, cudaStream_t st) {
+  size_t smem = (size_t)(a.PM * 9 + a.S * SRC64_STRIDE) * sizeof(double);
+  long long blocks = a.pixlist ? (a.n_list + kTileThreads - 1) / kTileThreads
+                               : a.n_tiles;
+  if (blocks <= 0) return cudaSuccess;
+  void (*kern)(SpotArgs) = nullptr;
+  int key = a.shape * 2 + a.interp;
+  switch (key) {
+    case 0: kern = spots_f64_kernel<0, 0>; break;
+    case 1: kern = spots_f64_kernel<0, 1>; break;
+    case 2: kern = spots_f64_kernel<1, 0>; break;
+    default: kern = spots_f64_kernel<1, 1>; break;
+  }
+  cudaError_t e = cudaFuncSetAttribute(
+      kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<(unsigned)blocks, kTileThreads, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace nbgb

@@ -1,0 +1,53 @@
+"""Algorithmic work of the Bragg-spot sum, for the roofline figure.
+
+The count is the method's own arithmetic in FP32 flops (an FMA is 2), with
+the loop invariants hoisted as the definition allows, independent of how a
+kernel implements it (the double-float emulation of the fractional offset
+in NB_MIXED costs ~3x more instructions and is NOT counted):
+
+  per pixel-step (every step)
+    h_x = G_x u_k + r_x (one FMA per axis)                      6
+    f_x = h_x - rint(h_x)                                        3
+    Gaussian: sum_x (N_x f_x)^2                                  8
+    sinc:     per axis N f, reduction, sin(pi y) and sin(pi f)
+              as degree-11 odd polynomials (14 flops each);
+              the product and one division                     96
+  per evaluated term (Gaussian terms whose F_latt^2 underflows in FP32
+  are not evaluated; sinc terms always are)
+    Gaussian: exponent scale, exp, (Na Nb Nc)^2                  3
+    tricubic: 3 x 4 Lagrange weights (10 each) + 84 FMAs      198
+    term = F^2 F_latt^2 w and its accumulation                   4
+  per (subpixel, layer, phi x mosaic) item
+    G = A . (d - i0): 3 dot products, r = u0 G - n0            21
+  per (subpixel, layer) unit
+    position, |P|, d, solid angle, capture, polarization      60
+"""
+from __future__ import annotations
+
+STEP_HKL = 6 + 3
+STEP_GAUSS = 8
+STEP_SINC = 96
+TERM_GAUSS = 3
+TERM_TRICUBIC = 198
+TERM_ACCUM = 4
+ITEM = 21
+UNIT = 60
+
+
+def algorithmic_flops(shot, evaluated_terms: int, pixels: int = None) -> float:
+    """FP32 flops of one image of `shot` (or of `pixels` of its pixels),
+    given the number of evaluated terms reported by nb_get_stats."""
+    npix = shot.npix if pixels is None else pixels
+    units = npix * shot.oversample ** 2 * shot.n_layers
+    items = units * shot.n_mosaic * shot.n_phi
+    steps = items * shot.n_src
+    per_step = STEP_HKL + (STEP_GAUSS if shot.shape == 1 else STEP_SINC)
+    per_term = TERM_ACCUM + (TERM_GAUSS if shot.shape == 1 else 0) + (
+        TERM_TRICUBIC if shot.interp == 1 else 0)
+    return float(per_step * steps + per_term * evaluated_terms
+                 + ITEM * items + UNIT * units)
+
+
+def fp32_peak_tflops(sm_count: int = 152, mhz: float = 2070.0) -> float:
+    """FP32 FMA peak: SMs x 128 lanes x 2 flops x clock."""
+    return sm_count * 128 * 2 * mhz * 1e6 / 1e12

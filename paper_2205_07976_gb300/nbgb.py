@@ -1,0 +1,247 @@
+"""Thin ctypes binding of libnbgb (include/nbgb.h): argument marshalling
+only.  Every step of the Bragg-spot sum runs in the library's CUDA kernels;
+there is no CPU fallback, and loading fails loudly when the library (or a
+GPU) is missing.
+
+The functions keep the C names (``nb_sim_create``, ``nb_set_crystal`` ...);
+``Sim`` is a small convenience wrapper that feeds a ``workloads.Shot``
+through them.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+NB_OK, NB_EINVAL, NB_ENOMEM, NB_ECUDA, NB_ESTATE, NB_ETIMEOUT = (
+    0, -1, -2, -3, -4, -5)
+NB_F64, NB_MIXED, NB_F32 = 0, 1, 2
+NB_DTYPE_F32, NB_DTYPE_F64 = 0, 1
+PRECISIONS = {"f64": NB_F64, "mixed": NB_MIXED, "f32": NB_F32}
+
+_LOCK = threading.Lock()
+_LIB = None
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_fp = ctypes.POINTER(ctypes.c_float)
+_ip = ctypes.POINTER(ctypes.c_int)
+_llp = ctypes.POINTER(ctypes.c_longlong)
+_vp = ctypes.c_void_p
+
+
+class NbPanel(ctypes.Structure):
+    _fields_ = [("origin", ctypes.c_double * 3), ("fdir", ctypes.c_double * 3),
+                ("sdir", ctypes.c_double * 3), ("ndir", ctypes.c_double * 3),
+                ("pixel_m", ctypes.c_double), ("nfast", ctypes.c_int),
+                ("nslow", ctypes.c_int)]
+
+
+# name -> (restype, argtypes); every symbol declared in include/nbgb.h
+SIGNATURES = {
+    "nb_sim_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int,
+                                     ctypes.c_int, _vp]),
+    "nb_set_crystal": (ctypes.c_int, [
+        _vp, _dp, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+        ctypes.c_double, _dp, ctypes.c_double, ctypes.c_double,
+        ctypes.c_double, ctypes.c_int, _fp, _ip, _ip, ctypes.c_int,
+        ctypes.c_double]),
+    "nb_set_scale": (ctypes.c_int, [_vp, ctypes.c_double]),
+    "nb_set_beam": (ctypes.c_int, [_vp, _dp, _dp, _dp, ctypes.c_int,
+                                   ctypes.c_double, ctypes.c_double, _dp]),
+    "nb_set_detector": (ctypes.c_int, [_vp, ctypes.c_int,
+                                       ctypes.POINTER(NbPanel), ctypes.c_int,
+                                       ctypes.c_int, ctypes.c_double,
+                                       ctypes.c_double]),
+    "nb_num_pixels": (ctypes.c_longlong, [_vp]),
+    "nb_add_spots": (ctypes.c_int, [_vp]),
+    "nb_add_spots_pixels": (ctypes.c_int, [_vp, _llp, ctypes.c_longlong]),
+    "nb_zero_image": (ctypes.c_int, [_vp]),
+    "nb_get_image": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t, ctypes.c_int,
+                                    ctypes.c_int]),
+    "nb_image_device_ptr": (_vp, [_vp]),
+    "nb_get_stats": (ctypes.c_int, [_vp, _llp, _llp]),
+    "nb_synchronize": (ctypes.c_int, [_vp]),
+    "nb_free": (ctypes.c_int, [_vp]),
+    "nb_last_error": (ctypes.c_char_p, [_vp]),
+    "nb_version": (ctypes.c_char_p, []),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build: bool = True):
+    """Load libnbgb.so (building it first if asked); raises if missing."""
+    global _LIB
+    with _LOCK:
+        if _LIB is None:
+            path = _build.build() if build else _build.LIB
+            if not os.path.exists(path):
+                raise RuntimeError(f"libnbgb.so not found at {path}")
+            lib = ctypes.CDLL(path)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _LIB = lib
+    return _LIB
+
+
+class NbError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"nbgb error {code}: {msg}")
+        self.code = code
+
+
+def _check(rc, handle=None):
+    if rc != NB_OK:
+        msg = load().nb_last_error(handle).decode() if handle else ""
+        raise NbError(rc, msg)
+
+
+def _d(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def _ptr(a, t=_dp):
+    return a.ctypes.data_as(t)
+
+
+def panels_array(panels):
+    arr = (NbPanel * len(panels))()
+    for i, p in enumerate(panels):
+        arr[i].origin[:] = [float(v) for v in p.origin]
+        arr[i].fdir[:] = [float(v) for v in p.fdir]
+        arr[i].sdir[:] = [float(v) for v in p.sdir]
+        arr[i].ndir[:] = [float(v) for v in p.ndir]
+        arr[i].pixel_m = float(p.pixel_m)
+        arr[i].nfast = int(p.nfast)
+        arr[i].nslow = int(p.nslow)
+    return arr
+
+
+class Sim:
+    """One nb_sim handle.  `stream` is a torch.cuda.Stream, a raw
+    cudaStream_t (int) or None (legacy default stream)."""
+
+    def __init__(self, precision: str = "mixed", device: int = 0,
+                 stream=None):
+        self.lib = load()
+        h = _vp()
+        raw = 0
+        if stream is not None:
+            raw = int(getattr(stream, "cuda_stream", stream))
+        self.stream = stream
+        _check(self.lib.nb_sim_create(ctypes.byref(h), int(device),
+                                      PRECISIONS[precision], _vp(raw)))
+        self.h = h
+        self.precision = precision
+        self.npix = 0
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.nb_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- setters ---------------------------------------------------------
+    def set_crystal(self, shot, with_F: bool = True, axes=None):
+        axes = _d(shot.axes if axes is None else axes).ravel()
+        umats = _d(shot.umats).reshape(-1)
+        if with_F:
+            F = np.ascontiguousarray(shot.F, dtype=np.float32)
+            fptr = F.ctypes.data_as(_fp)
+        else:
+            F, fptr = None, None
+        hmin = (ctypes.c_int * 3)(*[int(v) for v in shot.hkl_min])
+        hn = (ctypes.c_int * 3)(*[int(v) for v in shot.F.shape])
+        sp = _d(shot.spindle)
+        N = [float(v) for v in shot.ncells]
+        _check(self.lib.nb_set_crystal(
+            self.h, _ptr(axes), _ptr(umats), int(shot.umats.shape[0]),
+            int(shot.n_phi), float(shot.phi0_deg), float(shot.phistep_deg),
+            _ptr(sp), N[0], N[1], N[2], int(shot.shape), fptr,
+            ctypes.cast(hmin, _ip), ctypes.cast(hn, _ip), int(shot.interp),
+            float(shot.default_F)), self.h)
+        _check(self.lib.nb_set_scale(self.h, float(shot.scale)), self.h)
+
+    def set_beam(self, shot):
+        dirs, lam, w, e = (_d(shot.dirs).ravel(), _d(shot.lambdas),
+                           _d(shot.weights), _d(shot.evec))
+        _check(self.lib.nb_set_beam(self.h, _ptr(dirs), _ptr(lam), _ptr(w),
+                                    int(lam.shape[0]), float(shot.fluence),
+                                    float(shot.kahn), _ptr(e)), self.h)
+
+    def set_detector(self, shot):
+        arr = panels_array(shot.panels)
+        _check(self.lib.nb_set_detector(
+            self.h, len(shot.panels), arr, int(shot.oversample),
+            int(shot.n_layers), float(shot.thickness_m),
+            float(shot.atten_m)), self.h)
+        self.npix = int(self.lib.nb_num_pixels(self.h))
+
+    def set_shot(self, shot):
+        self.set_crystal(shot)
+        self.set_beam(shot)
+        self.set_detector(shot)
+        return self
+
+    # -- work --------------------------------------------------------------
+    def add_spots(self, pixels=None):
+        if pixels is None:
+            _check(self.lib.nb_add_spots(self.h), self.h)
+        else:
+            pix = np.ascontiguousarray(np.asarray(pixels, dtype=np.int64))
+            _check(self.lib.nb_add_spots_pixels(self.h, _ptr(pix, _llp),
+                                                pix.shape[0]), self.h)
+
+    def zero(self):
+        _check(self.lib.nb_zero_image(self.h), self.h)
+
+    def stats(self):
+        """(evaluated_terms, pixel_steps) of the last add_spots call."""
+        ev, ps = ctypes.c_longlong(), ctypes.c_longlong()
+        _check(self.lib.nb_get_stats(self.h, ctypes.byref(ev),
+                                     ctypes.byref(ps)), self.h)
+        return int(ev.value), int(ps.value)
+
+    def synchronize(self):
+        _check(self.lib.nb_synchronize(self.h), self.h)
+
+    def image(self, dtype=np.float64) -> np.ndarray:
+        out = np.empty(self.npix, dtype=dtype)
+        code = NB_DTYPE_F64 if out.dtype == np.float64 else NB_DTYPE_F32
+        _check(self.lib.nb_get_image(self.h, out.ctypes.data_as(_vp),
+                                     out.shape[0], code, 0), self.h)
+        return out
+
+    def image_to_device(self, dst_ptr: int, n: int, dtype_code: int):
+        _check(self.lib.nb_get_image(self.h, _vp(dst_ptr), n, dtype_code, 1),
+               self.h)
+
+    def image_device_ptr(self) -> int:
+        return int(self.lib.nb_image_device_ptr(self.h) or 0)
+
+
+def simulate(shot, precision: str = "mixed", pixels=None,
+             device: int = 0) -> np.ndarray:
+    """Image of `shot` (all pixels, or the listed ones in list order)."""
+    sim = Sim(precision, device).set_shot(shot)
+    try:
+        sim.add_spots(pixels)
+        img = sim.image()
+        if pixels is not None:
+            return img[np.asarray(pixels, dtype=np.int64)]
+        return img
+    finally:
+        sim.close()

@@ -1,0 +1,238 @@
+"""GPU images vs the FP64 CPU oracle, element by element, through the C ABI.
+
+Tolerances (max relative error per pixel):
+  NB_F64    1e-12 on pixels above 1e-6 of the image maximum, and 1e-12 of
+            the maximum in absolute terms everywhere;
+  NB_MIXED  1e-5 on pixels above 1e-3 of the image maximum;
+  NB_F32    reported only (the precision sweep's naive arm).
+Windows are chosen with odd sizes so that every launch has ragged 16x8
+tiles at its right and bottom edges.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2205_07976_gb300 import nbgb
+from paper_2205_07976_gb300 import workloads as W
+from tests.helpers import abs_err_frac, masked_rel_err
+
+pytestmark = pytest.mark.gpu
+
+F64_TOL = 1e-12
+MIXED_TOL = 1e-5
+
+
+def check_f64(got, ref):
+    rel, n = masked_rel_err(got, ref, 1e-6)
+    assert rel <= F64_TOL, (rel, n)
+    assert abs_err_frac(got, ref) <= F64_TOL
+
+
+def check_mixed(got, ref, tol=MIXED_TOL):
+    rel, n = masked_rel_err(got, ref, 1e-3)
+    assert rel <= tol, (rel, n)
+    assert abs_err_frac(got, ref) <= tol
+
+
+def run(shot, precision, pixels=None):
+    return nbgb.simulate(shot, precision, pixels)
+
+
+# ------------------------------------------------------ single shot (c0)
+
+
+@pytest.fixture(scope="module")
+def c0():
+    s = W.single_shot_small()
+    return s, oracle.image(s)
+
+
+def test_single_shot_f64(c0):
+    s, ref = c0
+    check_f64(run(s, "f64"), ref)
+
+
+def test_single_shot_mixed(c0):
+    s, ref = c0
+    check_mixed(run(s, "mixed"), ref)
+
+
+def test_single_shot_f32_is_finite_and_close(c0):
+    s, ref = c0
+    got = run(s, "f32")
+    assert np.isfinite(got).all()
+    rel, _ = masked_rel_err(got, ref, 1e-3)
+    assert rel < 0.5  # N = 10, |h| <= 11: plain FP32 is still roughly right
+
+
+# ---------------------------------------------- large shot windows (c1)
+
+
+@pytest.fixture(scope="module", params=[(2500, 700, 37, 29),
+                                        (1600, 1500, 33, 19)])
+def c1win(request):
+    f0, s0, nf, ns = request.param
+    s = W.shrink(W.large_shot(), nf, ns, f0, s0)
+    return s, oracle.image(s)
+
+
+def test_large_shot_window_f64(c1win):
+    s, ref = c1win
+    check_f64(run(s, "f64"), ref)
+
+
+def test_large_shot_window_mixed(c1win):
+    s, ref = c1win
+    check_mixed(run(s, "mixed"), ref)
+
+
+# ---------------------------------------------- precision sweep (c2)
+
+
+@pytest.mark.parametrize("N", [10, 50, 200])
+def test_precision_window(N):
+    s = W.shrink(W.precision_shot(N), 45, 35, 600, 640)
+    ref = oracle.image(s)
+    f64 = run(s, "f64")
+    rel, _ = masked_rel_err(f64, ref, 1e-6)
+    # the sinc's phase pi N f carries the FP64 rounding of h times N
+    assert rel <= (F64_TOL if N <= 50 else 1e-10), rel
+    check_mixed(run(s, "mixed"), ref)
+    assert np.isfinite(run(s, "f32")).all()
+
+
+# ---------------------------------------------- multi-panel (c3 forward)
+
+
+@pytest.mark.parametrize("n_src", [1, 8])
+def test_multipanel_full_detector(n_src):
+    s = W.multipanel_shot(n_src)
+    ref = oracle.image(s)
+    check_f64(run(s, "f64"), ref)
+    check_mixed(run(s, "mixed"), ref)
+
+
+# ---------------------------------------------- paths and edge cases
+
+
+def test_pixel_list_path_matches_oracle():
+    s = W.large_shot()
+    pix = np.concatenate([W.sample_pixels(s, 3, 7, 11),
+                          np.arange(700 * 3072 + 2500, 700 * 3072 + 2537)])
+    ref = oracle.image(s, pix)
+    for prec, chk in (("f64", check_f64), ("mixed", check_mixed)):
+        sim = nbgb.Sim(prec).set_shot(s)
+        sim.add_spots(pix)
+        img = sim.image()
+        chk(img[pix], ref)
+        # untouched pixels stay exactly zero
+        mask = np.ones(sim.npix, dtype=bool)
+        mask[pix] = False
+        assert not img[mask].any()
+        sim.close()
+
+
+def test_accumulate_is_the_fused_addarray():
+    s = W.shrink(W.single_shot_small(), 21, 13, 150, 140)
+    for prec in ("f64", "mixed"):
+        sim = nbgb.Sim(prec).set_shot(s)
+        sim.add_spots()
+        one = sim.image()
+        sim.add_spots()
+        two = sim.image()
+        # lhs += (double) rhs twice: exactly twice the first image
+        assert np.array_equal(two, 2.0 * one)
+        sim.zero()
+        assert not sim.image().any()
+        f32 = sim.image(np.float32)
+        assert f32.dtype == np.float32 and not f32.any()
+        sim.close()
+
+
+def _edge_shot(seed=4):
+    """Small shot with divergent sources, three phi steps about a tilted
+    spindle, two sensor layers, oversample 3, Kahn 0.7 and a small F table
+    (|h| exceeds it) with a non-zero default_F."""
+    rng = np.random.default_rng(seed)
+    U = W.random_orientation(rng)
+    dirs = np.array([[0.0, 0.0, 1.0], [1e-3, 0.0, 1.0], [0.0, -2e-3, 1.0]])
+    dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+    s = W._base_shot(
+        axes=W.orthorhombic_axes(79.0, 79.0, 38.0, U),
+        umats=W.mosaic_umats(rng, 4, 0.1), n_phi=3, phi0_deg=0.5,
+        phistep_deg=0.05, spindle=np.array([0.2, 1.0, 0.1]),
+        ncells=np.array([12.0, 9.0, 7.0]), shape=W.SHAPE_GAUSS,
+        F=W.structure_factors(rng, 6), hkl_min=np.array([-6, -6, -6],
+                                                         dtype=np.int32),
+        interp=W.INTERP_TRICUBIC, default_F=35.0, dirs=dirs,
+        lambdas=np.array([1.2, 1.21, 1.19]), weights=np.array([.5, .3, .2]),
+        kahn=0.7, evec=np.array([1.0, 0.2, 0.0]),
+        panels=[W.flat_detector(29, 23, 1.5e-4, 0.08,
+                                beam_center=(-60.0, -40.0))],
+        oversample=3, n_layers=2, thickness_m=3e-4, atten_m=2e-4)
+    return s
+
+
+@pytest.mark.parametrize("shape,interp", [(0, 0), (0, 1), (1, 0), (1, 1)])
+def test_edge_case_shot(shape, interp):
+    s = _edge_shot()
+    s.shape, s.interp = shape, interp
+    if shape == 0:
+        s.ncells = np.array([12.0, 9.0, 7.0])
+    ref = oracle.image(s)
+    check_f64(run(s, "f64"), ref)
+    check_mixed(run(s, "mixed"), ref)
+
+
+def test_single_pixel_and_empty_list():
+    s = W.shrink(W.single_shot_small(), 1, 1, 200, 170)
+    ref = oracle.image(s)
+    check_f64(run(s, "f64"), ref) if ref.max() > 0 else None
+    sim = nbgb.Sim("mixed").set_shot(s)
+    sim.add_spots(np.zeros(0, dtype=np.int64))
+    assert not sim.image().any()
+    sim.close()
+
+
+def test_bad_arguments_are_rejected():
+    s = W.single_shot_small()
+    sim = nbgb.Sim("mixed")
+    with pytest.raises(nbgb.NbError) as e:
+        sim.add_spots()
+    assert e.value.code == nbgb.NB_ESTATE
+    sim.set_shot(s)
+    with pytest.raises(nbgb.NbError) as e:
+        sim.add_spots([sim.npix])
+    assert e.value.code == nbgb.NB_EINVAL
+    bad = s.copy()
+    bad.ncells = np.array([10.5, 10.0, 10.0])
+    with pytest.raises(nbgb.NbError) as e:
+        sim.set_crystal(bad)
+    assert e.value.code == nbgb.NB_EINVAL
+    bad = s.copy()
+    bad.lambdas = np.array([-1.0])
+    with pytest.raises(nbgb.NbError):
+        sim.set_beam(bad)
+    bad = s.copy()
+    bad.n_layers = 2
+    with pytest.raises(nbgb.NbError):
+        sim.set_detector(bad)
+    assert sim.lib.nb_get_image(sim.h, None, sim.npix, 1, 0) == nbgb.NB_EINVAL
+    out = np.empty(3)
+    assert sim.lib.nb_get_image(sim.h, out.ctypes.data_as(nbgb._vp), 3, 1,
+                                0) == nbgb.NB_EINVAL
+    sim.close()
+
+
+# ------------------------------------- full-size large shot, sampled rows
+
+
+def test_large_shot_full_size_sampled_rows():
+    """The whole 3072x3072 image in the launch configuration the benchmark
+    times; the oracle computes three full rows (9216 pixels) of it."""
+    s = W.large_shot()
+    rows = [700, 1500, 2417]
+    pix = np.concatenate([np.arange(r * 3072, (r + 1) * 3072) for r in rows])
+    ref = oracle.image(s, pix)
+    got = run(s, "mixed")[pix]
+    check_mixed(got, ref)
