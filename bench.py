@@ -54,6 +54,11 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--f64-rows-every", type=int, default=96)
+    ap.add_argument("--window", type=int, default=0,
+                    help="time an N x N window of the large shot instead "
+                         "of the whole image (for profiling)")
+    ap.add_argument("--legs", default="main,e2e,f64,cpu",
+                    help="comma list of main, e2e, f64, cpu")
     return ap.parse_args()
 
 
@@ -179,7 +184,10 @@ def run_ours(args):
     world, rank, local, pg = dist_setup(args)
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    legs = set(args.legs.split(","))
     shot = W.large_shot(seed=1 + rank)
+    if args.window:
+        shot = W.shrink(shot, args.window, args.window, 1024, 1024)
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32,
                         device=dev)
@@ -228,47 +236,12 @@ def run_ours(args):
     value = units / t_step
     clocks = clk.summary()
 
-    # end to end through the C ABI with host buffers
-    img_host = torch.empty(shot.npix, dtype=torch.float32).pin_memory()
-    F_host = torch.from_numpy(np.ascontiguousarray(shot.F)).pin_memory()
-
-    def step_e2e():
-        s2 = shot.copy()
-        s2.F = F_host.numpy()
-        sim.set_crystal(s2, with_F=True)
-        sim.set_beam(s2)
-        sim.set_detector(s2)
-        sim.add_spots()
-        code = nbgb.NB_DTYPE_F32
-        nbgb._check(sim.lib.nb_get_image(sim.h, nbgb._vp(img_host.data_ptr()),
-                                         shot.npix, code, 0), sim.h)
-
-    step_e2e()
-    torch.cuda.synchronize()
-    barrier(pg)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        step_e2e()
-    torch.cuda.synchronize()
-    barrier(pg)
-    t_e2e = max_over_ranks(pg, (time.perf_counter() - t0) / args.steps)
-    h2d = (shot.F.nbytes + shot.umats.nbytes + shot.axes.nbytes
-           + shot.dirs.nbytes + shot.lambdas.nbytes + shot.weights.nbytes)
-    d2h = shot.npix * 4
-
-    # plain FP64 form on a strided pixel subset of the same shot
-    rows = W.strided_rows(shot, args.f64_rows_every)
-    sim64 = nbgb.Sim("f64", device=local, stream=stream).set_shot(shot)
-    sim64.add_spots(rows)
-    stream.synchronize()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    sim64.add_spots(rows)
-    ev1.record(stream)
-    stream.synchronize()
-    t64 = ev0.elapsed_time(ev1) / 1e3
-    f64_rate = len(rows) * shot.steps_per_pixel / t64
+    e2e = None
+    if "e2e" in legs:
+        e2e = run_e2e(args, sim, shot, world, pg, torch, np, nbgb)
+    f64 = None
+    if "f64" in legs:
+        f64 = run_f64(args, shot, local, stream, torch, nbgb, W)
 
     if rank != 0:
         return
@@ -291,11 +264,8 @@ def run_ours(args):
                    "pixel_steps_per_image": shot.pixel_steps,
                    "precision": "FP32-mixed", "parallelism": "replicas",
                    "l2": "512 MB buffer rewritten between timed steps"},
-        "e2e": {"value": shot.pixel_steps * world / t_e2e, "unit": UNIT,
-                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": d2h},
-        "f64": {"value": f64_rate, "unit": UNIT,
-                "sample": f"every {args.f64_rows_every}th row "
-                          f"({len(rows)} pixels)", "ms": t64 * 1e3},
+        "e2e": e2e,
+        "f64": f64,
         "gpu_launches": args.steps,
         "roofline": {"bound": "alu", "achieved": achieved,
                      "peak": peak_fp32, "unit": "TFLOP/s",
@@ -311,9 +281,65 @@ def run_ours(args):
                          if sm_mhz else None)},
         "clocks": clocks,
     }
-    if world == 1 and not args.no_cpu_baseline:
+    if args.window:
+        line["config"]["window"] = f"{args.window}x{args.window} pixels"
+    if world == 1 and not args.no_cpu_baseline and "cpu" in legs:
         line["cpu_baseline"] = cpu_baseline(shot, 192)
     print(json.dumps(line), flush=True)
+
+
+def run_e2e(args, sim, shot, world, pg, torch, np, nbgb):
+    """The same metric end to end through the C ABI with host buffers: the
+    shot's inputs (F table from pinned memory, crystal, beam, detector)
+    copied in and the float image copied out every step."""
+    img_host = torch.empty(shot.npix, dtype=torch.float32).pin_memory()
+    F_host = torch.from_numpy(np.ascontiguousarray(shot.F)).pin_memory()
+    s2 = shot.copy()
+    s2.F = F_host.numpy()
+
+    def step_e2e():
+        sim.set_crystal(s2, with_F=True)
+        sim.set_beam(s2)
+        sim.set_detector(s2)
+        sim.add_spots()
+        nbgb._check(sim.lib.nb_get_image(sim.h, nbgb._vp(img_host.data_ptr()),
+                                         shot.npix, nbgb.NB_DTYPE_F32, 0),
+                    sim.h)
+
+    step_e2e()
+    torch.cuda.synchronize()
+    barrier(pg)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step_e2e()
+    torch.cuda.synchronize()
+    barrier(pg)
+    t_e2e = max_over_ranks(pg, (time.perf_counter() - t0) / args.steps)
+    h2d = (shot.F.nbytes + shot.umats.nbytes + shot.axes.nbytes
+           + shot.dirs.nbytes + shot.lambdas.nbytes + shot.weights.nbytes)
+    return {"value": shot.pixel_steps * world / t_e2e, "unit": UNIT,
+            "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(shot.npix * 4),
+            "ms_per_step": t_e2e * 1e3}
+
+
+def run_f64(args, shot, local, stream, torch, nbgb, W):
+    """The plain FP64 form on every n-th row of the same shot."""
+    rows = W.strided_rows(shot, args.f64_rows_every)
+    sim64 = nbgb.Sim("f64", device=local, stream=stream).set_shot(shot)
+    sim64.add_spots(rows)
+    stream.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    sim64.add_spots(rows)
+    ev1.record(stream)
+    stream.synchronize()
+    t64 = ev0.elapsed_time(ev1) / 1e3
+    sim64.close()
+    return {"value": len(rows) * shot.steps_per_pixel / t64, "unit": UNIT,
+            "sample": f"every {args.f64_rows_every}th row "
+                      f"({len(rows)} pixels)", "ms": t64 * 1e3}
 
 
 # ------------------------------------------------------- reference arm

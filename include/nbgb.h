@@ -173,6 +173,21 @@ const double *nb_image_device_ptr(const nb_sim *sim);
 int nb_get_stats(nb_sim *sim, long long *evaluated_terms,
                  long long *pixel_steps);
 
+/* Tuning options (nb_set_option keys). */
+enum {
+    /* kernel variant of NB_MIXED: NB_VARIANT_AUTO (default: one warp per
+     * pixel for Gaussian shapes with tricubic lookup, <= 32 subpixel x layer
+     * units and >= 16 (unit, phi x mosaic) items per pixel, else one thread
+     * per pixel), NB_VARIANT_THREAD, NB_VARIANT_WARP (Gaussian shapes with
+     * <= 32 units only; falls back to NB_VARIANT_THREAD otherwise) */
+    NB_OPT_VARIANT = 1
+};
+enum { NB_VARIANT_AUTO = 0, NB_VARIANT_THREAD = 1, NB_VARIANT_WARP = 2 };
+
+/* Set a tuning option; results agree across variants within the precision's
+ * tolerance.  Errors: NB_EINVAL for an unknown key or value. */
+int nb_set_option(nb_sim *sim, int key, long long value);
+
 /* Wait for the handle's queued work. */
 int nb_synchronize(nb_sim *sim);
 

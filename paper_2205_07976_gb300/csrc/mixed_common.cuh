@@ -1,0 +1,106 @@
+// mixed_common.cuh -- device helpers shared by the FP32-bulk kernels:
+// the double-float dot product, the double-float fractional offset, and
+// the FP32 structure-factor lookup (nearest / tricubic).
+#pragma once
+
+#include "nbgb_internal.cuh"
+
+namespace nbgb {
+
+__device__ __forceinline__ double dot3d_m(const double *a, const double *b) {
+  return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+
+// double-float dot product of A (hi, lo) with v (hi, lo)
+__device__ __forceinline__ void ff_dot3(const float *Ah, const float *Al,
+                                        const float *vh, const float *vl,
+                                        float &gh, float &gl) {
+  float p0, e0, p1, e1, p2, e2;
+  two_prod(Ah[0], vh[0], p0, e0);
+  two_prod(Ah[1], vh[1], p1, e1);
+  two_prod(Ah[2], vh[2], p2, e2);
+  float s, t, s2, t2;
+  two_sum(p0, p1, s, t);
+  two_sum(s, p2, s2, t2);
+  float lo = e0 + e1 + e2 + t + t2;
+  lo = fmaf(Ah[0], vl[0], lo);
+  lo = fmaf(Ah[1], vl[1], lo);
+  lo = fmaf(Ah[2], vl[2], lo);
+  lo = fmaf(Al[0], vh[0], lo);
+  lo = fmaf(Al[1], vh[1], lo);
+  lo = fmaf(Al[2], vh[2], lo);
+  fast_two_sum(s2, lo, gh, gl);
+}
+
+// fractional offset of h = G (u0 + delta) - E relative to its nearest
+// integer, given r = G u0 - n0 (double-float).  Returns f = fh + fl and the
+// integer shift nf (h = n0 + nf + f).
+template <int HASDIV>
+__device__ __forceinline__ void frac_ff(float Gh, float Gl, float rh, float rl,
+                                        float dh, float dl, float Eh, float El,
+                                        float &fh, float &fl, float &nf) {
+  float p, pe, t, te;
+  two_prod(Gh, dh, p, pe);
+  two_sum(p, rh, t, te);
+  float lo = pe + te + rl;
+  if (HASDIV) {
+    float t3, te3;
+    two_sum(t, -Eh, t3, te3);
+    t = t3;
+    lo = lo + te3 - El;
+  }
+  lo = fmaf(Gh, dl, lo);
+  lo = fmaf(Gl, dh, lo);
+  nf = rintf(t);
+  float t2 = __fsub_rn(t, nf);  // exact
+  fh = __fadd_rn(t2, lo);
+  fl = __fsub_rn(lo, __fsub_rn(fh, t2));
+}
+
+template <int INTERP>
+__device__ __forceinline__ float fcell_f32(const SpotArgs &a, const int n[3],
+                                           const float fr[3]) {
+  if (INTERP == 1) {
+    int fl[3];
+    float x[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      int neg = fr[c] < 0.f;
+      fl[c] = n[c] - neg;
+      x[c] = neg ? 1.f + fr[c] : fr[c];
+    }
+    // the 4x4x4 stencil fl-1 .. fl+2 must lie inside the table
+    if (fl[0] >= 1 && fl[0] + 2 < a.hn[0] && fl[1] >= 1 &&
+        fl[1] + 2 < a.hn[1] && fl[2] >= 1 && fl[2] + 2 < a.hn[2]) {
+      float wh[4], wk[4], wl[4];
+      lagrange4(x[0], wh);
+      lagrange4(x[1], wk);
+      lagrange4(x[2], wl);
+      const float *base =
+          a.F + ((long long)(fl[0] - 1) * a.hn[1] + (fl[1] - 1)) * a.hn[2] +
+          (fl[2] - 1);
+      float sum = 0.f;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        float si = 0.f;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const float *row = base + ((long long)i * a.hn[1] + j) * a.hn[2];
+          float sj = wl[0] * __ldg(row);
+          sj = fmaf(wl[1], __ldg(row + 1), sj);
+          sj = fmaf(wl[2], __ldg(row + 2), sj);
+          sj = fmaf(wl[3], __ldg(row + 3), sj);
+          si = fmaf(wk[j], sj, si);
+        }
+        sum = fmaf(wh[i], si, sum);
+      }
+      return sum;
+    }
+  }
+  if ((unsigned)n[0] < (unsigned)a.hn[0] && (unsigned)n[1] < (unsigned)a.hn[1] &&
+      (unsigned)n[2] < (unsigned)a.hn[2])
+    return __ldg(a.F + ((long long)n[0] * a.hn[1] + n[1]) * a.hn[2] + n[2]);
+  return a.defF;
+}
+
+}  // namespace nbgb

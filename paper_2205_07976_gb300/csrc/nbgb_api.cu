@@ -84,7 +84,9 @@ struct nb_sim {
   double thick = 0, atten = 0;
   // device
   DevBuf d_panels, d_ax64, d_axh, d_axl, d_src64, d_src32, d_divh, d_divl,
-      d_F, d_image, d_list, d_tmp, d_stats;
+      d_F, d_image, d_list, d_tmp, d_stats, d_work;
+  int variant = NB_VARIANT_AUTO;
+  int sm_count = 0;
   long long last_pixel_steps = 0;
   int has_div = 0;
   double u0 = 0;
@@ -343,6 +345,12 @@ int nb_sim_create(nb_sim **out, int device, int precision,
   if (!s) return NB_ENOMEM;
   s->device = device;
   s->precision = precision;
+  if (cudaDeviceGetAttribute(&s->sm_count, cudaDevAttrMultiProcessorCount,
+                             device) != cudaSuccess) {
+    cudaGetLastError();
+    delete s;
+    return NB_ECUDA;
+  }
   s->stream = (cudaStream_t)cuda_stream;
   *out = s;
   return NB_OK;
@@ -357,7 +365,7 @@ int nb_free(nb_sim *sim) {
                       &sim->d_axl,    &sim->d_src64, &sim->d_src32,
                       &sim->d_divh,   &sim->d_divl,  &sim->d_F,
                       &sim->d_image,  &sim->d_list,  &sim->d_tmp,
-                      &sim->d_stats};
+                      &sim->d_stats,  &sim->d_work};
     for (DevBuf *b : bufs) b->release();
   }
   delete sim;
@@ -576,9 +584,27 @@ static int launch(nb_sim *s, const long long *dev_list, long long n_list) {
   long long pix = dev_list ? n_list : s->npix;
   s->last_pixel_steps = pix * (long long)s->os * s->os * s->T * s->n_src *
                         s->n_mosaic * s->n_phi;
-  e = s->precision == NB_F64
-          ? nbgb::launch_spots_f64(a, s->stream)
-          : nbgb::launch_spots_mixed(a, s->precision, s->stream);
+  // one warp per pixel pays off where the scattered terms are expensive
+  // (tricubic lookups) and a pixel has enough items to fill the lanes
+  bool auto_warp = a.interp == NB_INTERP_TRICUBIC &&
+                   (long long)a.os * a.os * a.T * a.PM >= 16;
+  bool warp_variant =
+      s->precision == NB_MIXED && nbgb::split_supported(a) &&
+      (s->variant == NB_VARIANT_WARP ||
+       (s->variant == NB_VARIANT_AUTO && auto_warp));
+  if (s->precision == NB_F64) {
+    e = nbgb::launch_spots_f64(a, s->stream);
+  } else if (warp_variant) {
+    e = s->d_work.ensure(sizeof(unsigned long long));
+    if (e != cudaSuccess) return fail(s, NB_ENOMEM, "work counter");
+    e = cudaMemsetAsync(s->d_work.p, 0, sizeof(unsigned long long),
+                        s->stream);
+    if (e == cudaSuccess)
+      e = nbgb::launch_spots_split(a, (unsigned long long *)s->d_work.p,
+                                   s->sm_count, s->stream);
+  } else {
+    e = nbgb::launch_spots_mixed(a, s->precision, s->stream);
+  }
   if (e != cudaSuccess) return cuda_fail(s, e, "spots launch");
   return NB_OK;
 }
@@ -667,6 +693,17 @@ int nb_get_image(nb_sim *s, void *dst, size_t n_elems, int dtype,
 
 const double *nb_image_device_ptr(const nb_sim *s) {
   return (s && s->have_det) ? (const double *)s->d_image.p : nullptr;
+}
+
+int nb_set_option(nb_sim *s, int key, long long value) {
+  if (!s) return NB_EINVAL;
+  if (key == NB_OPT_VARIANT) {
+    if (value < NB_VARIANT_AUTO || value > NB_VARIANT_WARP)
+      return fail(s, NB_EINVAL, "bad variant");
+    s->variant = (int)value;
+    return NB_OK;
+  }
+  return fail(s, NB_EINVAL, "unknown option");
 }
 
 int nb_get_stats(nb_sim *s, long long *evaluated_terms,

@@ -210,6 +210,10 @@ __device__ __forceinline__ void lagrange4(T x, T w[4]) {
 }
 
 cudaError_t launch_spots_f64(const SpotArgs &a, cudaStream_t st);
+size_t split_smem_bytes(const SpotArgs &a);
+bool split_supported(const SpotArgs &a);
+cudaError_t launch_spots_split(const SpotArgs &a, unsigned long long *work,
+                               int sm_count, cudaStream_t st);
 cudaError_t launch_spots_mixed(const SpotArgs &a, int precision,
                                cudaStream_t st);
 

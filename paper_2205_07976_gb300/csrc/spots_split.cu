@@ -1,0 +1,273 @@
+// spots_split.cu -- the FP32-mixed Bragg-spot sum for Gaussian lattice
+// shapes, one warp per pixel (the per-pixel step reduction of Sec. III-B's
+// nanoBraggSpots, split across lanes, with the fused addArray accumulate).
+//
+// Why a second variant: with a Gaussian F_latt only a few percent of the
+// (subpixel, layer, phi x mosaic, source) steps of a pixel carry a term that
+// does not underflow in FP32, and each such term needs the structure factor
+// (64 gathers for tricubic interpolation).  With one thread per pixel those
+// terms are scattered over lanes and a warp serialises them.  Here:
+//   1. lanes 0..U-1 set up the U = os^2 x layers sub-pixel units of the
+//      pixel in FP64 (position, direction, solid angle, capture,
+//      polarization) into shared memory;
+//   2. lanes take (unit, phi x mosaic) items round-robin, form G and r in
+//      double-float, and scan all sources with a 7-flop-per-axis fractional
+//      offset; a step whose exponent sum N^2 f^2 / 0.63 stays below the
+//      underflow cut is pushed into a per-warp ring in shared memory;
+//   3. whenever the ring holds 32 terms, every lane evaluates one of them
+//      (exp, F_cell lookup, product) into its own Kahan sum;
+//   4. the 32 lane sums are reduced with warp shuffles in FP64.
+// The order of every operation depends only on the pixel's own inputs, so
+// a pixel's value does not depend on what else is in the launch.
+// Pixels are handed to warps through an atomic counter in a scratch word.
+#include "mixed_common.cuh"
+
+namespace nbgb {
+
+constexpr int kSplitWarps = 4;
+constexpr int kSplitThreads = kSplitWarps * 32;
+constexpr int kRing = 64;
+constexpr int kMaxUnits = 32;
+constexpr int kUnitFloats = 10;  // vh[3], vl[3], scal, df[3]
+
+struct SplitRing {
+  float f[3][kRing];
+  int n[3][kRing];
+  float w[kRing];
+};
+
+template <int INTERP>
+__device__ __forceinline__ void eval_term(const SpotArgs &a,
+                                          const SplitRing &q, int e,
+                                          Kahan &acc) {
+  float fr[3] = {q.f[0][e], q.f[1][e], q.f[2][e]};
+  int n[3] = {q.n[0][e], q.n[1][e], q.n[2][e]};
+  float rad2 = a.N[0] * a.N[0] * fr[0] * fr[0];
+  rad2 = fmaf(a.N[1] * a.N[1], fr[1] * fr[1], rad2);
+  rad2 = fmaf(a.N[2] * a.N[2], fr[2] * fr[2], rad2);
+  float fl2 = a.N6 * expf(-2.f * rad2 * (1.f / 0.63f));
+  float fc = fcell_f32<INTERP>(a, n, fr);
+  acc.add(fc * fc * fl2 * q.w[e]);
+}
+
+template <int INTERP, int HASDIV>
+__global__ void __launch_bounds__(kSplitThreads, 6)
+    spots_split_kernel(SpotArgs a, unsigned long long *work) {
+  extern __shared__ float sms[];
+  const int PM = a.PM, S = a.S;
+  float *s_axh = sms;
+  float *s_axl = s_axh + PM * 9;
+  float *s_src = s_axl + PM * 9;
+  float *s_unit = s_src + S * SRC32_STRIDE;  // [warp][unit][kUnitFloats]
+  SplitRing *rings =
+      reinterpret_cast<SplitRing *>(s_unit + kSplitWarps * kMaxUnits *
+                                                 kUnitFloats);
+  for (int i = threadIdx.x; i < PM * 9; i += blockDim.x) {
+    s_axh[i] = a.axh[i];
+    s_axl[i] = a.axl[i];
+  }
+  for (int i = threadIdx.x; i < S * SRC32_STRIDE; i += blockDim.x)
+    s_src[i] = a.src32[i];
+  __syncthreads();
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float *unit = s_unit + warp * kMaxUnits * kUnitFloats;
+  SplitRing &q = rings[warp];
+  const unsigned lt_mask = (1u << lane) - 1u;
+  const int os = a.os, U = a.os * a.os * a.T, items = U * PM;
+  const float cutg = kGaussCut * 0.63f;
+  const float kahn = a.kahn;
+  const float N2[3] = {a.N[0] * a.N[0], a.N[1] * a.N[1], a.N[2] * a.N[2]};
+  const long long n_work = a.pixlist ? a.n_list : a.npix;
+  unsigned long long evals = 0;  // terms evaluated by this warp
+
+  while (true) {
+    long long item_pix = 0;
+    if (lane == 0) item_pix = (long long)atomicAdd(work, 1ULL);
+    item_pix = __shfl_sync(0xffffffffu, item_pix, 0);
+    if (item_pix >= n_work) break;
+    long long gp = a.pixlist ? a.pixlist[item_pix] : item_pix;
+    int qp = panel_of_pixel(a, gp);
+    const DevPanel &P = a.panels[qp];
+    long long local = gp - P.pix0;
+    int s = (int)(local / P.nfast);
+    int f = (int)(local - (long long)s * P.nfast);
+
+    // ---- 1. per-unit geometry (FP64) into shared memory
+    for (int u = lane; u < U; u += 32) {
+      int t = u % a.T, ij = u / a.T, i = ij / os, j = ij % os;
+      double px = P.px;
+      double cf = (f + (i + 0.5) / os) * px, cs = (s + (j + 0.5) / os) * px,
+             cn = t * a.dt;
+      double pos[3], d[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        pos[c] = P.origin[c] + cf * P.fdir[c] + cs * P.sdir[c] +
+                 cn * P.ndir[c];
+      double R = sqrt(dot3d_m(pos, pos));
+      float *ud = unit + u * kUnitFloats;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        d[c] = pos[c] / R;
+        double v = d[c] - a.i0[c];
+        float vh = (float)v;
+        ud[c] = vh;
+        ud[3 + c] = (float)(v - (double)vh);
+        ud[7 + c] = (float)d[c];
+      }
+      float omega = (float)(px * px * dot3d_m(P.ndir, pos) / (R * R * R));
+      float cap = 1.f;
+      if (a.thickness > 0.0) {
+        float rho = (float)dot3d_m(d, P.ndir);
+        float L = (float)a.atten * rho, dtf = (float)a.dt;
+        cap = expf(-t * dtf / L) - expf(-(t + 1) * dtf / L);
+      }
+      float scal = omega * cap;
+      if (!HASDIV) {
+        float c2 = (float)dot3d_m(d, a.i0), x = (float)dot3d_m(d, a.e0),
+              y = (float)dot3d_m(d, a.b0);
+        scal *= 0.5f * (1.f + c2 * c2 - kahn * (x * x - y * y));
+      }
+      ud[6] = scal;
+    }
+    __syncwarp();
+
+    // ---- 2./3. scan the steps, evaluate surviving terms 32 at a time
+    Kahan acc;
+    int head = 0, tail = 0;
+    for (int base = 0; base < items; base += 32) {
+      int it = base + lane;
+      bool valid = it < items;
+      int u = valid ? it / PM : 0, pm = valid ? it - u * PM : 0;
+      const float *ud = unit + u * kUnitFloats;
+      float vh[3] = {ud[0], ud[1], ud[2]}, vl[3] = {ud[3], ud[4], ud[5]};
+      float scal = ud[6];
+      float Gh[3], Gl[3], rq[3], rl[3], n0[3];
+#pragma unroll
+      for (int x = 0; x < 3; ++x) {
+        ff_dot3(s_axh + pm * 9 + 3 * x, s_axl + pm * 9 + 3 * x, vh, vl,
+                Gh[x], Gl[x]);
+        float qh, qe;
+        two_prod(Gh[x], a.u0h, qh, qe);
+        float ql = fmaf(Gh[x], a.u0l, fmaf(Gl[x], a.u0h, qe));
+        n0[x] = rintf(qh);
+        float rh, rl0;
+        two_sum(__fsub_rn(qh, n0[x]), ql, rh, rl0);
+        // r_hi on a 2^-21 grid: r_hi - n is then exact for |n| < 7
+        rq[x] = __fmul_rn(rintf(__fmul_rn(rh, 2097152.f)), 1.f / 2097152.f);
+        rl[x] = rl0 + __fsub_rn(rh, rq[x]);
+      }
+      for (int k = 0; k < S; ++k) {
+        const float *src = s_src + k * SRC32_STRIDE;
+        const float dh = src[SRC32_DH];
+        // cut test on the cheap offset t - rint(t) (error ~1 ulp of t, which
+        // only moves terms ~1e-38 below the peak across the cut)
+        float tq[3], nf[3], fr[3];
+#pragma unroll
+        for (int x = 0; x < 3; ++x) {
+          tq[x] = fmaf(Gh[x], dh, rq[x]);
+          if (HASDIV && valid) tq[x] -= __ldg(a.divh + ((size_t)pm * S + k) * 3 + x);
+          nf[x] = rintf(tq[x]);
+          fr[x] = tq[x] - nf[x];
+        }
+        float rad2 = N2[0] * fr[0] * fr[0];
+        rad2 = fmaf(N2[1] * fr[1], fr[1], rad2);
+        rad2 = fmaf(N2[2] * fr[2], fr[2], rad2);
+        bool hit = valid && rad2 <= cutg;
+        unsigned m = __ballot_sync(0xffffffffu, hit);
+        if (m == 0u) continue;
+        if (hit) {
+          // the precise offset: G_hi d_hi + (r_q - n) in one rounding (r_q
+          // on a 2^-21 grid makes r_q - n exact) plus the small terms
+          const float dl = src[SRC32_DL];
+#pragma unroll
+          for (int x = 0; x < 3; ++x) {
+            float sx = fmaf(Gh[x], dh, __fsub_rn(rq[x], nf[x]));
+            float c = fmaf(Gh[x], dl, fmaf(Gl[x], dh, rl[x]));
+            fr[x] = sx + c;
+            if (HASDIV) {
+              // the divergence term moves h after the rint: re-centre
+              size_t e = ((size_t)pm * S + k) * 3 + x;
+              fr[x] -= __ldg(a.divh + e) + __ldg(a.divl + e);
+              float n2 = rintf(fr[x]);
+              fr[x] -= n2;
+              nf[x] += n2;
+            }
+          }
+          int e = (tail + __popc(m & lt_mask)) & (kRing - 1);
+          float w = src[SRC32_W] * scal;
+          if (HASDIV) {
+            const float *df = ud + 7, *dir = src + SRC32_DIR,
+                        *ev = src + SRC32_E, *bv = src + SRC32_B;
+            float c2 = df[0] * dir[0] + df[1] * dir[1] + df[2] * dir[2];
+            float x = df[0] * ev[0] + df[1] * ev[1] + df[2] * ev[2];
+            float y = df[0] * bv[0] + df[1] * bv[1] + df[2] * bv[2];
+            w *= 0.5f * (1.f + c2 * c2 - kahn * (x * x - y * y));
+          }
+#pragma unroll
+          for (int x = 0; x < 3; ++x) {
+            q.f[x][e] = fr[x];
+            q.n[x][e] = __float2int_rn(n0[x] + nf[x]) - a.hmin[x];
+          }
+          q.w[e] = w;
+        }
+        tail += __popc(m);
+        if (tail - head >= 32) {
+          __syncwarp();
+          eval_term<INTERP>(a, q, (head + lane) & (kRing - 1), acc);
+          head += 32;
+          __syncwarp();
+        }
+      }
+    }
+    __syncwarp();
+    if (lane < tail - head)
+      eval_term<INTERP>(a, q, (head + lane) & (kRing - 1), acc);
+    evals += tail;
+    __syncwarp();
+
+    // ---- 4. warp reduction in FP64, fused accumulate into the image
+    double v = acc.value();
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) a.image[gp] += a.prefactor * v;
+    __syncwarp();
+  }
+  if (lane == 0 && a.stats && evals) atomicAdd(a.stats, evals);
+}
+
+size_t split_smem_bytes(const SpotArgs &a) {
+  return (size_t)(2 * a.PM * 9 + a.S * SRC32_STRIDE +
+                  kSplitWarps * kMaxUnits * kUnitFloats) * sizeof(float) +
+         kSplitWarps * sizeof(SplitRing);
+}
+
+bool split_supported(const SpotArgs &a) {
+  return a.shape == 1 && a.os * a.os * a.T <= kMaxUnits &&
+         split_smem_bytes(a) <= 200 * 1024;
+}
+
+cudaError_t launch_spots_split(const SpotArgs &a, unsigned long long *work,
+                               int sm_count, cudaStream_t st) {
+  size_t smem = split_smem_bytes(a);
+  void (*kern)(SpotArgs, unsigned long long *) =
+      a.interp ? (a.has_div ? spots_split_kernel<1, 1> : spots_split_kernel<1, 0>)
+               : (a.has_div ? spots_split_kernel<0, 1> : spots_split_kernel<0, 0>);
+  cudaError_t e = cudaFuncSetAttribute(
+      kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern,
+                                                    kSplitThreads, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  long long n_work = a.pixlist ? a.n_list : a.npix;
+  long long blocks = (long long)sm_count * per_sm;
+  long long need = (n_work + kSplitWarps - 1) / kSplitWarps;
+  if (blocks > need) blocks = need;
+  if (blocks < 1) return cudaSuccess;
+  kern<<<(unsigned)blocks, kSplitThreads, smem, st>>>(a, work);
+  return cudaGetLastError();
+}
+
+}  // namespace nbgb

@@ -22,6 +22,8 @@ NB_OK, NB_EINVAL, NB_ENOMEM, NB_ECUDA, NB_ESTATE, NB_ETIMEOUT = (
 NB_F64, NB_MIXED, NB_F32 = 0, 1, 2
 NB_DTYPE_F32, NB_DTYPE_F64 = 0, 1
 PRECISIONS = {"f64": NB_F64, "mixed": NB_MIXED, "f32": NB_F32}
+NB_OPT_VARIANT = 1
+VARIANTS = {"auto": 0, "thread": 1, "warp": 2}
 
 _LOCK = threading.Lock()
 _LIB = None
@@ -64,6 +66,7 @@ SIGNATURES = {
                                     ctypes.c_int]),
     "nb_image_device_ptr": (_vp, [_vp]),
     "nb_get_stats": (ctypes.c_int, [_vp, _llp, _llp]),
+    "nb_set_option": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_longlong]),
     "nb_synchronize": (ctypes.c_int, [_vp]),
     "nb_free": (ctypes.c_int, [_vp]),
     "nb_last_error": (ctypes.c_char_p, [_vp]),
@@ -208,6 +211,11 @@ class Sim:
     def zero(self):
         _check(self.lib.nb_zero_image(self.h), self.h)
 
+    def set_variant(self, name: str):
+        _check(self.lib.nb_set_option(self.h, NB_OPT_VARIANT,
+                                      VARIANTS[name]), self.h)
+        return self
+
     def stats(self):
         """(evaluated_terms, pixel_steps) of the last add_spots call."""
         ev, ps = ctypes.c_longlong(), ctypes.c_longlong()
@@ -234,9 +242,9 @@ class Sim:
 
 
 def simulate(shot, precision: str = "mixed", pixels=None,
-             device: int = 0) -> np.ndarray:
+             device: int = 0, variant: str = "auto") -> np.ndarray:
     """Image of `shot` (all pixels, or the listed ones in list order)."""
-    sim = Sim(precision, device).set_shot(shot)
+    sim = Sim(precision, device).set_shot(shot).set_variant(variant)
     try:
         sim.add_spots(pixels)
         img = sim.image()

@@ -34,8 +34,8 @@ def check_mixed(got, ref, tol=MIXED_TOL):
     assert abs_err_frac(got, ref) <= tol
 
 
-def run(shot, precision, pixels=None):
-    return nbgb.simulate(shot, precision, pixels)
+def run(shot, precision, pixels=None, variant="auto"):
+    return nbgb.simulate(shot, precision, pixels, variant=variant)
 
 
 # ------------------------------------------------------ single shot (c0)
@@ -81,9 +81,10 @@ def test_large_shot_window_f64(c1win):
     check_f64(run(s, "f64"), ref)
 
 
-def test_large_shot_window_mixed(c1win):
+@pytest.mark.parametrize("variant", ["thread", "warp"])
+def test_large_shot_window_mixed(c1win, variant):
     s, ref = c1win
-    check_mixed(run(s, "mixed"), ref)
+    check_mixed(run(s, "mixed", variant=variant), ref)
 
 
 # ---------------------------------------------- precision sweep (c2)
@@ -109,7 +110,8 @@ def test_multipanel_full_detector(n_src):
     s = W.multipanel_shot(n_src)
     ref = oracle.image(s)
     check_f64(run(s, "f64"), ref)
-    check_mixed(run(s, "mixed"), ref)
+    for variant in ("thread", "warp"):
+        check_mixed(run(s, "mixed", variant=variant), ref)
 
 
 # ---------------------------------------------- paths and edge cases
@@ -181,7 +183,39 @@ def test_edge_case_shot(shape, interp):
         s.ncells = np.array([12.0, 9.0, 7.0])
     ref = oracle.image(s)
     check_f64(run(s, "f64"), ref)
-    check_mixed(run(s, "mixed"), ref)
+    for variant in ("thread", "warp"):
+        check_mixed(run(s, "mixed", variant=variant), ref)
+
+
+@pytest.mark.parametrize("variant", ["thread", "warp"])
+def test_pixel_alone_equals_pixel_in_full_launch(variant):
+    """A pixel's value depends on its own inputs only: launched alone (or
+    in any subset) it is bitwise the value it has in the whole image."""
+    s = W.shrink(W.large_shot(), 40, 24, 2490, 695)
+    full = run(s, "mixed", variant=variant)
+    rng = np.random.default_rng(0)
+    sub = rng.choice(s.npix, 37, replace=False)
+    sim = nbgb.Sim("mixed").set_shot(s).set_variant(variant)
+    sim.add_spots(sub)
+    part = sim.image()[sub]
+    sim.close()
+    assert np.array_equal(part, full[sub])
+
+
+def test_stats_count_evaluated_terms():
+    s = W.shrink(W.large_shot(), 24, 16, 2500, 700)
+    counts = []
+    for variant in ("thread", "warp"):
+        sim = nbgb.Sim("mixed").set_shot(s).set_variant(variant)
+        sim.add_spots()
+        ev, ps = sim.stats()
+        assert ps == s.pixel_steps
+        assert 0 < ev < ps
+        counts.append(ev)
+        sim.close()
+    # both variants skip exactly the same underflowing terms, up to the
+    # rounding of f at the cut
+    assert abs(counts[0] - counts[1]) <= 1e-4 * counts[0]
 
 
 def test_single_pixel_and_empty_list():
@@ -234,5 +268,6 @@ def test_large_shot_full_size_sampled_rows():
     rows = [700, 1500, 2417]
     pix = np.concatenate([np.arange(r * 3072, (r + 1) * 3072) for r in rows])
     ref = oracle.image(s, pix)
-    got = run(s, "mixed")[pix]
-    check_mixed(got, ref)
+    for variant in ("auto", "thread"):
+        got = run(s, "mixed", variant=variant)[pix]
+        check_mixed(got, ref)
