@@ -38,7 +38,7 @@
  *   Kahn  pol = (1 + cos^2 2theta - K cos 2psi sin^2 2theta) / 2, cos 2theta =
  *         d . i, psi the azimuth of d about i measured from the E vector.
  *
- * Every reading of a point the paper leaves open is listed in the design doc.
+ * Every point the paper leaves open is fixed by one of the readings above.
  *
  * The differentiable form (orc_loss_grad) parametrises the lab-frame axes as
  * rows of Rx(tx) Ry(ty) Rz(tz) U diag(a, b, c): an orthorhombic cell with
