@@ -188,6 +188,49 @@ enum { NB_VARIANT_AUTO = 0, NB_VARIANT_THREAD = 1, NB_VARIANT_WARP = 2 };
  * tolerance.  Errors: NB_EINVAL for an unknown key or value. */
 int nb_set_option(nb_sim *sim, int key, long long value);
 
+/* Bragg-spot sum without any allocation by the library.  The paper has no
+ * counterpart: this exists for callers that must not call cudaMalloc (for
+ * example code whose device memory all comes from its own pool or arena,
+ * or a plug-in whose host forbids device allocations).  It runs the
+ * NB_MIXED one-warp-per-pixel kernel for a Gaussian shape on one panel and
+ * adds the result to `image`.
+ *
+ * Device pointers (caller-owned, on the calling thread's current device):
+ *   axes_pm    n_pm x 9 doubles, rows a, b, c (Angstrom) of each crystal
+ *              orientation U_m R_phi (a, b, c)_lab, already rotated by the
+ *              caller; the sum averages over the n_pm entries.
+ *   F          structure factors as for nb_set_crystal.
+ *   lambda_A, weights   n_src doubles each.
+ *   image      nfast x nslow doubles (slow-major), accumulated into.
+ * Host values: panel (copied), oversample and n_layers (os^2 x layers <=
+ * 32), thickness_m, atten_m, Na, Nb, Nc, scale, hkl_min, hkl_n, interp,
+ * default_F, dir (the one propagation direction of every source), fluence,
+ * kahn_K, e_vec, as for the other calls; cuda_stream a cudaStream_t.
+ *
+ * Scratch: a file-scope device array of about 200 KB on every GPU that
+ * loads the library (held until the process exits) holds the staged tables
+ * and two counters; n_pm <= 2048 and n_src <= 1024 are the limits it fits,
+ * and larger values return NB_EINVAL.  Every call shares the array and
+ * rewrites it (the counters are cleared before the kernel runs), so calls
+ * whose work overlaps on the GPU race: serialise them.  The first call on a
+ * device looks up the array's device address once (cudaGetSymbolAddress
+ * with that device current); make that first call before any stream
+ * capture.  The call waits for its table set-up on `cuda_stream` (a
+ * 8-byte device-to-host read) and then queues the kernel asynchronously.
+ * Errors: NB_EINVAL for NULL pointers, sizes outside the limits above, a
+ * non-unit dir, e_vec parallel to dir, or bad geometry; NB_ECUDA if a CUDA
+ * call fails. */
+int nb_add_spots_noalloc(const nb_panel *panel, int oversample, int n_layers,
+                         double thickness_m, double atten_m,
+                         const double *axes_pm, int n_pm, double Na,
+                         double Nb, double Nc, double scale, const float *F,
+                         const int hkl_min[3], const int hkl_n[3], int interp,
+                         double default_F, const double *lambda_A,
+                         const double *weights, int n_src,
+                         const double dir[3], double fluence, double kahn_K,
+                         const double e_vec[3], double *image,
+                         void *cuda_stream);
+
 /* Wait for the handle's queued work. */
 int nb_synchronize(nb_sim *sim);
 

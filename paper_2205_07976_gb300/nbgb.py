@@ -67,6 +67,12 @@ SIGNATURES = {
     "nb_image_device_ptr": (_vp, [_vp]),
     "nb_get_stats": (ctypes.c_int, [_vp, _llp, _llp]),
     "nb_set_option": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_longlong]),
+    "nb_add_spots_noalloc": (ctypes.c_int, [
+        ctypes.POINTER(NbPanel), ctypes.c_int, ctypes.c_int, ctypes.c_double,
+        ctypes.c_double, _vp, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+        ctypes.c_double, ctypes.c_double, _vp, _ip, _ip, ctypes.c_int,
+        ctypes.c_double, _vp, _vp, ctypes.c_int, _dp, ctypes.c_double,
+        ctypes.c_double, _dp, _vp, _vp]),
     "nb_synchronize": (ctypes.c_int, [_vp]),
     "nb_free": (ctypes.c_int, [_vp]),
     "nb_last_error": (ctypes.c_char_p, [_vp]),
