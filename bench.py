@@ -44,6 +44,24 @@ WORKLOAD = ("large shot 3072x3072, oversample 2, 2 layers (0.5 mm, atten "
             "[-60,60]^3, Kahn 0.99")
 SM_COUNT_GB300 = 152
 FP32_LANES_PER_SM = 128
+# DRAM bytes (read + write) of one full-size launch of the warp-per-pixel
+# kernel, from one ncu capture (profiles/spots_split_large_shot_dram.txt);
+# valid only while the kernel sources hash to the value they had then
+TRAFFIC_CAPTURE = {"bytes": 76818176 + 27227136,
+                   "sources": ["paper_2205_07976_gb300/csrc/spots_split.cu",
+                               "paper_2205_07976_gb300/csrc/mixed_common.cuh"],
+                   "sha256_16": "06436b219c46efa3"}
+
+
+def captured_traffic():
+    import hashlib
+    h = hashlib.sha256()
+    for f in TRAFFIC_CAPTURE["sources"]:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    if h.hexdigest()[:16] != TRAFFIC_CAPTURE["sha256_16"]:
+        return None
+    return TRAFFIC_CAPTURE["bytes"]
 
 
 def parse():
@@ -192,6 +210,7 @@ def run_ours(args):
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32,
                         device=dev)
     sim = nbgb.Sim("mixed", device=local, stream=stream).set_shot(shot)
+    sim.set_variant("warp")  # the warp-per-pixel kernel (spots_split_kernel)
 
     kernel_times = []
 
@@ -269,8 +288,10 @@ def run_ours(args):
         "gpu_launches": args.steps,
         "roofline": {"bound": "alu", "achieved": achieved,
                      "peak": peak_fp32, "unit": "TFLOP/s",
-                     "frac": achieved / peak_fp32, "traffic": None,
-                     "kernel": "spots_mixed", "kernel_ms": t_kernel * 1e3,
+                     "frac": achieved / peak_fp32,
+                     "traffic": None if args.window else captured_traffic(),
+                     "kernel": "spots_split_kernel",
+                     "kernel_ms": t_kernel * 1e3,
                      "algorithmic_tflop_per_launch": alg / 1e12,
                      "evaluated_terms": evaluated,
                      "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x "

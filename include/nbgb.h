@@ -173,6 +173,38 @@ const double *nb_image_device_ptr(const nb_sim *sim);
 int nb_get_stats(nb_sim *sim, long long *evaluated_terms,
                  long long *pixel_steps);
 
+/* Differentiable crystal (the refinement loop of x-ray tracing, Sec. II:
+ * crystal parameters are refined until the simulated image matches the
+ * measured one).  Sets the lab axes to the rows of Rx(tx) Ry(ty) Rz(tz) U
+ * diag(a, b, c) -- axis v is cell[v] times column v of R U -- with U a
+ * row-major 3x3 rotation, cell = (a, b, c) in Angstrom, rot = (tx, ty, tz)
+ * in radians; and sets Na, Nb, Nc and the scale.  Keeps the mosaic, phi,
+ * shape and table of the last nb_set_crystal, which must come first.
+ * Errors: NB_ESTATE before nb_set_crystal; NB_EINVAL for non-positive cell
+ * or N (integral N for sinc), non-finite values. */
+int nb_set_crystal_params(nb_sim *sim, const double U[9], const double cell[3],
+                          const double rot[3], const double ncells[3],
+                          double scale);
+
+/* Adjoint of the Bragg-spot sum.  Given dLdI (device, nb_num_pixels
+ * doubles: dL/dI_p of any scalar loss L of the image), writes
+ * grad = dL/d(tx, ty, tz, a, b, c, Na, Nb, Nc, scale) (host, 10 doubles)
+ * and, when gradF (device, hkl_n[0] hkl_n[1] hkl_n[2] doubles) is not NULL,
+ * adds dL/dF of every structure factor into it (scatter-add).  Every step
+ * of the forward sum is recomputed in the FP32-mixed arithmetic; nothing
+ * is stored between the passes.  Blocks until done.  Needs a handle made
+ * with NB_MIXED, a Gaussian shape, nearest lookup, one source direction
+ * and nb_set_crystal_params.  Errors: NB_ESTATE / NB_EINVAL otherwise. */
+int nb_adjoint(nb_sim *sim, const double *dLdI, double grad[10],
+               double *gradF);
+
+/* Poisson image loss L = sum_p (I_p + bkg - y_p log(I_p + bkg)) of the
+ * current image against y (device, nb_num_pixels doubles); writes dL/dI_p
+ * into dLdI (device, nb_num_pixels doubles) and L into *loss (host).
+ * Blocks until done.  Errors: NB_EINVAL for NULL pointers or bkg <= 0. */
+int nb_poisson_loss(nb_sim *sim, const double *y, double bkg, double *dLdI,
+                    double *loss);
+
 /* Tuning options (nb_set_option keys). */
 enum {
     /* kernel variant of NB_MIXED: NB_VARIANT_AUTO (default: one warp per

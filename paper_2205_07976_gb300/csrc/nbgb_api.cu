@@ -88,6 +88,11 @@ struct nb_sim {
   int variant = NB_VARIANT_AUTO;
   int sm_count = 0;
   long long last_pixel_steps = 0;
+  // parametrised crystal (for gradients): U, cell, rotation angles
+  bool have_params = false;
+  double pU[9] = {0}, pcell[3] = {0}, prot[3] = {0};
+  double daxes[6][9];  // d(lab axes)/d(tx, ty, tz, a, b, c)
+  DevBuf d_dax, d_part, d_grad;
   int has_div = 0;
   double u0 = 0;
   bool tables_dirty = true;
@@ -130,7 +135,13 @@ static void axis_rotation(const double *k, double ang, double *R) {
 }
 
 // rows (a, b, c) of U_m R_phi(j) (a, b, c)_lab for all (j, m): ax[pm][9]
+static void build_axes_of(const nb_sim *s, const double *lab,
+                          std::vector<double> &ax);
 static void build_axes(const nb_sim *s, std::vector<double> &ax) {
+  build_axes_of(s, s->axes, ax);
+}
+static void build_axes_of(const nb_sim *s, const double *lab,
+                          std::vector<double> &ax) {
   int PM = s->n_phi * s->n_mosaic;
   ax.assign((size_t)PM * 9, 0.0);
   double k[3] = {0, 1, 0};
@@ -150,11 +161,76 @@ static void build_axes(const nb_sim *s, std::vector<double> &ax) {
       double *out = ax.data() + ((size_t)j * s->n_mosaic + m) * 9;
       for (int v = 0; v < 3; ++v)
         for (int r = 0; r < 3; ++r)
-          out[3 * v + r] = UR[3 * r] * s->axes[3 * v] +
-                           UR[3 * r + 1] * s->axes[3 * v + 1] +
-                           UR[3 * r + 2] * s->axes[3 * v + 2];
+          out[3 * v + r] = UR[3 * r] * lab[3 * v] +
+                           UR[3 * r + 1] * lab[3 * v + 1] +
+                           UR[3 * r + 2] * lab[3 * v + 2];
     }
   }
+}
+
+// 3x3 row-major product C = A B
+static void mat3_mul(const double *A, const double *B, double *C) {
+  double T[9];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j)
+      T[3 * i + j] = A[3 * i] * B[j] + A[3 * i + 1] * B[3 + j] +
+                     A[3 * i + 2] * B[6 + j];
+  std::memcpy(C, T, sizeof T);
+}
+
+// elementary rotation about axis `ax` (0 x, 1 y, 2 z) by t, or its
+// derivative with respect to t
+static void elem_rot(int ax, double t, bool deriv, double *M) {
+  double c = std::cos(t), s = std::sin(t);
+  double dc = -s, ds = c;
+  if (deriv) {
+    c = dc;
+    s = ds;
+  }
+  double one = deriv ? 0.0 : 1.0;
+  double R[9] = {0};
+  int i = (ax + 1) % 3, j = (ax + 2) % 3;
+  R[3 * ax + ax] = one;
+  R[3 * i + i] = c;
+  R[3 * i + j] = -s;
+  R[3 * j + i] = s;
+  R[3 * j + j] = c;
+  std::memcpy(M, R, sizeof R);
+}
+
+// lab axes (rows a, b, c) = rows of Rx(tx) Ry(ty) Rz(tz) U diag(cell), i.e.
+// axis v = cell_v times column v of R U; and their derivatives
+static void param_axes(const double *U, const double *cell, const double *rot,
+                       double *axes, double dax[6][9]) {
+  double Rx[9], Ry[9], Rz[9], D[3][9];
+  elem_rot(0, rot[0], false, Rx);
+  elem_rot(1, rot[1], false, Ry);
+  elem_rot(2, rot[2], false, Rz);
+  double RU[9], dRU[3][9], T[9];
+  mat3_mul(Ry, Rz, T);
+  mat3_mul(Rx, T, RU);
+  mat3_mul(RU, U, RU);
+  for (int r = 0; r < 3; ++r) {
+    double Rs[3][9];
+    std::memcpy(Rs[0], Rx, sizeof Rx);
+    std::memcpy(Rs[1], Ry, sizeof Ry);
+    std::memcpy(Rs[2], Rz, sizeof Rz);
+    elem_rot(r, rot[r], true, D[r]);
+    std::memcpy(Rs[r], D[r], sizeof D[r]);
+    mat3_mul(Rs[1], Rs[2], T);
+    mat3_mul(Rs[0], T, dRU[r]);
+    mat3_mul(dRU[r], U, dRU[r]);
+  }
+  for (int v = 0; v < 3; ++v)
+    for (int c = 0; c < 3; ++c) axes[3 * v + c] = cell[v] * RU[3 * c + v];
+  for (int r = 0; r < 6; ++r)
+    for (int i = 0; i < 9; ++i) dax[r][i] = 0.0;
+  for (int r = 0; r < 3; ++r)
+    for (int v = 0; v < 3; ++v)
+      for (int c = 0; c < 3; ++c)
+        dax[r][3 * v + c] = cell[v] * dRU[r][3 * c + v];
+  for (int v = 0; v < 3; ++v)
+    for (int c = 0; c < 3; ++c) dax[3 + v][3 * v + c] = RU[3 * c + v];
 }
 
 // transverse polarization basis of source direction dir: E' = unit part of
@@ -267,6 +343,22 @@ static int upload_tables(nb_sim *s) {
     cudaMemcpyAsync(s->d_divl.p, divl.data(), divl.size() * 4,
                     cudaMemcpyHostToDevice, s->stream);
   }
+  if (s->have_params) {
+    // derivative of every rotated axis: the same rotations applied to the
+    // derivative of the lab axes (the maps are linear): [PM][6][9] floats
+    std::vector<float> dax((size_t)PM * 54);
+    for (int r = 0; r < 6; ++r) {
+      std::vector<double> t;
+      build_axes_of(s, s->daxes[r], t);
+      for (int pm = 0; pm < PM; ++pm)
+        for (int i = 0; i < 9; ++i)
+          dax[(size_t)pm * 54 + r * 9 + i] = (float)t[(size_t)pm * 9 + i];
+    }
+    if ((e = s->d_dax.ensure(dax.size() * 4)) != cudaSuccess)
+      return fail(s, NB_ENOMEM, "derivative table");
+    cudaMemcpyAsync(s->d_dax.p, dax.data(), dax.size() * 4,
+                    cudaMemcpyHostToDevice, s->stream);
+  }
   // pageable copies are staged before return; check the queue is healthy
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(s, e, "table upload");
@@ -365,7 +457,8 @@ int nb_free(nb_sim *sim) {
                       &sim->d_axl,    &sim->d_src64, &sim->d_src32,
                       &sim->d_divh,   &sim->d_divl,  &sim->d_F,
                       &sim->d_image,  &sim->d_list,  &sim->d_tmp,
-                      &sim->d_stats,  &sim->d_work};
+                      &sim->d_stats,  &sim->d_work,  &sim->d_dax,
+                      &sim->d_part,   &sim->d_grad};
     for (DevBuf *b : bufs) b->release();
   }
   delete sim;
@@ -438,6 +531,34 @@ int nb_set_crystal(nb_sim *s, const double axes[9], const double *umats,
     if (std::isfinite(default_F)) s->defF = default_F;
   }
   s->have_crystal = true;
+  s->have_params = false;
+  s->tables_dirty = true;
+  return NB_OK;
+}
+
+int nb_set_crystal_params(nb_sim *s, const double U[9], const double cell[3],
+                          const double rot[3], const double ncells[3],
+                          double scale) {
+  if (!s) return NB_EINVAL;
+  if (!U || !cell || !rot || !ncells)
+    return fail(s, NB_EINVAL, "NULL parameter array");
+  if (!s->have_crystal)
+    return fail(s, NB_ESTATE, "nb_set_crystal must come first");
+  for (int i = 0; i < 3; ++i) {
+    if (!(cell[i] > 0) || !std::isfinite(cell[i]) || !std::isfinite(rot[i]))
+      return fail(s, NB_EINVAL, "cell / rotation");
+    if (!(ncells[i] > 0) || !std::isfinite(ncells[i]) ||
+        (s->shape == NB_SHAPE_SINC && ncells[i] != std::floor(ncells[i])))
+      return fail(s, NB_EINVAL, "N");
+  }
+  if (!std::isfinite(scale)) return fail(s, NB_EINVAL, "scale");
+  std::memcpy(s->pU, U, sizeof s->pU);
+  std::memcpy(s->pcell, cell, sizeof s->pcell);
+  std::memcpy(s->prot, rot, sizeof s->prot);
+  param_axes(U, cell, rot, s->axes, s->daxes);
+  std::memcpy(s->N, ncells, sizeof s->N);
+  s->scale = scale;
+  s->have_params = true;
   s->tables_dirty = true;
   return NB_OK;
 }
@@ -693,6 +814,68 @@ int nb_get_image(nb_sim *s, void *dst, size_t n_elems, int dtype,
 
 const double *nb_image_device_ptr(const nb_sim *s) {
   return (s && s->have_det) ? (const double *)s->d_image.p : nullptr;
+}
+
+int nb_adjoint(nb_sim *s, const double *dLdI, double grad[10],
+               double *gradF) {
+  if (!s) return NB_EINVAL;
+  if (!dLdI || !grad) return fail(s, NB_EINVAL, "NULL dLdI / grad");
+  if (!s->have_crystal || !s->have_beam || !s->have_det || !s->have_F)
+    return fail(s, NB_ESTATE, "crystal, beam and detector must be set first");
+  if (!s->have_params)
+    return fail(s, NB_ESTATE, "nb_set_crystal_params must come first");
+  if (s->precision != NB_MIXED || s->shape != NB_SHAPE_GAUSS ||
+      s->interp != NB_INTERP_NEAREST)
+    return fail(s, NB_EINVAL,
+                "the adjoint needs NB_MIXED, a Gaussian shape and nearest "
+                "lookup");
+  DeviceGuard g(s->device);
+  int rc = upload_tables(s);
+  if (rc != NB_OK) return rc;
+  if (s->has_div)
+    return fail(s, NB_EINVAL, "the adjoint needs one source direction");
+  SpotArgs a;
+  fill_args(s, a);
+  if (nbgb::adjoint_smem_bytes(a) > 200 * 1024)
+    return fail(s, NB_EINVAL, "tables exceed 200 KB of shared memory");
+  long long blocks = nbgb::adjoint_blocks(a);
+  cudaError_t e = s->d_part.ensure((size_t)(blocks + 1) * 10 * sizeof(double));
+  if (e == cudaSuccess) e = s->d_grad.ensure(16 * sizeof(double));
+  if (e != cudaSuccess) return fail(s, NB_ENOMEM, "gradient scratch");
+  double kc = nbgb::kElectronRadius * nbgb::kElectronRadius * s->fluence /
+              ((double)s->os * s->os * s->n_mosaic * s->n_phi);
+  e = nbgb::launch_adjoint(a, (const float *)s->d_dax.p, dLdI, gradF,
+                           (double *)s->d_part.p, kc, s->scale,
+                           (double *)s->d_grad.p, s->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(grad, s->d_grad.p, 10 * sizeof(double),
+                        cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e, "adjoint");
+  return NB_OK;
+}
+
+int nb_poisson_loss(nb_sim *s, const double *y, double bkg, double *dLdI,
+                    double *loss) {
+  if (!s) return NB_EINVAL;
+  if (!y || !dLdI || !loss) return fail(s, NB_EINVAL, "NULL argument");
+  if (!s->have_det) return fail(s, NB_ESTATE, "detector not set");
+  if (!(bkg > 0) || !std::isfinite(bkg))
+    return fail(s, NB_EINVAL, "bkg must be positive");
+  DeviceGuard g(s->device);
+  int blocks = nbgb::loss_blocks(s->npix);
+  cudaError_t e = s->d_part.ensure((size_t)(blocks + 1) * 10 * sizeof(double));
+  if (e == cudaSuccess) e = s->d_grad.ensure(16 * sizeof(double));
+  if (e != cudaSuccess) return fail(s, NB_ENOMEM, "loss scratch");
+  e = nbgb::launch_poisson_loss((const double *)s->d_image.p, y, s->npix, bkg,
+                                dLdI, (double *)s->d_part.p,
+                                (double *)s->d_grad.p, s->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(loss, s->d_grad.p, sizeof(double),
+                        cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e, "loss");
+  return NB_OK;
 }
 
 int nb_set_option(nb_sim *s, int key, long long value) {

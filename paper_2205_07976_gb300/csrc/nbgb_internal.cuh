@@ -210,6 +210,17 @@ __device__ __forceinline__ void lagrange4(T x, T w[4]) {
 }
 
 cudaError_t launch_spots_f64(const SpotArgs &a, cudaStream_t st);
+size_t adjoint_smem_bytes(const SpotArgs &a);
+long long adjoint_blocks(const SpotArgs &a);
+int loss_blocks(long long n);
+cudaError_t launch_adjoint(const SpotArgs &a, const float *dax,
+                           const double *dLdI, double *gradF,
+                           double *partials, double kc, double scale,
+                           double *grad_out, cudaStream_t st);
+cudaError_t launch_poisson_loss(const double *img, const double *y,
+                                long long n, double bkg, double *dLdI,
+                                double *partials, double *loss_out,
+                                cudaStream_t st);
 size_t split_smem_bytes(const SpotArgs &a);
 bool split_supported(const SpotArgs &a);
 cudaError_t launch_spots_split(const SpotArgs &a, unsigned long long *work,

@@ -67,6 +67,10 @@ SIGNATURES = {
     "nb_image_device_ptr": (_vp, [_vp]),
     "nb_get_stats": (ctypes.c_int, [_vp, _llp, _llp]),
     "nb_set_option": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_longlong]),
+    "nb_set_crystal_params": (ctypes.c_int, [_vp, _dp, _dp, _dp, _dp,
+                                             ctypes.c_double]),
+    "nb_adjoint": (ctypes.c_int, [_vp, _vp, _dp, _vp]),
+    "nb_poisson_loss": (ctypes.c_int, [_vp, _vp, ctypes.c_double, _vp, _dp]),
     "nb_add_spots_noalloc": (ctypes.c_int, [
         ctypes.POINTER(NbPanel), ctypes.c_int, ctypes.c_int, ctypes.c_double,
         ctypes.c_double, _vp, ctypes.c_int, ctypes.c_double, ctypes.c_double,
@@ -150,7 +154,9 @@ class Sim:
                                       PRECISIONS[precision], _vp(raw)))
         self.h = h
         self.precision = precision
+        self.device = int(device)
         self.npix = 0
+        self.shot = None
 
     def close(self):
         if getattr(self, "h", None):
@@ -199,7 +205,14 @@ class Sim:
             float(shot.atten_m)), self.h)
         self.npix = int(self.lib.nb_num_pixels(self.h))
 
+    def upload_F(self, F):
+        """Replace the structure-factor table (same shape and origin)."""
+        s = self.shot.copy()
+        s.F = np.ascontiguousarray(F, dtype=np.float32)
+        self.set_crystal(s)
+
     def set_shot(self, shot):
+        self.shot = shot
         self.set_crystal(shot)
         self.set_beam(shot)
         self.set_detector(shot)
@@ -216,6 +229,30 @@ class Sim:
 
     def zero(self):
         _check(self.lib.nb_zero_image(self.h), self.h)
+
+    def set_params(self, U, cell, rot, ncells, scale):
+        """Lab axes = rows of Rx Ry Rz U diag(cell); sets N and scale."""
+        U, cell, rot, N = _d(U).ravel(), _d(cell), _d(rot), _d(ncells)
+        _check(self.lib.nb_set_crystal_params(self.h, _ptr(U), _ptr(cell),
+                                              _ptr(rot), _ptr(N),
+                                              float(scale)), self.h)
+        return self
+
+    def adjoint(self, dLdI_ptr: int, gradF_ptr: int = 0) -> np.ndarray:
+        """dL/d(tx, ty, tz, a, b, c, Na, Nb, Nc, scale) given a device
+        array of dL/dI; adds dL/dF into the device array at gradF_ptr."""
+        g = np.zeros(10)
+        _check(self.lib.nb_adjoint(self.h, _vp(dLdI_ptr), _ptr(g),
+                                   _vp(gradF_ptr) if gradF_ptr else None),
+               self.h)
+        return g
+
+    def poisson_loss(self, y_ptr: int, bkg: float, dLdI_ptr: int) -> float:
+        out = ctypes.c_double()
+        _check(self.lib.nb_poisson_loss(self.h, _vp(y_ptr), float(bkg),
+                                        _vp(dLdI_ptr), ctypes.byref(out)),
+               self.h)
+        return float(out.value)
 
     def set_variant(self, name: str):
         _check(self.lib.nb_set_option(self.h, NB_OPT_VARIANT,

@@ -1,0 +1,161 @@
+"""Gradients of the Poisson image loss through the hand-written adjoint
+(nb_adjoint, FP32-mixed), against the FP64 oracle's analytic gradient and
+against central finite differences of the GPU FP64 forward."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2205_07976_gb300 import nbgb
+from paper_2205_07976_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+BKG = 1.0
+THETA_TRUE = dict(rot=np.zeros(3), cell=np.array([79.0, 79.0, 38.0]),
+                  N=np.array([15.0, 15.0, 15.0]), scale=1.0)
+THETA = dict(rot=np.array([3e-4, -2e-4, 1e-4]),
+             cell=np.array([79.05, 78.97, 38.02]),
+             N=np.array([14.5, 15.5, 15.2]), scale=1.1)
+
+
+def grad_shot(n_src):
+    """2x2 panels of 41x37 pixels (0.11 mm) around the brightest pixel of
+    a 120x120 survey of the multi-panel shot (10 domains, N=15 Gaussian,
+    nearest lookup on [-40,40]^3)."""
+    s = W.multipanel_shot(n_src, tiles=(1, 1), panel=(120, 120))
+    U = W.random_orientation(np.random.default_rng(3))
+    img = oracle.image(s).reshape(120, 120)
+    js, jf = np.unravel_index(np.argmax(img), img.shape)
+    p = s.panels[0]
+    c = p.origin + (jf + 0.5) * p.pixel_m * p.fdir + (js + 0.5) * p.pixel_m * p.sdir
+    panels = []
+    for ts in range(2):
+        for tf in range(2):
+            o = c + (tf * 42 - 41) * p.pixel_m * p.fdir + (ts * 38 - 37) * p.pixel_m * p.sdir
+            panels.append(W.Panel(origin=o, fdir=p.fdir, sdir=p.sdir,
+                                  ndir=p.ndir, pixel_m=p.pixel_m, nfast=41,
+                                  nslow=37))
+    s.panels = panels
+    return s, U
+
+
+def with_theta(shot, U, th):
+    t = shot.copy()
+    t.axes, _ = oracle.param_axes(U, th["cell"], th["rot"])
+    t.ncells = th["N"].copy()
+    t.scale = th["scale"]
+    return t
+
+
+@pytest.fixture(scope="module", params=[1, 2])
+def case(request):
+    shot, U = grad_shot(request.param)
+    truth = oracle.image(with_theta(shot, U, THETA_TRUE))
+    y = np.random.default_rng(7).poisson(truth + BKG).astype(np.float64)
+    s = with_theta(shot, U, THETA)
+    L, g, gF, model = oracle.loss_grad(s, U, THETA["cell"], THETA["rot"], y,
+                                       BKG)
+    return shot, U, y, (L, g, gF, model)
+
+
+def gpu_grad(shot, U, y, th, precision="mixed"):
+    dev = torch.device("cuda", 0)
+    sim = nbgb.Sim(precision).set_shot(with_theta(shot, U, th))
+    sim.set_params(U, th["cell"], th["rot"], th["N"], th["scale"])
+    sim.add_spots()
+    yd = torch.from_numpy(y).to(dev)
+    dL = torch.empty_like(yd)
+    torch.cuda.synchronize()
+    L = sim.poisson_loss(yd.data_ptr(), BKG, dL.data_ptr())
+    if precision != "mixed":
+        return L, None, None, sim.image()
+    gF = torch.zeros(shot.F.size, dtype=torch.float64, device=dev)
+    g = sim.adjoint(dL.data_ptr(), gF.data_ptr())
+    img = sim.image()
+    sim.close()
+    return L, g, gF.cpu().numpy().reshape(shot.F.shape), img
+
+
+def test_adjoint_matches_oracle_gradient(case):
+    shot, U, y, (L0, g0, gF0, model0) = case
+    L, g, gF, img = gpu_grad(shot, U, y, THETA)
+    assert abs(L - L0) <= 1e-6 * abs(L0)
+    gmax = np.abs(g0).max()
+    for r in range(10):
+        assert abs(g[r] - g0[r]) <= 1e-4 * abs(g0[r]) + 1e-6 * gmax, (
+            r, g[r], g0[r])
+    assert np.abs(gF - gF0).max() <= 1e-4 * np.abs(gF0).max()
+    big = np.abs(gF0) > 1e-2 * np.abs(gF0).max()
+    assert big.sum() >= 3
+    np.testing.assert_allclose(gF[big], gF0[big], rtol=1e-4)
+
+
+def test_adjoint_matches_fd_of_f64_forward(case):
+    shot, U, y, (L0, g0, _, _) = case
+    _, g, _, _ = gpu_grad(shot, U, y, THETA)
+    x0 = np.concatenate([THETA["rot"], THETA["cell"], THETA["N"],
+                         [THETA["scale"]]])
+
+    def loss_f64(x):
+        th = dict(rot=x[0:3], cell=x[3:6], N=x[6:9], scale=x[9])
+        sim = nbgb.Sim("f64").set_shot(with_theta(shot, U, th))
+        sim.set_params(U, th["cell"], th["rot"], th["N"], th["scale"])
+        sim.add_spots()
+        m = sim.image() + BKG
+        sim.close()
+        return float(np.sum(m - y * np.log(m)))
+
+    for r in range(10):
+        h = 1e-6 if r < 3 else 1e-6 * abs(x0[r])
+        xp, xm = x0.copy(), x0.copy()
+        xp[r] += h
+        xm[r] -= h
+        fd = (loss_f64(xp) - loss_f64(xm)) / (2 * h)
+        # the oracle's analytic gradient is exact up to FD's own error
+        assert abs(fd - g0[r]) <= 1e-5 * abs(g0[r]) + 1e-6 * np.abs(g0).max()
+        # the FP32-mixed adjoint, at the mixed tolerance
+        assert abs(fd - g[r]) <= 1e-4 * abs(fd) + 1e-6 * np.abs(g0).max(), (
+            r, fd, g[r])
+
+
+def test_autograd_function_matches_adjoint(case):
+    from paper_2205_07976_gb300.autograd import bragg_image
+    shot, U, y, _ = case
+    dev = torch.device("cuda", 0)
+    sim = nbgb.Sim("mixed").set_shot(with_theta(shot, U, THETA))
+    params = torch.tensor(np.concatenate([THETA["rot"], THETA["cell"],
+                                          THETA["N"], [THETA["scale"]]]),
+                          dtype=torch.float64, requires_grad=True)
+    # a float64 leaf gets a float64 gradient (autograd casts to the
+    # input's dtype); the table itself is uploaded as float32 either way
+    F = torch.from_numpy(shot.F.astype(np.float64)).requires_grad_(True)
+    img = bragg_image(params, F, sim, U)
+    yd = torch.from_numpy(y).to(dev)
+    loss = (img + BKG - yd * torch.log(img + BKG)).sum()
+    loss.backward()
+    L, g, gF, _ = gpu_grad(shot, U, y, THETA)
+    assert abs(loss.item() - L) <= 1e-9 * abs(L)
+    np.testing.assert_allclose(params.grad.numpy(), g, rtol=1e-8,
+                               atol=1e-12 * np.abs(g).max())
+    np.testing.assert_allclose(F.grad.numpy(), gF, rtol=1e-8,
+                               atol=1e-12 * np.abs(gF).max())
+    sim.close()
+
+
+def test_adjoint_rejects_unsupported_setups():
+    shot, U = grad_shot(1)
+    sim = nbgb.Sim("mixed").set_shot(shot)
+    dev = torch.device("cuda", 0)
+    buf = torch.zeros(sim.npix, dtype=torch.float64, device=dev)
+    with pytest.raises(nbgb.NbError) as e:
+        sim.adjoint(buf.data_ptr())
+    assert e.value.code == nbgb.NB_ESTATE  # no nb_set_crystal_params yet
+    t = shot.copy()
+    t.interp = W.INTERP_TRICUBIC
+    sim.set_crystal(t)
+    sim.set_params(U, THETA["cell"], THETA["rot"], THETA["N"], 1.0)
+    with pytest.raises(nbgb.NbError) as e:
+        sim.adjoint(buf.data_ptr())
+    assert e.value.code == nbgb.NB_EINVAL
+    sim.close()
