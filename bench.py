@@ -75,8 +75,10 @@ def parse():
     ap.add_argument("--window", type=int, default=0,
                     help="time an N x N window of the large shot instead "
                          "of the whole image (for profiling)")
-    ap.add_argument("--legs", default="main,e2e,f64,cpu",
-                    help="comma list of main, e2e, f64, cpu")
+    ap.add_argument("--legs", default="main,e2e,f64,cpu,serve",
+                    help="comma list of main, e2e, f64, cpu, serve")
+    ap.add_argument("--serve-requests", type=int, default=4096)
+    ap.add_argument("--serve-seq-subset", type=int, default=16)
     return ap.parse_args()
 
 
@@ -255,6 +257,9 @@ def run_ours(args):
     value = units / t_step
     clocks = clk.summary()
 
+    serving = None
+    if "serve" in legs:
+        serving = run_serving(args, local, torch, nbgb, W)
     e2e = None
     if "e2e" in legs:
         e2e = run_e2e(args, sim, shot, world, pg, torch, np, nbgb)
@@ -285,6 +290,7 @@ def run_ours(args):
                    "l2": "512 MB buffer rewritten between timed steps"},
         "e2e": e2e,
         "f64": f64,
+        "serving": serving,
         "gpu_launches": args.steps,
         "roofline": {"bound": "alu", "achieved": achieved,
                      "peak": peak_fp32, "unit": "TFLOP/s",
@@ -361,6 +367,78 @@ def run_f64(args, shot, local, stream, torch, nbgb, W):
     return {"value": len(rows) * shot.steps_per_pixel / t64, "unit": UNIT,
             "sample": f"every {args.f64_rows_every}th row "
                       f"({len(rows)} pixels)", "ms": t64 * 1e3}
+
+
+def run_serving(args, local, torch, nbgb, W):
+    """Continuous batching of shot requests (random orientation, 1-100
+    sources, 1-50 mosaic domains, ROI of 1e3-4e6 pixels, log-uniform) with
+    the 3072x3072 detector and the tricubic F table resident: capacity with
+    all requests queued at t=0, then Poisson arrivals at 0.5, 0.8 and 1.0 x
+    that capacity (latency = arrival to image fetched to host); and, on a
+    fixed subset, the same requests as sequential stand-alone launches in
+    FP64 and in FP32-mixed."""
+    import numpy as np
+    base = W.serving_detector_shot()
+    reqs = W.serving_requests(args.serve_requests, seed=5)
+    total_steps = sum(r.pixel_steps for r in reqs)
+    buf = np.empty(max(r.npix for r in reqs), dtype=np.float64)
+
+    def serve(arrivals):
+        srv = nbgb.Server(base, max_slots=256, pool_bytes=4 << 30,
+                          step_budget=500_000_000, device=local)
+        t0 = time.perf_counter()
+        arr = {}
+        lat = []
+        i = 0
+        n = len(reqs)
+        while len(lat) < n:
+            now = time.perf_counter() - t0
+            while i < n and arrivals[i] <= now:
+                r = reqs[i]
+                rid = srv.submit(r.axes, r.umats, r.lambdas, r.weights,
+                                 r.scale, r.roi)
+                arr[rid] = (arrivals[i], r.npix)
+                i += 1
+            if not arr:
+                # nothing queued or running: wait for the next arrival
+                time.sleep(min(max(arrivals[i] - now, 0.0), 5e-4))
+                continue
+            srv.step()
+            for rid in srv.completed():
+                a, npx = arr.pop(rid)
+                srv.result(rid, out=buf[:npx])
+                lat.append(time.perf_counter() - t0 - a)
+        wall = time.perf_counter() - t0
+        srv.close()
+        lat = np.array(lat)
+        return {"shots_per_s": n / wall, "wall_s": wall,
+                "pixel_steps_per_s": total_steps / wall,
+                "p50_ms": float(np.percentile(lat, 50) * 1e3),
+                "p99_ms": float(np.percentile(lat, 99) * 1e3)}
+
+    cap = serve(np.zeros(len(reqs)))
+    out = {"requests": len(reqs), "pixel_steps": total_steps,
+           "capacity": cap, "rates": {}}
+    for f in (0.5, 0.8, 1.0):
+        arrivals = W.poisson_arrivals(len(reqs), f * cap["shots_per_s"],
+                                      seed=int(f * 10))
+        out["rates"][str(f)] = serve(arrivals)
+    # sequential stand-alone launches on a fixed subset
+    sub = reqs[:args.serve_seq_subset]
+    for prec in ("f64", "mixed"):
+        t0 = time.perf_counter()
+        for r in sub:
+            sim = nbgb.Sim(prec, device=local).set_shot(
+                W.request_shot(base, r))
+            sim.add_spots()
+            sim.image()
+            sim.close()
+        dt = time.perf_counter() - t0
+        out[f"sequential_{prec}"] = {
+            "shots_per_s": len(sub) / dt,
+            "pixel_steps_per_s": sum(r.pixel_steps for r in sub) / dt,
+            "subset": f"first {len(sub)} requests"}
+    return out
 
 
 # ------------------------------------------------------- reference arm

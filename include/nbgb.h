@@ -205,6 +205,92 @@ int nb_adjoint(nb_sim *sim, const double *dLdI, double grad[10],
 int nb_poisson_loss(nb_sim *sim, const double *y, double bkg, double *dLdI,
                     double *loss);
 
+/* ------------------------------------------------------------------ */
+/* Serving: continuous batching of shot requests on one GPU.  The paper
+ * hides I/O latency by sharing a GPU between several ranks, each with its
+ * own batch of images (Sec. IV, Fig. 3); here one server keeps the
+ * structure-factor table and the detector resident and admits requests of
+ * uneven size as slots and image memory free up, batching all running
+ * requests into each launch. */
+typedef struct nb_server nb_server; /* opaque, owned by the library */
+
+enum { NB_REQ_UNKNOWN = -1, NB_REQ_QUEUED = 0, NB_REQ_RUNNING = 1,
+       NB_REQ_DONE = 2 };
+
+/* Create a server on `device`, queuing work on `cuda_stream` (a
+ * non-default cudaStream_t, or NULL: the server makes its own).
+ *   max_slots    requests resident at once (1..4096; each slot holds up to
+ *                64 mosaic domains and 128 sources).
+ *   pool_bytes   device memory for the images of resident requests (FP64,
+ *                8 bytes per ROI pixel); admission needs room here.
+ *   step_budget  pixel-steps per scheduling step (<= 0: 1e9).
+ *   panel ...    the resident detector (one panel), oversample, layers.
+ *   F ...        the resident structure-factor table (copied).
+ *   Na, Nb, Nc   Gaussian lattice shape (the only shape served).
+ *   dir, fluence, kahn_K, e_vec   beam direction shared by all sources,
+ *                fluence, polarization.
+ * Every step is one replay of a CUDA graph: work-list upload, counter
+ * reset and a persistent kernel whose blocks pull 128-pixel work items.
+ * Errors: NB_EINVAL (bad sizes), NB_ENOMEM, NB_ECUDA. */
+int nb_server_create(nb_server **out, int device, void *cuda_stream,
+                     int max_slots, long long pool_bytes,
+                     long long step_budget, const nb_panel *panel,
+                     int oversample, int n_layers, double thickness_m,
+                     double atten_m, const float *F, const int hkl_min[3],
+                     const int hkl_n[3], int interp, double default_F,
+                     double Na, double Nb, double Nc, const double dir[3],
+                     double fluence, double kahn_K, const double e_vec[3]);
+
+/* Queue one shot: lab axes (rows a, b, c), n_mosaic domain matrices,
+ * n_src wavelengths and weights, scale, and the ROI (a rectangle of the
+ * resident panel).  Inputs are copied.  *request_id receives its id.
+ * Errors: NB_EINVAL for sizes beyond a slot, an ROI outside the panel or
+ * larger than the whole pool. */
+int nb_server_submit(nb_server *srv, const double axes[9],
+                     const double *umats, int n_mosaic,
+                     const double *lambda_A, const double *weights,
+                     int n_src, double scale, int roi_f0, int roi_s0,
+                     int roi_nf, int roi_ns, long long *request_id);
+
+/* One scheduling step: finish the step in flight, admit queued requests
+ * (FIFO; a request that does not fit may be passed by later ones until it
+ * has waited 8 steps), cut the running requests into work items round
+ * robin up to the pixel-step budget, launch, and wait for it up to
+ * timeout_s seconds.  A request's slot is released when it completes;
+ * its image stays in the pool until fetched.  *n_active (may be NULL) =
+ * queued + running.  Errors: NB_ETIMEOUT if the step is still running
+ * after timeout_s (the next call waits for it again); NB_ESTATE if
+ * requests are queued but nothing runs and none can be admitted (the pool
+ * is held by unfetched results: fetch them); NB_ECUDA. */
+int nb_server_step(nb_server *srv, double timeout_s, int *n_active);
+
+/* Ids of requests completed since the last call (up to max_ids). */
+int nb_server_completed(nb_server *srv, long long *ids, int max_ids,
+                        int *n_out);
+
+/* State of a request: NB_REQ_QUEUED, NB_REQ_RUNNING, NB_REQ_DONE, or
+ * NB_REQ_UNKNOWN (never submitted, or already fetched). */
+int nb_server_state(nb_server *srv, long long request_id, int *state);
+
+/* Copy a completed request's image (ROI pixels, slow-major, FP64:
+ * dtype must be NB_DTYPE_F64) to dst (device memory if on_device, else
+ * host), then release its pool memory.  A server only admits new requests
+ * while pool memory is free, so fetch results.
+ * Errors: NB_ESTATE if not done; NB_EINVAL for a wrong size or id. */
+int nb_server_result(nb_server *srv, long long request_id, void *dst,
+                     size_t n_elems, int dtype, int on_device);
+
+/* Queue lengths and free pool bytes (any pointer may be NULL). */
+int nb_server_info(const nb_server *srv, long long *queued,
+                   long long *running, long long *done,
+                   long long *pool_free_bytes);
+
+/* Text of the server's last error. */
+const char *nb_server_last_error(const nb_server *srv);
+
+/* Free the server (waits for its work); NULL is a no-op. */
+int nb_server_free(nb_server *srv);
+
 /* Tuning options (nb_set_option keys). */
 enum {
     /* kernel variant of NB_MIXED: NB_VARIANT_AUTO (default: one warp per

@@ -134,31 +134,28 @@ static void axis_rotation(const double *k, double ang, double *R) {
     R[i] = (i % 4 == 0 ? 1.0 : 0.0) + sn * K[i] + cs * K2[i];
 }
 
-// rows (a, b, c) of U_m R_phi(j) (a, b, c)_lab for all (j, m): ax[pm][9]
-static void build_axes_of(const nb_sim *s, const double *lab,
-                          std::vector<double> &ax);
-static void build_axes(const nb_sim *s, std::vector<double> &ax) {
-  build_axes_of(s, s->axes, ax);
-}
-static void build_axes_of(const nb_sim *s, const double *lab,
-                          std::vector<double> &ax) {
-  int PM = s->n_phi * s->n_mosaic;
+namespace nbgb {
+// rows (a, b, c) of U_m R_phi(j) lab for all (j, m): ax[pm][9]
+void rotated_axes_table(const double *lab, const double *umats, int n_mosaic,
+                        int n_phi, double phi0_deg, double phistep_deg,
+                        const double *spindle, std::vector<double> &ax) {
+  int PM = n_phi * n_mosaic;
   ax.assign((size_t)PM * 9, 0.0);
   double k[3] = {0, 1, 0};
-  double nk = norm3(s->spindle);
+  double nk = norm3(spindle);
   if (nk > 0)
-    for (int i = 0; i < 3; ++i) k[i] = s->spindle[i] / nk;
-  for (int j = 0; j < s->n_phi; ++j) {
+    for (int i = 0; i < 3; ++i) k[i] = spindle[i] / nk;
+  for (int j = 0; j < n_phi; ++j) {
     double R[9];
-    axis_rotation(k, (s->phi0 + j * s->phistep) * (M_PI / 180.0), R);
-    for (int m = 0; m < s->n_mosaic; ++m) {
-      const double *U = s->umats.data() + 9 * m;
+    axis_rotation(k, (phi0_deg + j * phistep_deg) * (M_PI / 180.0), R);
+    for (int m = 0; m < n_mosaic; ++m) {
+      const double *U = umats + 9 * m;
       double UR[9];
       for (int r = 0; r < 3; ++r)
         for (int c = 0; c < 3; ++c)
           UR[3 * r + c] = U[3 * r] * R[c] + U[3 * r + 1] * R[3 + c] +
                           U[3 * r + 2] * R[6 + c];
-      double *out = ax.data() + ((size_t)j * s->n_mosaic + m) * 9;
+      double *out = ax.data() + ((size_t)j * n_mosaic + m) * 9;
       for (int v = 0; v < 3; ++v)
         for (int r = 0; r < 3; ++r)
           out[3 * v + r] = UR[3 * r] * lab[3 * v] +
@@ -166,6 +163,17 @@ static void build_axes_of(const nb_sim *s, const double *lab,
                            UR[3 * r + 2] * lab[3 * v + 2];
     }
   }
+}
+}  // namespace nbgb
+
+static void build_axes_of(const nb_sim *s, const double *lab,
+                          std::vector<double> &ax) {
+  nbgb::rotated_axes_table(lab, s->umats.data(), s->n_mosaic, s->n_phi,
+                           s->phi0, s->phistep, s->spindle, ax);
+}
+
+static void build_axes(const nb_sim *s, std::vector<double> &ax) {
+  build_axes_of(s, s->axes, ax);
 }
 
 // 3x3 row-major product C = A B
@@ -251,24 +259,62 @@ static void split_ff(double v, float &hi, float &lo) {
   lo = (float)(v - (double)hi);
 }
 
+namespace nbgb {
+// u0 = centre of the 1/lambda range of the sources
+double source_u0(const double *lam, int S) {
+  double umin = 1e300, umax = -1e300;
+  for (int k = 0; k < S; ++k) {
+    double u = 1.0 / lam[k];
+    umin = std::fmin(umin, u);
+    umax = std::fmax(umax, u);
+  }
+  return 0.5 * (umin + umax);
+}
+
+// FP32 tables of one shot: double-float axes [PM][9] and the source rows
+// [S][SRC32_STRIDE] (delta = 1/lambda - u0 split, w, dir, E', B')
+void shot_tables_f32(const std::vector<double> &ax, const double *lam,
+                     const double *w, const double *dirs, int S,
+                     const double *evec, double u0, bool plain_f32,
+                     std::vector<float> &axh, std::vector<float> &axl,
+                     std::vector<float> &src32) {
+  axh.resize(ax.size());
+  axl.resize(ax.size());
+  for (size_t i = 0; i < ax.size(); ++i) split_ff(ax[i], axh[i], axl[i]);
+  src32.assign((size_t)S * SRC32_STRIDE, 0.f);
+  for (int k = 0; k < S; ++k) {
+    const double *dir = dirs + 3 * k;
+    double u = 1.0 / lam[k], ep[3], bp[3];
+    pol_basis(dir, evec, ep, bp);
+    float *q = src32.data() + (size_t)k * SRC32_STRIDE;
+    if (plain_f32) {
+      q[SRC32_DH] = 0.f;
+      q[SRC32_DL] = (float)u;  // plain FP32 arm reads u_k here
+    } else {
+      split_ff(u - u0, q[SRC32_DH], q[SRC32_DL]);
+    }
+    q[SRC32_W] = (float)w[k];
+    for (int c = 0; c < 3; ++c) {
+      q[SRC32_DIR + c] = (float)dir[c];
+      q[SRC32_E + c] = (float)ep[c];
+      q[SRC32_B + c] = (float)bp[c];
+    }
+  }
+}
+}  // namespace nbgb
+
 // Uploads the crystal x beam tables (they depend on both).
 static int upload_tables(nb_sim *s) {
   if (!s->tables_dirty) return NB_OK;
   int PM = s->n_phi * s->n_mosaic, S = s->n_src;
   std::vector<double> ax;
   build_axes(s, ax);
-  std::vector<float> axh(ax.size()), axl(ax.size());
-  for (size_t i = 0; i < ax.size(); ++i) split_ff(ax[i], axh[i], axl[i]);
-  // sources: u = 1/lambda, u0 the centre of the range
-  double umin = 1e300, umax = -1e300;
-  for (int k = 0; k < S; ++k) {
-    double u = 1.0 / s->lam[k];
-    umin = std::fmin(umin, u);
-    umax = std::fmax(umax, u);
-  }
-  s->u0 = 0.5 * (umin + umax);
+  s->u0 = nbgb::source_u0(s->lam.data(), S);
+  std::vector<float> axh, axl, src32;
+  nbgb::shot_tables_f32(ax, s->lam.data(), s->w.data(), s->dirs.data(), S,
+                        s->evec, s->u0, s->precision == NB_F32, axh, axl,
+                        src32);
   std::vector<double> src64((size_t)S * nbgb::SRC64_STRIDE);
-  std::vector<float> src32((size_t)S * nbgb::SRC32_STRIDE);
   s->has_div = 0;
   for (int k = 0; k < S; ++k) {
     const double *dir = s->dirs.data() + 3 * k;
@@ -282,21 +328,11 @@ static int upload_tables(nb_sim *s) {
     double *r = src64.data() + (size_t)k * nbgb::SRC64_STRIDE;
     r[nbgb::SRC64_LAM] = s->lam[k];
     r[nbgb::SRC64_W] = s->w[k];
-    float *q = src32.data() + (size_t)k * nbgb::SRC32_STRIDE;
-    if (s->precision == NB_F32) {
-      q[nbgb::SRC32_DH] = 0.f;
-      q[nbgb::SRC32_DL] = (float)u;  // plain FP32 arm reads u_k here
-    } else {
-      split_ff(u - s->u0, q[nbgb::SRC32_DH], q[nbgb::SRC32_DL]);
-    }
-    q[nbgb::SRC32_W] = (float)s->w[k];
+    (void)u;
     for (int c = 0; c < 3; ++c) {
       r[nbgb::SRC64_DIR + c] = dir[c];
       r[nbgb::SRC64_E + c] = ep[c];
       r[nbgb::SRC64_B + c] = bp[c];
-      q[nbgb::SRC32_DIR + c] = (float)dir[c];
-      q[nbgb::SRC32_E + c] = (float)ep[c];
-      q[nbgb::SRC32_B + c] = (float)bp[c];
     }
   }
   // divergence term E[pm][k][x] = A_pm,x . (i_k - i_0) u_k

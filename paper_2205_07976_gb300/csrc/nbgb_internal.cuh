@@ -15,6 +15,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 namespace nbgb {
 
 constexpr double kElectronRadius = 2.8179403262e-15;  // m, CODATA 2018
@@ -208,6 +210,17 @@ __device__ __forceinline__ void lagrange4(T x, T w[4]) {
   w[2] = -b * x * T(0.5);
   w[3] = a * xp1 * T(1.0 / 6.0);
 }
+
+// host-side table builders shared by nb_sim and nb_server
+double source_u0(const double *lam, int S);
+void shot_tables_f32(const std::vector<double> &ax, const double *lam,
+                     const double *w, const double *dirs, int S,
+                     const double *evec, double u0, bool plain_f32,
+                     std::vector<float> &axh, std::vector<float> &axl,
+                     std::vector<float> &src32);
+void rotated_axes_table(const double *lab, const double *umats, int n_mosaic,
+                        int n_phi, double phi0_deg, double phistep_deg,
+                        const double *spindle, std::vector<double> &ax);
 
 cudaError_t launch_spots_f64(const SpotArgs &a, cudaStream_t st);
 size_t adjoint_smem_bytes(const SpotArgs &a);

@@ -1,0 +1,678 @@
+// serve.cu -- continuous batching of Bragg-spot shots on one GPU.
+//
+// The paper hides I/O latency by letting several MPI ranks share one GPU,
+// each simulating its own batch of images (Sec. IV, Fig. 3).  Here one
+// server process keeps the crystal's structure-factor table and the
+// detector resident and admits shot requests of uneven size (ROI pixels,
+// sources, mosaic domains) as slots and device memory free up:
+//
+//   submit  -> FIFO queue (inputs copied, tables built on the host)
+//   step    -> admit while a slot and room in the image pool exist (first
+//              fit; a blocked head request stops bypassing after 8 steps);
+//              cut the active requests into 128-pixel work items, round
+//              robin, up to a pixel-step budget; replay one CUDA graph
+//              (work list upload, counter reset, persistent kernel); wait;
+//              requests whose last item ran are complete
+//   result  -> copy the image out, free its pool range (its slot was freed
+//              when the request completed)
+//
+// The persistent kernel's blocks pull work items through an atomic
+// counter; each item stages its request's tables in shared memory and every
+// thread computes one pixel with the same per-pixel function as the
+// thread-per-pixel kernel, so a request's image does not depend on what it
+// was batched with.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/nbgb.h"
+#include "mixed_pixel.cuh"
+
+namespace nbgb {
+
+constexpr int kServeMaxPM = 64;
+constexpr int kServeMaxSrc = 128;
+constexpr int kServeItemPixels = kTileThreads;  // one pixel per thread
+constexpr int kServeMaxItems = 16384;
+
+struct SlotParams {
+  float axh[kServeMaxPM * 9];
+  float axl[kServeMaxPM * 9];
+  float src32[kServeMaxSrc * SRC32_STRIDE];
+  int PM, S;
+  float u0h, u0l;
+  double prefactor;
+  int f0, s0, nf, ns;
+  long long img_off;  // element offset in the image pool
+};
+
+struct WorkItem {
+  int slot;
+  int count;
+  long long first;  // first ROI pixel (row-major in the ROI)
+};
+
+struct WorkList {
+  int n;
+  int pad[3];
+  WorkItem items[kServeMaxItems];
+};
+
+template <int INTERP>
+__global__ void __launch_bounds__(kTileThreads, 4)
+    serve_kernel(SpotArgs base, const SlotParams *slots, const WorkList *wl,
+                 unsigned *counter, double *pool) {
+  __shared__ float s_axh[kServeMaxPM * 9];
+  __shared__ float s_axl[kServeMaxPM * 9];
+  __shared__ float s_src[kServeMaxSrc * SRC32_STRIDE];
+  __shared__ int s_item;
+  int staged = -1;
+  const DevPanel &P = base.panels[0];
+  const int n = wl->n;
+  while (true) {
+    if (threadIdx.x == 0) s_item = (int)atomicAdd(counter, 1u);
+    __syncthreads();
+    int it = s_item;
+    __syncthreads();
+    if (it >= n) break;
+    const WorkItem w = wl->items[it];
+    const SlotParams &sp = slots[w.slot];
+    if (w.slot != staged) {
+      for (int i = threadIdx.x; i < sp.PM * 9; i += blockDim.x) {
+        s_axh[i] = sp.axh[i];
+        s_axl[i] = sp.axl[i];
+      }
+      for (int i = threadIdx.x; i < sp.S * SRC32_STRIDE; i += blockDim.x)
+        s_src[i] = sp.src32[i];
+      staged = w.slot;
+      __syncthreads();
+    }
+    if ((int)threadIdx.x < w.count) {
+      long long p = w.first + threadIdx.x;
+      int s = sp.s0 + (int)(p / sp.nf);
+      int f = sp.f0 + (int)(p % sp.nf);
+      const PixelView v{sp.PM, sp.S, sp.u0h, sp.u0l};
+      unsigned evals = 0;
+      double total = mixed_pixel<1, INTERP, 0, 0>(base, v, s_axh, s_axl,
+                                                  s_src, P, s, f, evals);
+      pool[sp.img_off + p] = sp.prefactor * total;
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace nbgb
+
+using nbgb::SlotParams;
+using nbgb::WorkItem;
+using nbgb::WorkList;
+
+namespace {
+
+double now_s() {
+  using namespace std::chrono;
+  return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+struct Buf {
+  void *p = nullptr;
+  cudaError_t alloc(size_t n) { return cudaMalloc(&p, n); }
+  ~Buf() {
+    if (p) cudaFree(p);
+  }
+};
+
+struct Request {
+  long long id;
+  SlotParams params;  // host copy (img_off set at admission)
+  long long npix, steps_per_pixel;
+  long long next = 0;     // next ROI pixel to schedule
+  long long pending = 0;  // pixels scheduled in the in-flight step
+  int slot = -1;
+  long long pool_off = -1;
+  int state = NB_REQ_QUEUED;
+  int blocked_steps = 0;
+};
+
+}  // namespace
+
+struct nb_server {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int sm_count = 0, blocks = 0;
+  int max_slots = 0;
+  long long pool_elems = 0;
+  long long budget = 0;
+  double timeout_s = 60.0;
+  std::string err;
+  // shared resident state
+  nb_panel panel;
+  int os = 1, T = 1;
+  double thick = 0, atten = 0;
+  double N[3] = {1, 1, 1};
+  int shape = NB_SHAPE_GAUSS, interp = NB_INTERP_TRICUBIC;
+  int hmin[3], hn[3];
+  double defF = 0;
+  double fluence = 0, kahn = 0, evec[3] = {1, 0, 0}, dir[3] = {0, 0, 1};
+  Buf d_F, d_panel, d_slots, d_pool, d_work, d_counter;
+  WorkList *h_work = nullptr;  // pinned staging of the work list
+  nbgb::SpotArgs base;
+  cudaGraphExec_t graph = nullptr;
+  cudaEvent_t done_ev = nullptr;
+  bool in_flight = false;
+  double launched_at = 0;
+  // host bookkeeping
+  long long next_id = 1;
+  std::deque<long long> queue;
+  std::map<long long, Request> reqs;
+  std::vector<int> free_slots;
+  std::map<long long, long long> free_ranges;  // offset -> length
+  std::vector<long long> completed;            // not yet reported
+  long long rr_cursor = 0;
+};
+
+static int sfail(nb_server *s, int code, const std::string &m) {
+  if (s) s->err = m;
+  return code;
+}
+
+// first-fit allocation in the image pool (elements)
+static long long pool_alloc(nb_server *s, long long n) {
+  for (auto it = s->free_ranges.begin(); it != s->free_ranges.end(); ++it) {
+    if (it->second >= n) {
+      long long off = it->first, len = it->second;
+      s->free_ranges.erase(it);
+      if (len > n) s->free_ranges[off + n] = len - n;
+      return off;
+    }
+  }
+  return -1;
+}
+
+static void pool_free(nb_server *s, long long off, long long n) {
+  auto it = s->free_ranges.emplace(off, n).first;
+  auto nx = std::next(it);
+  if (nx != s->free_ranges.end() && it->first + it->second == nx->first) {
+    it->second += nx->second;
+    s->free_ranges.erase(nx);
+  }
+  if (it != s->free_ranges.begin()) {
+    auto pv = std::prev(it);
+    if (pv->first + pv->second == it->first) {
+      pv->second += it->second;
+      s->free_ranges.erase(it);
+    }
+  }
+}
+
+static int build_graph(nb_server *s) {
+  cudaError_t e = cudaStreamBeginCapture(s->stream,
+                                         cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return sfail(s, NB_ECUDA, "graph capture begin");
+  cudaMemcpyAsync(s->d_work.p, s->h_work, sizeof(WorkList),
+                  cudaMemcpyHostToDevice, s->stream);
+  cudaMemsetAsync(s->d_counter.p, 0, sizeof(unsigned), s->stream);
+  void (*kern)(nbgb::SpotArgs, const SlotParams *, const WorkList *,
+               unsigned *, double *) =
+      s->interp ? nbgb::serve_kernel<1> : nbgb::serve_kernel<0>;
+  kern<<<s->blocks, nbgb::kTileThreads, 0, s->stream>>>(
+      s->base, (const SlotParams *)s->d_slots.p, (const WorkList *)s->d_work.p,
+      (unsigned *)s->d_counter.p, (double *)s->d_pool.p);
+  cudaGraph_t g = nullptr;
+  e = cudaStreamEndCapture(s->stream, &g);
+  if (e != cudaSuccess) return sfail(s, NB_ECUDA, "graph capture end");
+  e = cudaGraphInstantiate(&s->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return sfail(s, NB_ECUDA, "graph instantiate");
+  return NB_OK;
+}
+
+extern "C" {
+
+int nb_server_create(nb_server **out, int device, void *cuda_stream,
+                     int max_slots, long long pool_bytes, long long step_budget,
+                     const nb_panel *panel, int oversample, int n_layers,
+                     double thickness_m, double atten_m, const float *F,
+                     const int hkl_min[3], const int hkl_n[3], int interp,
+                     double default_F, double Na, double Nb, double Nc,
+                     const double dir[3], double fluence, double kahn_K,
+                     const double e_vec[3]) {
+  if (!out) return NB_EINVAL;
+  *out = nullptr;
+  if (!panel || !F || !hkl_min || !hkl_n || !dir || !e_vec) return NB_EINVAL;
+  if (max_slots < 1 || max_slots > 4096 || pool_bytes < 8) return NB_EINVAL;
+  if (oversample < 1 || n_layers < 1 || oversample > 8 || n_layers > 8)
+    return NB_EINVAL;
+  if (!(thickness_m >= 0) || (thickness_m == 0 && n_layers != 1) ||
+      (thickness_m > 0 && !(atten_m > 0)))
+    return NB_EINVAL;
+  if (panel->nfast < 1 || panel->nslow < 1 || !(panel->pixel_m > 0))
+    return NB_EINVAL;
+  if (interp != NB_INTERP_NEAREST && interp != NB_INTERP_TRICUBIC)
+    return NB_EINVAL;
+  if (!(Na > 0 && Nb > 0 && Nc > 0) || !(kahn_K >= 0 && kahn_K <= 1))
+    return NB_EINVAL;
+  for (int i = 0; i < 3; ++i)
+    if (hkl_n[i] < 1) return NB_EINVAL;
+  double dn = std::sqrt(dir[0] * dir[0] + dir[1] * dir[1] + dir[2] * dir[2]);
+  if (std::fabs(dn - 1.0) > 1e-9) return NB_EINVAL;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 ||
+      device >= ndev) {
+    cudaGetLastError();
+    return NB_ECUDA;
+  }
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(device);
+  nb_server *s = new (std::nothrow) nb_server();
+  if (!s) return NB_ENOMEM;
+  int rc = NB_OK;
+  do {
+    s->device = device;
+    s->max_slots = max_slots;
+    s->pool_elems = pool_bytes / (long long)sizeof(double);
+    s->budget = step_budget > 0 ? step_budget : 1000000000LL;
+    s->panel = *panel;
+    s->os = oversample;
+    s->T = n_layers;
+    s->thick = thickness_m;
+    s->atten = atten_m;
+    s->N[0] = Na;
+    s->N[1] = Nb;
+    s->N[2] = Nc;
+    s->interp = interp;
+    s->defF = default_F;
+    s->fluence = fluence;
+    s->kahn = kahn_K;
+    std::memcpy(s->evec, e_vec, sizeof s->evec);
+    std::memcpy(s->dir, dir, sizeof s->dir);
+    for (int i = 0; i < 3; ++i) {
+      s->hmin[i] = hkl_min[i];
+      s->hn[i] = hkl_n[i];
+    }
+    if (cuda_stream) {
+      s->stream = (cudaStream_t)cuda_stream;
+    } else {
+      if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) !=
+          cudaSuccess) {
+        rc = sfail(s, NB_ECUDA, "stream");
+        break;
+      }
+      s->own_stream = true;
+    }
+    if (cudaDeviceGetAttribute(&s->sm_count, cudaDevAttrMultiProcessorCount,
+                               device) != cudaSuccess) {
+      rc = NB_ECUDA;
+      break;
+    }
+    size_t nF = (size_t)hkl_n[0] * hkl_n[1] * hkl_n[2];
+    if (s->d_F.alloc(nF * 4) != cudaSuccess ||
+        s->d_panel.alloc(sizeof(nbgb::DevPanel)) != cudaSuccess ||
+        s->d_slots.alloc(sizeof(SlotParams) * (size_t)max_slots) !=
+            cudaSuccess ||
+        s->d_pool.alloc((size_t)s->pool_elems * sizeof(double)) !=
+            cudaSuccess ||
+        s->d_work.alloc(sizeof(WorkList)) != cudaSuccess ||
+        s->d_counter.alloc(sizeof(unsigned)) != cudaSuccess ||
+        cudaHostAlloc((void **)&s->h_work, sizeof(WorkList),
+                      cudaHostAllocDefault) != cudaSuccess) {
+      cudaGetLastError();
+      rc = sfail(s, NB_ENOMEM, "server buffers");
+      break;
+    }
+    std::memset(s->h_work, 0, sizeof(WorkList));
+    cudaMemcpy(s->d_F.p, F, nF * 4, cudaMemcpyHostToDevice);
+    nbgb::DevPanel P;
+    std::memset(&P, 0, sizeof P);
+    for (int c = 0; c < 3; ++c) {
+      P.origin[c] = panel->origin[c];
+      P.fdir[c] = panel->fdir[c];
+      P.sdir[c] = panel->sdir[c];
+      P.ndir[c] = panel->ndir[c];
+    }
+    P.px = panel->pixel_m;
+    P.nfast = panel->nfast;
+    P.nslow = panel->nslow;
+    cudaMemcpy(s->d_panel.p, &P, sizeof P, cudaMemcpyHostToDevice);
+    // shared kernel arguments
+    nbgb::SpotArgs &a = s->base;
+    std::memset(&a, 0, sizeof a);
+    a.panels = (const nbgb::DevPanel *)s->d_panel.p;
+    a.n_panels = 1;
+    a.os = oversample;
+    a.T = n_layers;
+    a.dt = thickness_m > 0 ? thickness_m / n_layers : 0.0;
+    a.thickness = thickness_m;
+    a.atten = atten_m;
+    double ep[3], bp[3];
+    {
+      double de = dir[0] * e_vec[0] + dir[1] * e_vec[1] + dir[2] * e_vec[2];
+      for (int c = 0; c < 3; ++c) ep[c] = e_vec[c] - de * dir[c];
+      double en = std::sqrt(ep[0] * ep[0] + ep[1] * ep[1] + ep[2] * ep[2]);
+      if (!(en > 0)) {
+        rc = sfail(s, NB_EINVAL, "e_vec parallel to the beam");
+        break;
+      }
+      for (double &v : ep) v /= en;
+      bp[0] = dir[1] * ep[2] - dir[2] * ep[1];
+      bp[1] = dir[2] * ep[0] - dir[0] * ep[2];
+      bp[2] = dir[0] * ep[1] - dir[1] * ep[0];
+    }
+    for (int i = 0; i < 3; ++i) {
+      a.N64[i] = s->N[i];
+      a.N[i] = (float)s->N[i];
+      a.hmin[i] = hkl_min[i];
+      a.hn[i] = hkl_n[i];
+      a.i0[i] = dir[i];
+      a.e0[i] = ep[i];
+      a.b0[i] = bp[i];
+    }
+    double nn = Na * Nb * Nc;
+    a.N6 = (float)(nn * nn);
+    a.shape = NB_SHAPE_GAUSS;
+    a.interp = interp;
+    a.F = (const float *)s->d_F.p;
+    a.defF = (float)default_F;
+    a.defF64 = default_F;
+    a.kahn = (float)kahn_K;
+    a.kahn64 = kahn_K;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, interp ? nbgb::serve_kernel<1> : nbgb::serve_kernel<0>,
+        nbgb::kTileThreads, 0);
+    s->blocks = s->sm_count * (per_sm > 0 ? per_sm : 1);
+    for (int i = max_slots - 1; i >= 0; --i) s->free_slots.push_back(i);
+    s->free_ranges[0] = s->pool_elems;
+    if (cudaEventCreateWithFlags(&s->done_ev, cudaEventDisableTiming) !=
+        cudaSuccess) {
+      rc = NB_ECUDA;
+      break;
+    }
+    rc = build_graph(s);
+  } while (false);
+  if (cudaGetLastError() != cudaSuccess && rc == NB_OK) rc = NB_ECUDA;
+  cudaSetDevice(prev);
+  if (rc != NB_OK) {
+    nb_server_free(s);
+    return rc;
+  }
+  *out = s;
+  return NB_OK;
+}
+
+int nb_server_free(nb_server *s) {
+  if (!s) return NB_OK;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(s->device);
+  if (s->stream) cudaStreamSynchronize(s->stream);
+  if (s->graph) cudaGraphExecDestroy(s->graph);
+  if (s->done_ev) cudaEventDestroy(s->done_ev);
+  if (s->h_work) cudaFreeHost(s->h_work);
+  if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
+  {
+    Buf *bufs[] = {&s->d_F, &s->d_panel, &s->d_slots, &s->d_pool, &s->d_work,
+                   &s->d_counter};
+    for (Buf *b : bufs) {
+      if (b->p) cudaFree(b->p);
+      b->p = nullptr;
+    }
+  }
+  delete s;
+  cudaSetDevice(prev);
+  return NB_OK;
+}
+
+const char *nb_server_last_error(const nb_server *s) {
+  return s ? s->err.c_str() : "null server";
+}
+
+int nb_server_submit(nb_server *s, const double axes[9], const double *umats,
+                     int n_mosaic, const double *lambda_A,
+                     const double *weights, int n_src, double scale,
+                     int roi_f0, int roi_s0, int roi_nf, int roi_ns,
+                     long long *request_id) {
+  if (!s) return NB_EINVAL;
+  if (!axes || !umats || !lambda_A || !weights || !request_id)
+    return sfail(s, NB_EINVAL, "NULL argument");
+  if (n_mosaic < 1 || n_mosaic > nbgb::kServeMaxPM || n_src < 1 ||
+      n_src > nbgb::kServeMaxSrc)
+    return sfail(s, NB_EINVAL, "need 1 <= n_mosaic <= 64, 1 <= n_src <= 128");
+  if (roi_nf < 1 || roi_ns < 1 || roi_f0 < 0 || roi_s0 < 0 ||
+      roi_f0 + roi_nf > s->panel.nfast || roi_s0 + roi_ns > s->panel.nslow)
+    return sfail(s, NB_EINVAL, "ROI outside the detector");
+  long long npix = (long long)roi_nf * roi_ns;
+  if (npix > s->pool_elems)
+    return sfail(s, NB_EINVAL, "ROI larger than the whole image pool");
+  for (int k = 0; k < n_src; ++k)
+    if (!(lambda_A[k] > 0)) return sfail(s, NB_EINVAL, "wavelength");
+  Request r;
+  r.id = s->next_id++;
+  std::memset(&r.params, 0, sizeof r.params);
+  std::vector<double> ax;
+  double spindle[3] = {0, 1, 0};
+  nbgb::rotated_axes_table(axes, umats, n_mosaic, 1, 0.0, 0.0, spindle, ax);
+  double u0 = nbgb::source_u0(lambda_A, n_src);
+  std::vector<double> dirs(3 * (size_t)n_src);
+  for (int k = 0; k < n_src; ++k)
+    for (int c = 0; c < 3; ++c) dirs[3 * k + c] = s->dir[c];
+  std::vector<float> axh, axl, src32;
+  nbgb::shot_tables_f32(ax, lambda_A, weights, dirs.data(), n_src, s->evec,
+                        u0, false, axh, axl, src32);
+  std::memcpy(r.params.axh, axh.data(), axh.size() * 4);
+  std::memcpy(r.params.axl, axl.data(), axl.size() * 4);
+  std::memcpy(r.params.src32, src32.data(), src32.size() * 4);
+  r.params.PM = n_mosaic;
+  r.params.S = n_src;
+  r.params.u0h = (float)u0;
+  r.params.u0l = (float)(u0 - (double)r.params.u0h);
+  r.params.prefactor = nbgb::kElectronRadius * nbgb::kElectronRadius *
+                       s->fluence * scale /
+                       ((double)s->os * s->os * n_mosaic);
+  r.params.f0 = roi_f0;
+  r.params.s0 = roi_s0;
+  r.params.nf = roi_nf;
+  r.params.ns = roi_ns;
+  r.npix = npix;
+  r.steps_per_pixel =
+      (long long)s->os * s->os * s->T * n_src * (long long)n_mosaic;
+  s->queue.push_back(r.id);
+  *request_id = r.id;
+  s->reqs.emplace(r.id, std::move(r));
+  return NB_OK;
+}
+
+// admission: FIFO; later requests may pass a head that does not fit until
+// the head has waited 8 steps
+static int admit(nb_server *s) {
+  bool head_blocked_long = false;
+  for (auto it = s->queue.begin(); it != s->queue.end();) {
+    if (s->free_slots.empty()) break;
+    Request &r = s->reqs[*it];
+    long long off = pool_alloc(s, r.npix);
+    if (off < 0) {
+      if (it == s->queue.begin() && ++r.blocked_steps > 8)
+        head_blocked_long = true;
+      if (head_blocked_long) break;
+      ++it;
+      continue;
+    }
+    r.slot = s->free_slots.back();
+    s->free_slots.pop_back();
+    r.pool_off = off;
+    r.params.img_off = off;
+    r.state = NB_REQ_RUNNING;
+    cudaError_t e = cudaMemcpyAsync((SlotParams *)s->d_slots.p + r.slot,
+                                    &r.params, sizeof(SlotParams),
+                                    cudaMemcpyHostToDevice, s->stream);
+    if (e != cudaSuccess) return sfail(s, NB_ECUDA, "slot upload");
+    it = s->queue.erase(it);
+  }
+  return NB_OK;
+}
+
+static int finish_in_flight(nb_server *s, double timeout_s) {
+  if (!s->in_flight) return NB_OK;
+  double t0 = now_s();
+  while (true) {
+    cudaError_t q = cudaEventQuery(s->done_ev);
+    if (q == cudaSuccess) break;
+    if (q != cudaErrorNotReady) return sfail(s, NB_ECUDA, "step failed");
+    if (now_s() - t0 > timeout_s)
+      return sfail(s, NB_ETIMEOUT, "step did not finish in time");
+  }
+  s->in_flight = false;
+  for (auto &kv : s->reqs) {
+    Request &r = kv.second;
+    if (r.state != NB_REQ_RUNNING) continue;
+    r.pending = 0;
+    if (r.next >= r.npix) {
+      // its last work item has run: the slot's tables are free again; the
+      // image stays in the pool until nb_server_result fetches it
+      r.state = NB_REQ_DONE;
+      s->free_slots.push_back(r.slot);
+      r.slot = -1;
+      s->completed.push_back(r.id);
+    }
+  }
+  return NB_OK;
+}
+
+int nb_server_step(nb_server *s, double timeout_s, int *n_active) {
+  if (!s) return NB_EINVAL;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(s->device);
+  int rc = finish_in_flight(s, timeout_s);
+  if (rc == NB_OK) rc = admit(s);
+  if (rc == NB_OK) {
+    // round-robin cut of the active requests into work items
+    std::vector<Request *> act;
+    for (auto &kv : s->reqs)
+      if (kv.second.state == NB_REQ_RUNNING && kv.second.next < kv.second.npix)
+        act.push_back(&kv.second);
+    WorkList *wl = s->h_work;
+    int n = 0;
+    long long used = 0;
+    if (!act.empty()) {
+      size_t start = (size_t)(s->rr_cursor % (long long)act.size());
+      bool progress = true;
+      while (progress && used < s->budget && n < nbgb::kServeMaxItems) {
+        progress = false;
+        for (size_t j = 0; j < act.size() && n < nbgb::kServeMaxItems &&
+                           used < s->budget;
+             ++j) {
+          Request &r = *act[(start + j) % act.size()];
+          if (r.next >= r.npix) continue;
+          long long cnt = r.npix - r.next;
+          if (cnt > nbgb::kServeItemPixels) cnt = nbgb::kServeItemPixels;
+          wl->items[n].slot = r.slot;
+          wl->items[n].count = (int)cnt;
+          wl->items[n].first = r.next;
+          ++n;
+          r.next += cnt;
+          r.pending += cnt;
+          used += cnt * r.steps_per_pixel;
+          progress = true;
+        }
+      }
+      s->rr_cursor += 1;
+    }
+    wl->n = n;
+    if (n == 0 && !s->queue.empty()) {
+      // nothing runs and nothing can be admitted: the pool is held by
+      // completed images that were not fetched yet
+      rc = sfail(s, NB_ESTATE,
+                 "queued requests cannot be admitted: fetch completed "
+                 "results (nb_server_result) to free the image pool");
+    } else if (n > 0) {
+      cudaError_t e = cudaGraphLaunch(s->graph, s->stream);
+      if (e == cudaSuccess) e = cudaEventRecord(s->done_ev, s->stream);
+      if (e != cudaSuccess) {
+        rc = sfail(s, NB_ECUDA, "graph launch");
+      } else {
+        s->in_flight = true;
+        rc = finish_in_flight(s, timeout_s);
+      }
+    }
+  }
+  if (n_active) {
+    int na = 0;
+    for (auto &kv : s->reqs)
+      if (kv.second.state == NB_REQ_RUNNING) ++na;
+    *n_active = na + (int)s->queue.size();
+  }
+  cudaSetDevice(prev);
+  return rc;
+}
+
+int nb_server_completed(nb_server *s, long long *ids, int max_ids,
+                        int *n_out) {
+  if (!s || !n_out || (max_ids > 0 && !ids)) return NB_EINVAL;
+  int n = 0;
+  while (n < max_ids && !s->completed.empty()) {
+    ids[n++] = s->completed.front();
+    s->completed.erase(s->completed.begin());
+  }
+  *n_out = n;
+  return NB_OK;
+}
+
+int nb_server_state(nb_server *s, long long id, int *state) {
+  if (!s || !state) return NB_EINVAL;
+  auto it = s->reqs.find(id);
+  *state = it == s->reqs.end() ? NB_REQ_UNKNOWN : it->second.state;
+  return NB_OK;
+}
+
+int nb_server_result(nb_server *s, long long id, void *dst, size_t n_elems,
+                     int dtype, int on_device) {
+  if (!s || !dst) return NB_EINVAL;
+  auto it = s->reqs.find(id);
+  if (it == s->reqs.end()) return sfail(s, NB_EINVAL, "unknown request");
+  Request &r = it->second;
+  if (r.state != NB_REQ_DONE) return sfail(s, NB_ESTATE, "request not done");
+  if ((long long)n_elems != r.npix)
+    return sfail(s, NB_EINVAL, "n_elems differs from the ROI pixel count");
+  if (dtype != NB_DTYPE_F64)
+    return sfail(s, NB_EINVAL, "results are returned as float64");
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(s->device);
+  cudaError_t e = cudaMemcpyAsync(
+      dst, (double *)s->d_pool.p + r.pool_off, n_elems * sizeof(double),
+      on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+      s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  cudaSetDevice(prev);
+  if (e != cudaSuccess) return sfail(s, NB_ECUDA, "result copy");
+  pool_free(s, r.pool_off, r.npix);
+  s->reqs.erase(it);
+  return NB_OK;
+}
+
+int nb_server_info(const nb_server *s, long long *queued, long long *running,
+                   long long *done, long long *pool_free_bytes) {
+  if (!s) return NB_EINVAL;
+  long long q = (long long)s->queue.size(), ru = 0, d = 0, fr = 0;
+  for (auto &kv : s->reqs) {
+    if (kv.second.state == NB_REQ_RUNNING) ++ru;
+    if (kv.second.state == NB_REQ_DONE) ++d;
+  }
+  for (auto &kv : s->free_ranges) fr += kv.second;
+  if (queued) *queued = q;
+  if (running) *running = ru;
+  if (done) *done = d;
+  if (pool_free_bytes) *pool_free_bytes = fr * (long long)sizeof(double);
+  return NB_OK;
+}
+
+}  // extern "C"

@@ -16,7 +16,7 @@
 // One thread per pixel ("direct" variant); pixels are mapped in 16x8 tiles
 // so that a warp covers a 16x2 patch (neighbours share F_cell entries in
 // L1).  The rotated axes and the source table live in shared memory.
-#include "mixed_common.cuh"
+#include "mixed_pixel.cuh"
 
 namespace nbgb {
 
@@ -42,213 +42,10 @@ __global__ void __launch_bounds__(kTileThreads, 4)
   int q, s, f;
   if (!map_pixel(a, item, threadIdx.x, gp, q, s, f)) return;
   const DevPanel &P = a.panels[q];
-  const double px = P.px;
-  const int os = a.os;
-  const float kahn = a.kahn;
-  const float cutg = kGaussCut * 0.63f;
-  double total = 0.0;
+  const PixelView v{a.PM, a.S, a.u0h, a.u0l};
   unsigned evals = 0;  // terms evaluated (not skipped by the underflow cut)
-
-  for (int i = 0; i < os; ++i) {
-    for (int j = 0; j < os; ++j) {
-      for (int t = 0; t < a.T; ++t) {
-        // ---- per subpixel / layer: geometry
-        float df[3], vh[3], vl[3], omega, cap = 1.f;
-        if (MODE == 0) {
-          double cf = (f + (i + 0.5) / os) * px, cs = (s + (j + 0.5) / os) * px,
-                 cn = t * a.dt;
-          double pos[3], d[3];
-#pragma unroll
-          for (int c = 0; c < 3; ++c)
-            pos[c] = P.origin[c] + cf * P.fdir[c] + cs * P.sdir[c] +
-                     cn * P.ndir[c];
-          double R = sqrt(dot3d_m(pos, pos));
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            d[c] = pos[c] / R;
-            df[c] = (float)d[c];
-            double v = d[c] - a.i0[c];
-            vh[c] = (float)v;
-            vl[c] = (float)(v - (double)vh[c]);
-          }
-          omega = (float)(px * px * dot3d_m(P.ndir, pos) / (R * R * R));
-        } else {
-          float cf = (f + (i + 0.5f) / os) * (float)px,
-                cs = (s + (j + 0.5f) / os) * (float)px, cn = t * (float)a.dt;
-          float pos[3];
-#pragma unroll
-          for (int c = 0; c < 3; ++c)
-            pos[c] = (float)P.origin[c] + cf * (float)P.fdir[c] +
-                     cs * (float)P.sdir[c] + cn * (float)P.ndir[c];
-          float R = sqrtf(pos[0] * pos[0] + pos[1] * pos[1] + pos[2] * pos[2]);
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            df[c] = pos[c] / R;
-            vh[c] = df[c] - (float)a.i0[c];
-            vl[c] = 0.f;
-          }
-          float nd = pos[0] * (float)P.ndir[0] + pos[1] * (float)P.ndir[1] +
-                     pos[2] * (float)P.ndir[2];
-          omega = (float)px * (float)px * nd / (R * R * R);
-        }
-        if (a.thickness > 0.0) {
-          float rho = df[0] * (float)P.ndir[0] + df[1] * (float)P.ndir[1] +
-                      df[2] * (float)P.ndir[2];
-          float L = (float)a.atten * rho, dtf = (float)a.dt;
-          cap = expf(-t * dtf / L) - expf(-(t + 1) * dtf / L);
-        }
-        float scal = omega * cap;
-        if (!HASDIV) {
-          float c2 = df[0] * (float)a.i0[0] + df[1] * (float)a.i0[1] +
-                     df[2] * (float)a.i0[2];
-          float x = df[0] * (float)a.e0[0] + df[1] * (float)a.e0[1] +
-                    df[2] * (float)a.e0[2];
-          float y = df[0] * (float)a.b0[0] + df[1] * (float)a.b0[1] +
-                    df[2] * (float)a.b0[2];
-          scal *= 0.5f * (1.f + c2 * c2 - kahn * (x * x - y * y));
-        }
-        Kahan acc;
-        for (int pm = 0; pm < a.PM; ++pm) {
-          // ---- per (subpixel, phi x mosaic): G = A.(d - i0), r = u0 G - n0
-          const float *Ah = s_axh + pm * 9, *Al = s_axl + pm * 9;
-          float Gh[3], Gl[3], rh[3], rl[3], n0[3];
-#pragma unroll
-          for (int x = 0; x < 3; ++x) {
-            if (MODE == 0) {
-              ff_dot3(Ah + 3 * x, Al + 3 * x, vh, vl, Gh[x], Gl[x]);
-              float qh, qe;
-              two_prod(Gh[x], a.u0h, qh, qe);
-              float ql = fmaf(Gh[x], a.u0l, fmaf(Gl[x], a.u0h, qe));
-              n0[x] = rintf(qh);
-              two_sum(__fsub_rn(qh, n0[x]), ql, rh[x], rl[x]);
-              if (SHAPE == 1) {
-                // r_hi on a 2^-21 grid: r_hi - n is then exact for |n| < 7
-                float rq = __fmul_rn(rintf(__fmul_rn(rh[x], 2097152.f)),
-                                     1.f / 2097152.f);
-                rl[x] = rl[x] + __fsub_rn(rh[x], rq);
-                rh[x] = rq;
-              }
-            } else {
-              Gh[x] = Ah[3 * x] * vh[0] + Ah[3 * x + 1] * vh[1] +
-                      Ah[3 * x + 2] * vh[2];
-              Gl[x] = 0.f;
-              rh[x] = rl[x] = n0[x] = 0.f;
-            }
-          }
-          for (int k = 0; k < a.S; ++k) {
-            const float *src = s_src + k * SRC32_STRIDE;
-            float fr[3], frl[3];
-            int n[3];
-#pragma unroll
-            for (int x = 0; x < 3; ++x) {
-              float Eh = 0.f, El = 0.f;
-              if (HASDIV) {
-                size_t e = ((size_t)pm * a.S + k) * 3 + x;
-                Eh = __ldg(a.divh + e);
-                El = __ldg(a.divl + e);
-              }
-              float nf;
-              if (MODE == 0 && SHAPE == 1) {
-                // Gaussian: cheap offset for the cut test, refined below
-                float t = fmaf(Gh[x], src[SRC32_DH], rh[x]);
-                nf = rintf(t);
-                fr[x] = t - nf;
-                frl[x] = nf;  // keeps the shift for the refinement
-                if (HASDIV) {
-                  fr[x] -= Eh;
-                  float n2 = rintf(fr[x]);
-                  fr[x] -= n2;
-                  nf += n2;
-                }
-              } else if (MODE == 0) {
-                frac_ff<HASDIV>(Gh[x], Gl[x], rh[x], rl[x], src[SRC32_DH],
-                                src[SRC32_DL], Eh, El, fr[x], frl[x], nf);
-              } else {
-                // NB_F32: h = G u_k - E in plain FP32 (src[DL] holds u_k)
-                float h = Gh[x] * src[SRC32_DL] - Eh;
-                nf = rintf(h);
-                fr[x] = h - nf;
-                frl[x] = 0.f;
-              }
-              n[x] = __float2int_rn(n0[x] + nf) - a.hmin[x];
-            }
-            float fl2;
-            if (SHAPE == 1) {
-              float rad2 = a.N[0] * a.N[0] * fr[0] * fr[0];
-              rad2 = fmaf(a.N[1] * a.N[1], fr[1] * fr[1], rad2);
-              rad2 = fmaf(a.N[2] * a.N[2], fr[2] * fr[2], rad2);
-              if (rad2 > cutg) continue;
-              if (MODE == 0) {
-                // precise offset: G_hi d_hi + (r_q - n) in one rounding plus
-                // the small terms (and the divergence term, re-centred)
-#pragma unroll
-                for (int x = 0; x < 3; ++x) {
-                  float nfx = frl[x];
-                  float sx = fmaf(Gh[x], src[SRC32_DH], __fsub_rn(rh[x], nfx));
-                  float c = fmaf(Gh[x], src[SRC32_DL],
-                                 fmaf(Gl[x], src[SRC32_DH], rl[x]));
-                  fr[x] = sx + c;
-                  if (HASDIV) {
-                    // h - n0 - nfx - E, re-centred; the index follows it
-                    size_t e = ((size_t)pm * a.S + k) * 3 + x;
-                    fr[x] -= __ldg(a.divh + e) + __ldg(a.divl + e);
-                    float n2 = rintf(fr[x]);
-                    fr[x] -= n2;
-                    n[x] = __float2int_rn(n0[x] + nfx + n2) - a.hmin[x];
-                  }
-                }
-                rad2 = a.N[0] * a.N[0] * fr[0] * fr[0];
-                rad2 = fmaf(a.N[1] * a.N[1], fr[1] * fr[1], rad2);
-                rad2 = fmaf(a.N[2] * a.N[2], fr[2] * fr[2], rad2);
-              }
-              fl2 = a.N6 * expf(-2.f * rad2 * (1.f / 0.63f));
-              ++evals;
-            } else {
-              float nump = 1.f, denp = 1.f;
-#pragma unroll
-              for (int x = 0; x < 3; ++x) {
-                float yh, yr;
-                if (MODE == 0) {
-                  float ye;
-                  two_prod(a.N[x], fr[x], yh, ye);
-                  float yl = fmaf(a.N[x], frl[x], ye);
-                  yr = __fsub_rn(yh, rintf(yh)) + yl;
-                } else {
-                  yh = a.N[x] * fr[x];
-                  yr = yh - rintf(yh);
-                }
-                float num, den;
-                if (fabsf(fr[x]) < 1e-9f) {
-                  num = a.N[x];
-                  den = 1.f;
-                } else {
-                  num = sinpi_reduced(yr);
-                  den = sinpi_reduced(fr[x]);
-                }
-                nump *= num;
-                denp *= den;
-              }
-              float ratio = nump / denp;
-              fl2 = ratio * ratio;
-              ++evals;
-            }
-            float fc = fcell_f32<INTERP>(a, n, fr);
-            float w = src[SRC32_W];
-            if (HASDIV) {
-              const float *dir = src + SRC32_DIR, *ev = src + SRC32_E,
-                          *bv = src + SRC32_B;
-              float c2 = df[0] * dir[0] + df[1] * dir[1] + df[2] * dir[2];
-              float x = df[0] * ev[0] + df[1] * ev[1] + df[2] * ev[2];
-              float y = df[0] * bv[0] + df[1] * bv[1] + df[2] * bv[2];
-              w *= 0.5f * (1.f + c2 * c2 - kahn * (x * x - y * y));
-            }
-            acc.add(fc * fc * fl2 * w);
-          }
-        }
-        total += (double)scal * acc.value();
-      }
-    }
-  }
+  double total = mixed_pixel<SHAPE, INTERP, MODE, HASDIV>(
+      a, v, s_axh, s_axl, s_src, P, s, f, evals);
   a.image[gp] += a.prefactor * total;
   if (a.stats) warp_count(a.stats, evals);
 }

@@ -78,6 +78,25 @@ SIGNATURES = {
         ctypes.c_double, _vp, _vp, ctypes.c_int, _dp, ctypes.c_double,
         ctypes.c_double, _dp, _vp, _vp]),
     "nb_synchronize": (ctypes.c_int, [_vp]),
+    "nb_server_create": (ctypes.c_int, [
+        ctypes.POINTER(_vp), ctypes.c_int, _vp, ctypes.c_int,
+        ctypes.c_longlong, ctypes.c_longlong, ctypes.POINTER(NbPanel),
+        ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, _fp,
+        _ip, _ip, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+        ctypes.c_double, ctypes.c_double, _dp, ctypes.c_double,
+        ctypes.c_double, _dp]),
+    "nb_server_submit": (ctypes.c_int, [
+        _vp, _dp, _dp, ctypes.c_int, _dp, _dp, ctypes.c_int, ctypes.c_double,
+        ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _llp]),
+    "nb_server_step": (ctypes.c_int, [_vp, ctypes.c_double, _ip]),
+    "nb_server_completed": (ctypes.c_int, [_vp, _llp, ctypes.c_int, _ip]),
+    "nb_server_state": (ctypes.c_int, [_vp, ctypes.c_longlong, _ip]),
+    "nb_server_result": (ctypes.c_int, [_vp, ctypes.c_longlong, _vp,
+                                        ctypes.c_size_t, ctypes.c_int,
+                                        ctypes.c_int]),
+    "nb_server_info": (ctypes.c_int, [_vp, _llp, _llp, _llp, _llp]),
+    "nb_server_last_error": (ctypes.c_char_p, [_vp]),
+    "nb_server_free": (ctypes.c_int, [_vp]),
     "nb_free": (ctypes.c_int, [_vp]),
     "nb_last_error": (ctypes.c_char_p, [_vp]),
     "nb_version": (ctypes.c_char_p, []),
@@ -296,3 +315,121 @@ def simulate(shot, precision: str = "mixed", pixels=None,
         return img
     finally:
         sim.close()
+
+
+NB_REQ_UNKNOWN, NB_REQ_QUEUED, NB_REQ_RUNNING, NB_REQ_DONE = -1, 0, 1, 2
+
+
+def _check_srv(rc, lib, h):
+    if rc != NB_OK:
+        raise NbError(rc, lib.nb_server_last_error(h).decode() if h else "")
+
+
+class Server:
+    """Continuous-batching shot server (nb_server_*).  `shot` supplies the
+    resident state: its first panel, oversample, layers, F table, N,
+    beam direction, fluence and polarization."""
+
+    def __init__(self, shot, max_slots=64, pool_bytes=1 << 30,
+                 step_budget=0, device=0, stream=None):
+        self.lib = load()
+        h = _vp()
+        raw = 0 if stream is None else int(getattr(stream, "cuda_stream",
+                                                   stream))
+        p = panels_array(shot.panels[:1])
+        F = np.ascontiguousarray(shot.F, dtype=np.float32)
+        hmin = (ctypes.c_int * 3)(*[int(v) for v in shot.hkl_min])
+        hn = (ctypes.c_int * 3)(*[int(v) for v in F.shape])
+        d = _d(shot.dirs[0])
+        e = _d(shot.evec)
+        N = [float(v) for v in shot.ncells]
+        rc = self.lib.nb_server_create(
+            ctypes.byref(h), int(device), _vp(raw), int(max_slots),
+            int(pool_bytes), int(step_budget), p, int(shot.oversample),
+            int(shot.n_layers), float(shot.thickness_m), float(shot.atten_m),
+            F.ctypes.data_as(_fp), ctypes.cast(hmin, _ip),
+            ctypes.cast(hn, _ip), int(shot.interp), float(shot.default_F),
+            N[0], N[1], N[2], _ptr(d), float(shot.fluence), float(shot.kahn),
+            _ptr(e))
+        if rc != NB_OK:
+            raise NbError(rc, "nb_server_create")
+        self.h = h
+        self.npix_of = {}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.nb_server_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, axes, umats, lambdas, weights, scale, roi):
+        f0, s0, nf, ns = [int(v) for v in roi]
+        axes, umats = _d(axes).ravel(), _d(umats).ravel()
+        lam, w = _d(lambdas), _d(weights)
+        rid = ctypes.c_longlong()
+        _check_srv(self.lib.nb_server_submit(
+            self.h, _ptr(axes), _ptr(umats), int(umats.size // 9),
+            _ptr(lam), _ptr(w), int(lam.size), float(scale), f0, s0, nf, ns,
+            ctypes.byref(rid)), self.lib, self.h)
+        self.npix_of[rid.value] = nf * ns
+        return rid.value
+
+    def step(self, timeout_s=60.0):
+        n = ctypes.c_int()
+        _check_srv(self.lib.nb_server_step(self.h, float(timeout_s),
+                                           ctypes.byref(n)), self.lib, self.h)
+        return n.value
+
+    def completed(self, max_ids=4096):
+        ids = (ctypes.c_longlong * max_ids)()
+        n = ctypes.c_int()
+        _check_srv(self.lib.nb_server_completed(
+            self.h, ctypes.cast(ids, _llp), max_ids, ctypes.byref(n)),
+            self.lib, self.h)
+        return [ids[i] for i in range(n.value)]
+
+    def state(self, rid):
+        st = ctypes.c_int()
+        _check_srv(self.lib.nb_server_state(self.h, int(rid),
+                                            ctypes.byref(st)),
+                   self.lib, self.h)
+        return st.value
+
+    def result(self, rid, out=None):
+        n = self.npix_of[rid]
+        if out is None:
+            out = np.empty(n, dtype=np.float64)
+        _check_srv(self.lib.nb_server_result(
+            self.h, int(rid), out.ctypes.data_as(_vp), n, NB_DTYPE_F64, 0),
+            self.lib, self.h)
+        del self.npix_of[rid]
+        return out
+
+    def info(self):
+        v = [ctypes.c_longlong() for _ in range(4)]
+        _check_srv(self.lib.nb_server_info(self.h, *[ctypes.byref(x)
+                                                     for x in v]),
+                   self.lib, self.h)
+        return dict(zip(("queued", "running", "done", "pool_free_bytes"),
+                        [x.value for x in v]))
+
+    def run_all(self, timeout_s=60.0, fetch=False):
+        """Step until nothing is queued or running.  Returns the completed
+        ids in completion order, or with fetch=True a dict id -> image
+        (fetching as they complete, which frees their pool memory)."""
+        done, images = [], {}
+        while True:
+            active = self.step(timeout_s)
+            new = self.completed()
+            done += new
+            if fetch:
+                for rid in new:
+                    images[rid] = self.result(rid)
+            if active == 0:
+                break
+        return images if fetch else done

@@ -373,3 +373,88 @@ def strided_rows(shot: Shot, every: int) -> np.ndarray:
             out.append(base + s * p.nfast + np.arange(p.nfast))
         base += p.npix
     return np.concatenate(out).astype(np.int64)
+
+
+# --------------------------------------------------------------- serving
+
+
+@dataclasses.dataclass
+class ShotRequest:
+    """One served shot: its own orientation, mosaic domains, spectrum and
+    detector region of interest (f0, s0, nfast, nslow)."""
+    axes: np.ndarray
+    umats: np.ndarray
+    lambdas: np.ndarray
+    weights: np.ndarray
+    scale: float
+    roi: tuple
+
+    @property
+    def npix(self) -> int:
+        return self.roi[2] * self.roi[3]
+
+    @property
+    def pixel_steps(self) -> int:
+        return self.npix * self.umats.shape[0] * self.lambdas.shape[0]
+
+
+def serving_detector_shot(seed: int = 4) -> Shot:
+    """Resident state of the shot server: the 3072x3072 detector (0.1 mm at
+    100 mm, oversample 1, one layer), Na=Nb=Nc=25 Gaussian, tricubic F on
+    [-60,60]^3, beam along z, Kahn 0.99; crystal and spectrum per request."""
+    rng = np.random.default_rng(seed)
+    F = structure_factors(rng, 60)
+    dirs, lam, w = gaussian_spectrum(1, 9.5, 0.005)
+    return _base_shot(
+        axes=orthorhombic_axes(79.0, 79.0, 38.0, np.eye(3)),
+        umats=identity_umats(1), ncells=np.array([25.0, 25.0, 25.0]),
+        shape=SHAPE_GAUSS, F=F, hkl_min=np.array([-60, -60, -60],
+                                                 dtype=np.int32),
+        interp=INTERP_TRICUBIC, dirs=dirs, lambdas=lam, weights=w,
+        kahn=0.99, panels=[flat_detector(3072, 3072, 1.0e-4, 0.1)])
+
+
+def serving_requests(n: int, seed: int = 5, max_src: int = 100,
+                     max_mosaic: int = 50, min_pix: float = 1e3,
+                     max_pix: float = 4e6, det: int = 3072):
+    """n requests: random orientation of the 79x79x38 cell, S ~ U{1..max_src}
+    sources on the 0.5 % spectrum at 9.5 keV, M ~ U{1..max_mosaic} domains
+    (0.05 deg), an ROI of log-uniform area in [min_pix, max_pix] pixels with
+    aspect ratio in [1/2, 2], placed uniformly on the det x det detector."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n):
+        U = random_orientation(rng)
+        S = int(rng.integers(1, max_src + 1))
+        M = int(rng.integers(1, max_mosaic + 1))
+        area = math.exp(rng.uniform(math.log(min_pix), math.log(max_pix)))
+        aspect = math.exp(rng.uniform(math.log(0.5), math.log(2.0)))
+        nf = int(max(1, min(det, round(math.sqrt(area * aspect)))))
+        ns = int(max(1, min(det, round(area / nf))))
+        f0 = int(rng.integers(0, det - nf + 1))
+        s0 = int(rng.integers(0, det - ns + 1))
+        _, lam, w = gaussian_spectrum(S, 9.5, 0.005)
+        out.append(ShotRequest(axes=orthorhombic_axes(79.0, 79.0, 38.0, U),
+                               umats=mosaic_umats(rng, M, 0.05),
+                               lambdas=lam, weights=w, scale=1.0,
+                               roi=(f0, s0, nf, ns)))
+    return out
+
+
+def poisson_arrivals(n: int, rate: float, seed: int = 6) -> np.ndarray:
+    """Arrival times (s) of a Poisson process of the given rate (1/s)."""
+    rng = np.random.default_rng(seed)
+    return np.cumsum(rng.exponential(1.0 / rate, size=n))
+
+
+def request_shot(base: Shot, req: ShotRequest) -> Shot:
+    """The stand-alone Shot of a served request (its ROI as the panel)."""
+    s = base.copy()
+    s.axes = req.axes
+    s.umats = req.umats
+    s.lambdas = req.lambdas
+    s.weights = req.weights
+    s.dirs = np.repeat(base.dirs[:1], len(req.lambdas), axis=0)
+    s.scale = req.scale
+    f0, s0, nf, ns = req.roi
+    return shrink(s, nf, ns, f0, s0)
