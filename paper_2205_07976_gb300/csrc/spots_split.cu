@@ -29,6 +29,9 @@ constexpr int kSplitThreads = kSplitWarps * 32;
 constexpr int kRing = 64;
 constexpr int kMaxUnits = 32;
 constexpr int kUnitFloats = 10;  // vh[3], vl[3], scal, df[3]
+constexpr int kStateStride = 20;  // per-lane item state: G, r, n0, scal
+constexpr int kCandRing = 64;     // per-warp ring of (lane, source block)
+constexpr int kSrcBlock = 8;      // sources per pruning block
 
 struct SplitRing {
   float f[3][kRing];
@@ -62,12 +65,29 @@ __global__ void __launch_bounds__(kSplitThreads, 6)
   SplitRing *rings =
       reinterpret_cast<SplitRing *>(s_unit + kSplitWarps * kMaxUnits *
                                                  kUnitFloats);
+  float *s_state = reinterpret_cast<float *>(rings + kSplitWarps);
+  int *s_cring =
+      reinterpret_cast<int *>(s_state + kSplitWarps * 32 * kStateStride);
+  float *s_blk = reinterpret_cast<float *>(s_cring + kSplitWarps * kCandRing);
+  const int nblk = (S + kSrcBlock - 1) / kSrcBlock;
   for (int i = threadIdx.x; i < PM * 9; i += blockDim.x) {
     s_axh[i] = a.axh[i];
     s_axl[i] = a.axl[i];
   }
   for (int i = threadIdx.x; i < S * SRC32_STRIDE; i += blockDim.x)
     s_src[i] = a.src32[i];
+  __syncthreads();
+  // delta_hi range of every block of kSrcBlock sources (the pruning test)
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
+    float mn = 3.0e38f, mx = -3.0e38f;
+    for (int k = b * kSrcBlock; k < S && k < (b + 1) * kSrcBlock; ++k) {
+      float d = s_src[k * SRC32_STRIDE + SRC32_DH];
+      mn = fminf(mn, d);
+      mx = fmaxf(mx, d);
+    }
+    s_blk[2 * b] = mn;
+    s_blk[2 * b + 1] = mx;
+  }
   __syncthreads();
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -78,6 +98,13 @@ __global__ void __launch_bounds__(kSplitThreads, 6)
   const float cutg = kGaussCut * 0.63f;
   const float kahn = a.kahn;
   const float N2[3] = {a.N[0] * a.N[0], a.N[1] * a.N[1], a.N[2] * a.N[2]};
+  // |f_x| <= sqrt(cut) / N_x for every surviving term (with a margin for
+  // the rounding of the exponent sum)
+  const float cmarg[3] = {sqrtf(cutg) / a.N[0] * 1.0001f,
+                          sqrtf(cutg) / a.N[1] * 1.0001f,
+                          sqrtf(cutg) / a.N[2] * 1.0001f};
+  float *st = s_state + warp * 32 * kStateStride;
+  int *cring = s_cring + warp * kCandRing;
   const long long n_work = a.pixlist ? a.n_list : a.npix;
   unsigned long long evals = 0;  // terms evaluated by this warp
 
@@ -157,67 +184,159 @@ __global__ void __launch_bounds__(kSplitThreads, 6)
         rq[x] = __fmul_rn(rintf(__fmul_rn(rh, 2097152.f)), 1.f / 2097152.f);
         rl[x] = rl0 + __fsub_rn(rh, rq[x]);
       }
-      for (int k = 0; k < S; ++k) {
-        const float *src = s_src + k * SRC32_STRIDE;
-        const float dh = src[SRC32_DH];
-        // cut test on the cheap offset t - rint(t) (error ~1 ulp of t, which
-        // only moves terms ~1e-38 below the peak across the cut)
-        float tq[3], nf[3], fr[3];
+      if (HASDIV) {
+        for (int k = 0; k < S; ++k) {
+          const float *src = s_src + k * SRC32_STRIDE;
+          const float dh = src[SRC32_DH];
+          // cut test on the cheap offset t - rint(t) (error ~1 ulp of t, which
+          // only moves terms ~1e-38 below the peak across the cut)
+          float tq[3], nf[3], fr[3];
+#pragma unroll
+          for (int x = 0; x < 3; ++x) {
+            tq[x] = fmaf(Gh[x], dh, rq[x]);
+            if (HASDIV && valid) tq[x] -= __ldg(a.divh + ((size_t)pm * S + k) * 3 + x);
+            nf[x] = rintf(tq[x]);
+            fr[x] = tq[x] - nf[x];
+          }
+          float rad2 = N2[0] * fr[0] * fr[0];
+          rad2 = fmaf(N2[1] * fr[1], fr[1], rad2);
+          rad2 = fmaf(N2[2] * fr[2], fr[2], rad2);
+          bool hit = valid && rad2 <= cutg;
+          unsigned m = __ballot_sync(0xffffffffu, hit);
+          if (m == 0u) continue;
+          if (hit) {
+            // the precise offset: G_hi d_hi + (r_q - n) in one rounding (r_q
+            // on a 2^-21 grid makes r_q - n exact) plus the small terms
+            const float dl = src[SRC32_DL];
+#pragma unroll
+            for (int x = 0; x < 3; ++x) {
+              float sx = fmaf(Gh[x], dh, __fsub_rn(rq[x], nf[x]));
+              float c = fmaf(Gh[x], dl, fmaf(Gl[x], dh, rl[x]));
+              fr[x] = sx + c;
+              if (HASDIV) {
+                // the divergence term moves h after the rint: re-centre
+                size_t e = ((size_t)pm * S + k) * 3 + x;
+                fr[x] -= __ldg(a.divh + e) + __ldg(a.divl + e);
+                float n2 = rintf(fr[x]);
+                fr[x] -= n2;
+                nf[x] += n2;
+              }
+            }
+            int e = (tail + __popc(m & lt_mask)) & (kRing - 1);
+            float w = src[SRC32_W] * scal;
+            if (HASDIV) {
+              const float *df = ud + 7, *dir = src + SRC32_DIR,
+                          *ev = src + SRC32_E, *bv = src + SRC32_B;
+              float c2 = df[0] * dir[0] + df[1] * dir[1] + df[2] * dir[2];
+              float x = df[0] * ev[0] + df[1] * ev[1] + df[2] * ev[2];
+              float y = df[0] * bv[0] + df[1] * bv[1] + df[2] * bv[2];
+              w *= 0.5f * (1.f + c2 * c2 - kahn * (x * x - y * y));
+            }
+#pragma unroll
+            for (int x = 0; x < 3; ++x) {
+              q.f[x][e] = fr[x];
+              q.n[x][e] = __float2int_rn(n0[x] + nf[x]) - a.hmin[x];
+            }
+            q.w[e] = w;
+          }
+          tail += __popc(m);
+          if (tail - head >= 32) {
+            __syncwarp();
+            eval_term<INTERP>(a, q, (head + lane) & (kRing - 1), acc);
+            head += 32;
+            __syncwarp();
+          }
+        }
+      } else {
+        // ---- pruned scan: h_x = G_x delta + r_x is linear in delta, so a
+        // block of sources whose delta range [dmin, dmax] keeps some axis
+        // farther than sqrt(cut)/N_x from every integer holds no surviving
+        // term.  Surviving (lane, block) pairs go into a ring; the warp
+        // then runs 4 blocks x 8 sources = 32 steps at a time.
+        float *my = st + lane * kStateStride;
 #pragma unroll
         for (int x = 0; x < 3; ++x) {
-          tq[x] = fmaf(Gh[x], dh, rq[x]);
-          if (HASDIV && valid) tq[x] -= __ldg(a.divh + ((size_t)pm * S + k) * 3 + x);
-          nf[x] = rintf(tq[x]);
-          fr[x] = tq[x] - nf[x];
+          my[x] = Gh[x];
+          my[3 + x] = Gl[x];
+          my[6 + x] = rq[x];
+          my[9 + x] = rl[x];
+          my[12 + x] = n0[x];
         }
-        float rad2 = N2[0] * fr[0] * fr[0];
-        rad2 = fmaf(N2[1] * fr[1], fr[1], rad2);
-        rad2 = fmaf(N2[2] * fr[2], fr[2], rad2);
-        bool hit = valid && rad2 <= cutg;
-        unsigned m = __ballot_sync(0xffffffffu, hit);
-        if (m == 0u) continue;
-        if (hit) {
-          // the precise offset: G_hi d_hi + (r_q - n) in one rounding (r_q
-          // on a 2^-21 grid makes r_q - n exact) plus the small terms
-          const float dl = src[SRC32_DL];
+        my[15] = scal;
+        __syncwarp();
+        int ch = 0, ct = 0;
+        auto run_cands = [&](int nc) {
+          const int ci = lane >> 3, kk = lane & 7;
+          bool ok = ci < nc;
+          int ent = ok ? cring[(ch + ci) & (kCandRing - 1)] : 0;
+          int own = ent >> 16, b = ent & 0xffff;
+          int k = b * kSrcBlock + kk;
+          ok = ok && k < S;
+          const float *o = st + own * kStateStride;
+          const float *src = s_src + (ok ? k : 0) * SRC32_STRIDE;
+          const float dh = src[SRC32_DH];
+          float fr[3], nf[3];
 #pragma unroll
           for (int x = 0; x < 3; ++x) {
-            float sx = fmaf(Gh[x], dh, __fsub_rn(rq[x], nf[x]));
-            float c = fmaf(Gh[x], dl, fmaf(Gl[x], dh, rl[x]));
-            fr[x] = sx + c;
-            if (HASDIV) {
-              // the divergence term moves h after the rint: re-centre
-              size_t e = ((size_t)pm * S + k) * 3 + x;
-              fr[x] -= __ldg(a.divh + e) + __ldg(a.divl + e);
-              float n2 = rintf(fr[x]);
-              fr[x] -= n2;
-              nf[x] += n2;
+            float tq = fmaf(o[x], dh, o[6 + x]);
+            nf[x] = rintf(tq);
+            fr[x] = tq - nf[x];
+          }
+          float rad2 = N2[0] * fr[0] * fr[0];
+          rad2 = fmaf(N2[1] * fr[1], fr[1], rad2);
+          rad2 = fmaf(N2[2] * fr[2], fr[2], rad2);
+          bool hit = ok && rad2 <= cutg;
+          unsigned m = __ballot_sync(0xffffffffu, hit);
+          if (m == 0u) return;
+          if (hit) {
+            const float dl = src[SRC32_DL];
+            int e = (tail + __popc(m & lt_mask)) & (kRing - 1);
+#pragma unroll
+            for (int x = 0; x < 3; ++x) {
+              float sx = fmaf(o[x], dh, __fsub_rn(o[6 + x], nf[x]));
+              float c = fmaf(o[x], dl, fmaf(o[3 + x], dh, o[9 + x]));
+              q.f[x][e] = sx + c;
+              q.n[x][e] = __float2int_rn(o[12 + x] + nf[x]) - a.hmin[x];
+            }
+            q.w[e] = src[SRC32_W] * o[15];
+          }
+          tail += __popc(m);
+          if (tail - head >= 32) {
+            __syncwarp();
+            eval_term<INTERP>(a, q, (head + lane) & (kRing - 1), acc);
+            head += 32;
+            __syncwarp();
+          }
+        };
+        for (int b = 0; b < nblk; ++b) {
+          bool pass = false;
+          if (valid) {
+            const float dmn = s_blk[2 * b], dmx = s_blk[2 * b + 1];
+            pass = true;
+#pragma unroll
+            for (int x = 0; x < 3; ++x) {
+              float u = fmaf(Gh[x], dmn, rq[x]), v = fmaf(Gh[x], dmx, rq[x]);
+              float lo = fminf(u, v) - cmarg[x], hi = fmaxf(u, v) + cmarg[x];
+              pass = pass && floorf(hi) >= ceilf(lo);
             }
           }
-          int e = (tail + __popc(m & lt_mask)) & (kRing - 1);
-          float w = src[SRC32_W] * scal;
-          if (HASDIV) {
-            const float *df = ud + 7, *dir = src + SRC32_DIR,
-                        *ev = src + SRC32_E, *bv = src + SRC32_B;
-            float c2 = df[0] * dir[0] + df[1] * dir[1] + df[2] * dir[2];
-            float x = df[0] * ev[0] + df[1] * ev[1] + df[2] * ev[2];
-            float y = df[0] * bv[0] + df[1] * bv[1] + df[2] * bv[2];
-            w *= 0.5f * (1.f + c2 * c2 - kahn * (x * x - y * y));
-          }
-#pragma unroll
-          for (int x = 0; x < 3; ++x) {
-            q.f[x][e] = fr[x];
-            q.n[x][e] = __float2int_rn(n0[x] + nf[x]) - a.hmin[x];
-          }
-          q.w[e] = w;
-        }
-        tail += __popc(m);
-        if (tail - head >= 32) {
+          unsigned m = __ballot_sync(0xffffffffu, pass);
+          if (m == 0u) continue;
+          if (pass)
+            cring[(ct + __popc(m & lt_mask)) & (kCandRing - 1)] =
+                (lane << 16) | b;
+          ct += __popc(m);
           __syncwarp();
-          eval_term<INTERP>(a, q, (head + lane) & (kRing - 1), acc);
-          head += 32;
-          __syncwarp();
+          while (ct - ch >= 4) {
+            run_cands(4);
+            ch += 4;
+          }
         }
+        if (ct > ch) {
+          run_cands(ct - ch);
+          ch = ct;
+        }
+        __syncwarp();  // the state area is rewritten by the next round
       }
     }
     __syncwarp();
@@ -237,9 +356,13 @@ __global__ void __launch_bounds__(kSplitThreads, 6)
 }
 
 size_t split_smem_bytes(const SpotArgs &a) {
+  int nblk = (a.S + kSrcBlock - 1) / kSrcBlock;
   return (size_t)(2 * a.PM * 9 + a.S * SRC32_STRIDE +
                   kSplitWarps * kMaxUnits * kUnitFloats) * sizeof(float) +
-         kSplitWarps * sizeof(SplitRing);
+         kSplitWarps * sizeof(SplitRing) +
+         (size_t)kSplitWarps * 32 * kStateStride * sizeof(float) +
+         (size_t)kSplitWarps * kCandRing * sizeof(int) +
+         (size_t)2 * nblk * sizeof(float);
 }
 
 bool split_supported(const SpotArgs &a) {
