@@ -76,10 +76,29 @@ __device__ __forceinline__ float fcell_f32(const SpotArgs &a, const int n[3],
       lagrange4(x[0], wh);
       lagrange4(x[1], wk);
       lagrange4(x[2], wl);
-      const float *base =
-          a.F + ((long long)(fl[0] - 1) * a.hn[1] + (fl[1] - 1)) * a.hn[2] +
+      const long long off =
+          ((long long)(fl[0] - 1) * a.hn[1] + (fl[1] - 1)) * a.hn[2] +
           (fl[2] - 1);
       float sum = 0.f;
+      if (a.F4) {
+        const float4 *b4 = a.F4 + off;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          float si = 0.f;
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            float4 r = __ldg(b4 + ((long long)i * a.hn[1] + j) * a.hn[2]);
+            float sj = wl[0] * r.x;
+            sj = fmaf(wl[1], r.y, sj);
+            sj = fmaf(wl[2], r.z, sj);
+            sj = fmaf(wl[3], r.w, sj);
+            si = fmaf(wk[j], sj, si);
+          }
+          sum = fmaf(wh[i], si, sum);
+        }
+        return sum;
+      }
+      const float *base = a.F + off;
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         float si = 0.f;

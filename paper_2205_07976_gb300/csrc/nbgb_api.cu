@@ -92,7 +92,8 @@ struct nb_sim {
   bool have_params = false;
   double pU[9] = {0}, pcell[3] = {0}, prot[3] = {0};
   double daxes[6][9];  // d(lab axes)/d(tx, ty, tz, a, b, c)
-  DevBuf d_dax, d_part, d_grad;
+  DevBuf d_dax, d_part, d_grad, d_F4;
+  bool F4_valid = false;
   int has_div = 0;
   double u0 = 0;
   bool tables_dirty = true;
@@ -429,6 +430,7 @@ static void fill_args(const nb_sim *s, SpotArgs &a) {
   a.shape = s->shape;
   a.interp = s->interp;
   a.F = (const float *)s->d_F.p;
+  a.F4 = s->F4_valid ? (const float4 *)s->d_F4.p : nullptr;
   a.defF = (float)s->defF;
   a.defF64 = s->defF;
   a.S = s->n_src;
@@ -494,7 +496,7 @@ int nb_free(nb_sim *sim) {
                       &sim->d_divh,   &sim->d_divl,  &sim->d_F,
                       &sim->d_image,  &sim->d_list,  &sim->d_tmp,
                       &sim->d_stats,  &sim->d_work,  &sim->d_dax,
-                      &sim->d_part,   &sim->d_grad};
+                      &sim->d_part,   &sim->d_grad,  &sim->d_F4};
     for (DevBuf *b : bufs) b->release();
   }
   delete sim;
@@ -561,6 +563,7 @@ int nb_set_crystal(nb_sim *s, const double axes[9], const double *umats,
     s->interp = interp;
     s->defF = default_F;
     s->have_F = true;
+    s->F4_valid = false;
   } else {
     if (interp == NB_INTERP_NEAREST || interp == NB_INTERP_TRICUBIC)
       s->interp = interp;
@@ -716,11 +719,28 @@ int nb_set_detector(nb_sim *s, int n_panels, const nb_panel *panels,
   return NB_OK;
 }
 
+// 16-byte rows of the F table for tricubic lookups in the FP32 forms
+// (4x the table's memory; skipped if that allocation fails)
+static void ensure_sliding_table(nb_sim *s) {
+  if (s->F4_valid || s->interp != NB_INTERP_TRICUBIC ||
+      s->precision == NB_F64)
+    return;
+  size_t n = (size_t)s->hn[0] * s->hn[1] * s->hn[2];
+  if (s->d_F4.ensure(n * sizeof(float4)) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  if (nbgb::build_sliding_table((const float *)s->d_F.p, s->hn,
+                                (float4 *)s->d_F4.p, s->stream) == cudaSuccess)
+    s->F4_valid = true;
+}
+
 static int launch(nb_sim *s, const long long *dev_list, long long n_list) {
   if (!s->have_crystal || !s->have_beam || !s->have_det || !s->have_F)
     return fail(s, NB_ESTATE, "crystal, beam and detector must be set first");
   int rc = upload_tables(s);
   if (rc != NB_OK) return rc;
+  ensure_sliding_table(s);
   SpotArgs a;
   fill_args(s, a);
   a.pixlist = dev_list;

@@ -68,6 +68,9 @@ struct SpotArgs {
   float N6;  // (Na Nb Nc)^2
   int shape, interp;
   const float *F;
+  // optional copy of F for tricubic lookups: F4[i][j][l] holds
+  // F[i][j][l..l+3] (zero past the end), one 16-byte load per stencil row
+  const float4 *F4;
   int hmin[3], hn[3];
   float defF;
   double defF64;
@@ -223,6 +226,8 @@ void rotated_axes_table(const double *lab, const double *umats, int n_mosaic,
                         const double *spindle, std::vector<double> &ax);
 
 cudaError_t launch_spots_f64(const SpotArgs &a, cudaStream_t st);
+cudaError_t build_sliding_table(const float *F, const int hn[3], float4 *F4,
+                                cudaStream_t st);
 size_t adjoint_smem_bytes(const SpotArgs &a);
 long long adjoint_blocks(const SpotArgs &a);
 int loss_blocks(long long n);

@@ -161,7 +161,7 @@ struct nb_server {
   int hmin[3], hn[3];
   double defF = 0;
   double fluence = 0, kahn = 0, evec[3] = {1, 0, 0}, dir[3] = {0, 0, 1};
-  Buf d_F, d_panel, d_slots, d_pool, d_work, d_counter;
+  Buf d_F, d_F4, d_panel, d_slots, d_pool, d_work, d_counter;
   WorkList *h_work = nullptr;  // pinned staging of the work list
   nbgb::SpotArgs base;
   cudaGraphExec_t graph = nullptr;
@@ -380,6 +380,15 @@ int nb_server_create(nb_server **out, int device, void *cuda_stream,
     a.shape = NB_SHAPE_GAUSS;
     a.interp = interp;
     a.F = (const float *)s->d_F.p;
+    if (interp == NB_INTERP_TRICUBIC && s->d_F4.alloc(nF * sizeof(float4)) ==
+                                            cudaSuccess &&
+        nbgb::build_sliding_table((const float *)s->d_F.p, s->hn,
+                                  (float4 *)s->d_F4.p, s->stream) ==
+            cudaSuccess) {
+      cudaStreamSynchronize(s->stream);
+      a.F4 = (const float4 *)s->d_F4.p;
+    }
+    cudaGetLastError();
     a.defF = (float)default_F;
     a.defF64 = default_F;
     a.kahn = (float)kahn_K;
@@ -419,8 +428,8 @@ int nb_server_free(nb_server *s) {
   if (s->h_work) cudaFreeHost(s->h_work);
   if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
   {
-    Buf *bufs[] = {&s->d_F, &s->d_panel, &s->d_slots, &s->d_pool, &s->d_work,
-                   &s->d_counter};
+    Buf *bufs[] = {&s->d_F,    &s->d_F4,   &s->d_panel,  &s->d_slots,
+                   &s->d_pool, &s->d_work, &s->d_counter};
     for (Buf *b : bufs) {
       if (b->p) cudaFree(b->p);
       b->p = nullptr;

@@ -67,6 +67,28 @@ static void (*pick_mode(const SpotArgs &a))(SpotArgs) {
   }
 }
 
+__global__ void sliding_table_kernel(const float *F, int nl, long long n,
+                                     float4 *F4) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    int l = (int)(i % nl);
+    float4 v;
+    v.x = F[i];
+    v.y = l + 1 < nl ? F[i + 1] : 0.f;
+    v.z = l + 2 < nl ? F[i + 2] : 0.f;
+    v.w = l + 3 < nl ? F[i + 3] : 0.f;
+    F4[i] = v;
+  }
+}
+
+cudaError_t build_sliding_table(const float *F, const int hn[3], float4 *F4,
+                                cudaStream_t st) {
+  long long n = (long long)hn[0] * hn[1] * hn[2];
+  if (n <= 0) return cudaSuccess;
+  sliding_table_kernel<<<1216, 256, 0, st>>>(F, hn[2], n, F4);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_spots_mixed(const SpotArgs &a, int precision,
                                cudaStream_t st) {
   size_t smem = (size_t)(2 * a.PM * 9 + a.S * SRC32_STRIDE) * sizeof(float);

@@ -29,7 +29,8 @@ constexpr int kSplitThreads = kSplitWarps * 32;
 constexpr int kRing = 64;
 constexpr int kMaxUnits = 32;
 constexpr int kUnitFloats = 10;  // vh[3], vl[3], scal, df[3]
-constexpr int kStateStride = 20;  // per-lane item state: G, r, n0, scal
+constexpr int kStateStride = 17;  // per-lane item state: G, r, n0, scal
+                                  // (odd: distinct owners hit distinct banks)
 constexpr int kCandRing = 64;     // per-warp ring of (lane, source block)
 constexpr int kSrcBlock = 8;      // sources per pruning block
 
@@ -70,6 +71,7 @@ __global__ void __launch_bounds__(kSplitThreads, 6)
       reinterpret_cast<int *>(s_state + kSplitWarps * 32 * kStateStride);
   float *s_blk = reinterpret_cast<float *>(s_cring + kSplitWarps * kCandRing);
   const int nblk = (S + kSrcBlock - 1) / kSrcBlock;
+  float *s_dh = s_blk + 2 * nblk;  // delta_hi of every source, contiguous
   for (int i = threadIdx.x; i < PM * 9; i += blockDim.x) {
     s_axh[i] = a.axh[i];
     s_axl[i] = a.axl[i];
@@ -88,6 +90,8 @@ __global__ void __launch_bounds__(kSplitThreads, 6)
     s_blk[2 * b] = mn;
     s_blk[2 * b + 1] = mx;
   }
+  for (int k = threadIdx.x; k < S; k += blockDim.x)
+    s_dh[k] = s_src[k * SRC32_STRIDE + SRC32_DH];
   __syncthreads();
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -131,28 +135,39 @@ __global__ void __launch_bounds__(kSplitThreads, 6)
       for (int c = 0; c < 3; ++c)
         pos[c] = P.origin[c] + cf * P.fdir[c] + cs * P.sdir[c] +
                  cn * P.ndir[c];
+      // FP64 only where h needs it: one reciprocal of |P|, d = P / |P|
       double R = sqrt(dot3d_m(pos, pos));
+      double inv = 1.0 / R;
       float *ud = unit + u * kUnitFloats;
+      float df[3];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        d[c] = pos[c] / R;
+        d[c] = pos[c] * inv;
         double v = d[c] - a.i0[c];
         float vh = (float)v;
         ud[c] = vh;
         ud[3 + c] = (float)(v - (double)vh);
-        ud[7 + c] = (float)d[c];
+        df[c] = (float)d[c];
+        ud[7 + c] = df[c];
       }
-      float omega = (float)(px * px * dot3d_m(P.ndir, pos) / (R * R * R));
+      float invf = (float)inv;
+      float omega = (float)(px * px) * (float)dot3d_m(P.ndir, pos) * invf *
+                    invf * invf;
       float cap = 1.f;
       if (a.thickness > 0.0) {
-        float rho = (float)dot3d_m(d, P.ndir);
+        float rho = df[0] * (float)P.ndir[0] + df[1] * (float)P.ndir[1] +
+                    df[2] * (float)P.ndir[2];
         float L = (float)a.atten * rho, dtf = (float)a.dt;
         cap = expf(-t * dtf / L) - expf(-(t + 1) * dtf / L);
       }
       float scal = omega * cap;
       if (!HASDIV) {
-        float c2 = (float)dot3d_m(d, a.i0), x = (float)dot3d_m(d, a.e0),
-              y = (float)dot3d_m(d, a.b0);
+        float c2 = df[0] * (float)a.i0[0] + df[1] * (float)a.i0[1] +
+                   df[2] * (float)a.i0[2];
+        float x = df[0] * (float)a.e0[0] + df[1] * (float)a.e0[1] +
+                  df[2] * (float)a.e0[2];
+        float y = df[0] * (float)a.b0[0] + df[1] * (float)a.b0[1] +
+                  df[2] * (float)a.b0[2];
         scal *= 0.5f * (1.f + c2 * c2 - kahn * (x * x - y * y));
       }
       ud[6] = scal;
@@ -273,8 +288,7 @@ __global__ void __launch_bounds__(kSplitThreads, 6)
           int k = b * kSrcBlock + kk;
           ok = ok && k < S;
           const float *o = st + own * kStateStride;
-          const float *src = s_src + (ok ? k : 0) * SRC32_STRIDE;
-          const float dh = src[SRC32_DH];
+          const float dh = s_dh[ok ? k : 0];
           float fr[3], nf[3];
 #pragma unroll
           for (int x = 0; x < 3; ++x) {
@@ -289,6 +303,7 @@ __global__ void __launch_bounds__(kSplitThreads, 6)
           unsigned m = __ballot_sync(0xffffffffu, hit);
           if (m == 0u) return;
           if (hit) {
+            const float *src = s_src + k * SRC32_STRIDE;
             const float dl = src[SRC32_DL];
             int e = (tail + __popc(m & lt_mask)) & (kRing - 1);
 #pragma unroll
@@ -362,7 +377,7 @@ size_t split_smem_bytes(const SpotArgs &a) {
          kSplitWarps * sizeof(SplitRing) +
          (size_t)kSplitWarps * 32 * kStateStride * sizeof(float) +
          (size_t)kSplitWarps * kCandRing * sizeof(int) +
-         (size_t)2 * nblk * sizeof(float);
+         (size_t)(2 * nblk + a.S) * sizeof(float);
 }
 
 bool split_supported(const SpotArgs &a) {
