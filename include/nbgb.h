@@ -118,6 +118,8 @@ int nb_set_scale(nb_sim *sim, double scale);
  *   kahn_K    polarization factor K in [0, 1]; e_vec the E-vector of the
  *             polarized part (not parallel to any source direction when
  *             K != 0).
+ * The library keeps the sources ordered by ascending 1/lambda (the sum does
+ * not depend on their order; results agree to rounding). 
  * Errors: NB_EINVAL for n_src < 1, NULL arrays, non-unit directions,
  * lambda <= 0, K outside [0, 1], or e_vec parallel to a direction. */
 int nb_set_beam(nb_sim *sim, const double *dirs, const double *lambda_A,

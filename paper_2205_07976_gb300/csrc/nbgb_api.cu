@@ -5,6 +5,7 @@
 
 #include <cmath>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -261,6 +262,28 @@ static void split_ff(double v, float &hi, float &lo) {
 }
 
 namespace nbgb {
+// Reorders the sources by ascending 1/lambda (stable).  The sum over
+// sources does not depend on their order; sorted wavenumbers let the
+// warp-per-pixel kernel turn a wavenumber interval into a source range.
+void sort_sources(std::vector<double> &dirs, std::vector<double> &lam,
+                  std::vector<double> &w) {
+  size_t S = lam.size();
+  std::vector<size_t> idx(S);
+  for (size_t i = 0; i < S; ++i) idx[i] = i;
+  std::stable_sort(idx.begin(), idx.end(), [&](size_t a, size_t b) {
+    return 1.0 / lam[a] < 1.0 / lam[b];
+  });
+  std::vector<double> d2(3 * S), l2(S), w2(S);
+  for (size_t i = 0; i < S; ++i) {
+    for (int c = 0; c < 3; ++c) d2[3 * i + c] = dirs[3 * idx[i] + c];
+    l2[i] = lam[idx[i]];
+    w2[i] = w[idx[i]];
+  }
+  dirs.swap(d2);
+  lam.swap(l2);
+  w.swap(w2);
+}
+
 // u0 = centre of the 1/lambda range of the sources
 double source_u0(const double *lam, int S) {
   double umin = 1e300, umax = -1e300;
@@ -637,6 +660,7 @@ int nb_set_beam(nb_sim *s, const double *dirs, const double *lambda_A,
   s->dirs.assign(dirs, dirs + 3 * (size_t)n_src);
   s->lam.assign(lambda_A, lambda_A + n_src);
   s->w.assign(weights, weights + n_src);
+  nbgb::sort_sources(s->dirs, s->lam, s->w);
   s->n_src = n_src;
   s->fluence = fluence;
   s->kahn = kahn_K;

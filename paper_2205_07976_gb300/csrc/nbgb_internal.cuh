@@ -215,6 +215,8 @@ __device__ __forceinline__ void lagrange4(T x, T w[4]) {
 }
 
 // host-side table builders shared by nb_sim and nb_server
+void sort_sources(std::vector<double> &dirs, std::vector<double> &lam,
+                  std::vector<double> &w);
 double source_u0(const double *lam, int S);
 void shot_tables_f32(const std::vector<double> &ax, const double *lam,
                      const double *w, const double *dirs, int S,

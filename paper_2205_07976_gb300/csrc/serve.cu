@@ -469,13 +469,16 @@ int nb_server_submit(nb_server *s, const double axes[9], const double *umats,
   std::vector<double> ax;
   double spindle[3] = {0, 1, 0};
   nbgb::rotated_axes_table(axes, umats, n_mosaic, 1, 0.0, 0.0, spindle, ax);
-  double u0 = nbgb::source_u0(lambda_A, n_src);
   std::vector<double> dirs(3 * (size_t)n_src);
   for (int k = 0; k < n_src; ++k)
     for (int c = 0; c < 3; ++c) dirs[3 * k + c] = s->dir[c];
+  std::vector<double> lam(lambda_A, lambda_A + n_src),
+      wts(weights, weights + n_src);
+  nbgb::sort_sources(dirs, lam, wts);  // the order nb_set_beam uses
+  double u0 = nbgb::source_u0(lam.data(), n_src);
   std::vector<float> axh, axl, src32;
-  nbgb::shot_tables_f32(ax, lambda_A, weights, dirs.data(), n_src, s->evec,
-                        u0, false, axh, axl, src32);
+  nbgb::shot_tables_f32(ax, lam.data(), wts.data(), dirs.data(), n_src,
+                        s->evec, u0, false, axh, axl, src32);
   std::memcpy(r.params.axh, axh.data(), axh.size() * 4);
   std::memcpy(r.params.axl, axl.data(), axl.size() * 4);
   std::memcpy(r.params.src32, src32.data(), src32.size() * 4);

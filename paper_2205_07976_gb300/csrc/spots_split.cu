@@ -93,6 +93,12 @@ __global__ void __launch_bounds__(kSplitThreads, 6)
   for (int k = threadIdx.x; k < S; k += blockDim.x)
     s_dh[k] = s_src[k * SRC32_STRIDE + SRC32_DH];
   __syncthreads();
+  // exact intervals need delta_hi in ascending order (the library sorts the
+  // sources; a caller of the allocation-free entry may not)
+  int unsorted = 0;
+  for (int k = threadIdx.x; k + 1 < S; k += blockDim.x)
+    unsorted |= s_dh[k] > s_dh[k + 1];
+  const bool dh_sorted = __syncthreads_or(unsorted) == 0;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float *unit = s_unit + warp * kMaxUnits * kUnitFloats;
@@ -102,11 +108,20 @@ __global__ void __launch_bounds__(kSplitThreads, 6)
   const float cutg = kGaussCut * 0.63f;
   const float kahn = a.kahn;
   const float N2[3] = {a.N[0] * a.N[0], a.N[1] * a.N[1], a.N[2] * a.N[2]};
-  // |f_x| <= sqrt(cut) / N_x for every surviving term (with a margin for
-  // the rounding of the exponent sum)
-  const float cmarg[3] = {sqrtf(cutg) / a.N[0] * 1.0001f,
-                          sqrtf(cutg) / a.N[1] * 1.0001f,
-                          sqrtf(cutg) / a.N[2] * 1.0001f};
+  // a widened cut for the conservative tests: every surviving term has
+  // sum N^2 f^2 <= cutg < cwide, so |f_x| <= sqrt(cwide) / N_x
+  const float cwide = cutg * 1.02f + 1e-4f;
+  const float cmarg[3] = {sqrtf(cwide) / a.N[0], sqrtf(cwide) / a.N[1],
+                          sqrtf(cwide) / a.N[2]};
+  // exact delta-intervals per lattice point need the ellipsoids of
+  // neighbouring lattice points to be disjoint: sqrt(cwide)/N < 1/2
+  const bool iv_ok = dh_sorted && cmarg[0] < 0.49f && cmarg[1] < 0.49f &&
+                     cmarg[2] < 0.49f;
+  const float dmin = S > 0 ? s_dh[0] : 0.f;
+  const float dmax = S > 0 ? s_dh[S - 1] : 0.f;
+  const float dmarg = 1e-3f * (dmax - dmin) / (float)(S > 1 ? S - 1 : 1);
+  int sstep = 1;
+  while (sstep * 2 <= S) sstep *= 2;
   float *st = s_state + warp * 32 * kStateStride;
   int *cring = s_cring + warp * kCandRing;
   const long long n_work = a.pixlist ? a.n_list : a.npix;
@@ -281,12 +296,13 @@ __global__ void __launch_bounds__(kSplitThreads, 6)
         __syncwarp();
         int ch = 0, ct = 0;
         auto run_cands = [&](int nc) {
+          // ring entry: owner lane | first source << 5 | count << 16
           const int ci = lane >> 3, kk = lane & 7;
           bool ok = ci < nc;
           int ent = ok ? cring[(ch + ci) & (kCandRing - 1)] : 0;
-          int own = ent >> 16, b = ent & 0xffff;
-          int k = b * kSrcBlock + kk;
-          ok = ok && k < S;
+          int own = ent & 31, k0 = (ent >> 5) & 2047, cnt = (ent >> 16) & 15;
+          int k = k0 + kk;
+          ok = ok && kk < cnt && k < S;
           const float *o = st + own * kStateStride;
           const float dh = s_dh[ok ? k : 0];
           float fr[3], nf[3];
@@ -323,28 +339,110 @@ __global__ void __launch_bounds__(kSplitThreads, 6)
             __syncwarp();
           }
         };
-        for (int b = 0; b < nblk; ++b) {
-          bool pass = false;
-          if (valid) {
-            const float dmn = s_blk[2 * b], dmx = s_blk[2 * b + 1];
-            pass = true;
+        // lattice points the item's sweep can come near: per axis the
+        // integers within sqrt(cwide)/N_x of [h(dmin), h(dmax)]
+        int ml[3] = {0, 0, 0}, nm[3] = {0, 0, 0}, ncomb = 0;
+        if (iv_ok && valid) {
+          ncomb = 1;
 #pragma unroll
-            for (int x = 0; x < 3; ++x) {
-              float u = fmaf(Gh[x], dmn, rq[x]), v = fmaf(Gh[x], dmx, rq[x]);
-              float lo = fminf(u, v) - cmarg[x], hi = fmaxf(u, v) + cmarg[x];
-              pass = pass && floorf(hi) >= ceilf(lo);
+          for (int x = 0; x < 3; ++x) {
+            float u = fmaf(Gh[x], dmin, rq[x]), v = fmaf(Gh[x], dmax, rq[x]);
+            ml[x] = (int)ceilf(fminf(u, v) - cmarg[x]);
+            nm[x] = (int)floorf(fmaxf(u, v) + cmarg[x]) - ml[x] + 1;
+            if (nm[x] < 0) nm[x] = 0;
+            ncomb *= nm[x];
+          }
+        }
+        if (iv_ok && __all_sync(0xffffffffu, ncomb <= 8)) {
+          // exact intervals: for lattice point m the exponent sum along
+          // the sweep is A d^2 + 2 B d + C, below cwide on one interval
+          const int maxc = (int)__reduce_max_sync(0xffffffffu, (unsigned)ncomb);
+          for (int c = 0; c < maxc; ++c) {
+            int k1 = 0, k2 = 0;
+            if (c < ncomb) {
+              float dx[3];
+              int cc = c;
+#pragma unroll
+              for (int x = 0; x < 3; ++x) {
+                int mx = ml[x] + cc % nm[x];
+                cc /= nm[x];
+                dx[x] = rq[x] - (float)mx;  // exact: r_q on a 2^-21 grid
+              }
+              float A = N2[0] * Gh[0] * Gh[0];
+              A = fmaf(N2[1] * Gh[1], Gh[1], A);
+              A = fmaf(N2[2] * Gh[2], Gh[2], A);
+              float B = N2[0] * Gh[0] * dx[0];
+              B = fmaf(N2[1] * Gh[1], dx[1], B);
+              B = fmaf(N2[2] * Gh[2], dx[2], B);
+              float C0 = N2[0] * dx[0] * dx[0];
+              C0 = fmaf(N2[1] * dx[1], dx[1], C0);
+              C0 = fmaf(N2[2] * dx[2], dx[2], C0);
+              if (A > 0.f) {
+                float disc = fmaf(B, B, -A * (C0 - cwide));
+                if (disc >= 0.f) {
+                  float sq = sqrtf(disc);
+                  float lo = (-B - sq) / A, hi = (-B + sq) / A;
+                  float mg = 1e-4f * (fabsf(lo) + fabsf(hi)) + dmarg;
+                  lo -= mg;
+                  hi += mg;
+                  // k1 = #{delta < lo}, k2 = #{delta <= hi} (sorted table)
+                  for (int st = sstep; st > 0; st >>= 1) {
+                    if (k1 + st <= S && s_dh[k1 + st - 1] < lo) k1 += st;
+                    if (k2 + st <= S && s_dh[k2 + st - 1] <= hi) k2 += st;
+                  }
+                }
+              } else if (C0 <= cwide) {
+                k2 = S;  // the sweep does not move: all or nothing
+              }
+            }
+            const int nch = k2 > k1 ? (k2 - k1 + kSrcBlock - 1) / kSrcBlock : 0;
+            const int maxch =
+                (int)__reduce_max_sync(0xffffffffu, (unsigned)nch);
+            for (int j = 0; j < maxch; ++j) {
+              bool has = j < nch;
+              unsigned mm = __ballot_sync(0xffffffffu, has);
+              if (has) {
+                int st0 = k1 + j * kSrcBlock;
+                int cnt = min(kSrcBlock, k2 - st0);
+                cring[(ct + __popc(mm & lt_mask)) & (kCandRing - 1)] =
+                    lane | (st0 << 5) | (cnt << 16);
+              }
+              ct += __popc(mm);
+              __syncwarp();
+              while (ct - ch >= 4) {
+                run_cands(4);
+                ch += 4;
+              }
             }
           }
-          unsigned m = __ballot_sync(0xffffffffu, pass);
-          if (m == 0u) continue;
-          if (pass)
-            cring[(ct + __popc(m & lt_mask)) & (kCandRing - 1)] =
-                (lane << 16) | b;
-          ct += __popc(m);
-          __syncwarp();
-          while (ct - ch >= 4) {
-            run_cands(4);
-            ch += 4;
+        } else {
+          for (int b = 0; b < nblk; ++b) {
+            bool pass = false;
+            if (valid) {
+              const float dmn = s_blk[2 * b], dmx = s_blk[2 * b + 1];
+              pass = true;
+#pragma unroll
+              for (int x = 0; x < 3; ++x) {
+                float u = fmaf(Gh[x], dmn, rq[x]), v = fmaf(Gh[x], dmx, rq[x]);
+                float lo = fminf(u, v) - cmarg[x],
+                      hi = fmaxf(u, v) + cmarg[x];
+                pass = pass && floorf(hi) >= ceilf(lo);
+              }
+            }
+            unsigned m = __ballot_sync(0xffffffffu, pass);
+            if (m == 0u) continue;
+            if (pass) {
+              int st0 = b * kSrcBlock;
+              int cnt = min(kSrcBlock, S - st0);
+              cring[(ct + __popc(m & lt_mask)) & (kCandRing - 1)] =
+                  lane | (st0 << 5) | (cnt << 16);
+            }
+            ct += __popc(m);
+            __syncwarp();
+            while (ct - ch >= 4) {
+              run_cands(4);
+              ch += 4;
+            }
           }
         }
         if (ct > ch) {
