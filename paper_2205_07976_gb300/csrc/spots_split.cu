@@ -35,23 +35,26 @@ constexpr int kCandRing = 64;     // per-warp ring of (lane, source block)
 constexpr int kSrcBlock = 8;      // sources per pruning block
 
 struct SplitRing {
-  float f[3][kRing];
-  int n[3][kRing];
-  float w[kRing];
+  float4 fw[kRing];  // f_h, f_k, f_l, weight: one 16-byte store / load
+  int4 n[kRing];     // table-relative nearest index (h, k, l), unused
 };
+static_assert(sizeof(SplitRing) % 16 == 0, "rings stay 16-byte aligned");
 
 template <int INTERP>
 __device__ __forceinline__ void eval_term(const SpotArgs &a,
                                           const SplitRing &q, int e,
                                           Kahan &acc) {
-  float fr[3] = {q.f[0][e], q.f[1][e], q.f[2][e]};
-  int n[3] = {q.n[0][e], q.n[1][e], q.n[2][e]};
+  const float4 fw = q.fw[e];
+  const int4 ni = q.n[e];
+  float fr[3] = {fw.x, fw.y, fw.z};
+  int n[3] = {ni.x, ni.y, ni.z};
   float rad2 = a.N[0] * a.N[0] * fr[0] * fr[0];
   rad2 = fmaf(a.N[1] * a.N[1], fr[1] * fr[1], rad2);
   rad2 = fmaf(a.N[2] * a.N[2], fr[2] * fr[2], rad2);
-  float fl2 = a.N6 * expf(-2.f * rad2 * (1.f / 0.63f));
+  // fast exp: a few ulp for the significant terms (|argument| < ~20)
+  float fl2 = a.N6 * __expf(-2.f * rad2 * (1.f / 0.63f));
   float fc = fcell_f32<INTERP>(a, n, fr);
-  acc.add(fc * fc * fl2 * q.w[e]);
+  acc.add(fc * fc * fl2 * fw.w);
 }
 
 template <int INTERP, int HASDIV>
@@ -63,9 +66,12 @@ __global__ void __launch_bounds__(kSplitThreads, 6)
   float *s_axl = s_axh + PM * 9;
   float *s_src = s_axl + PM * 9;
   float *s_unit = s_src + S * SRC32_STRIDE;  // [warp][unit][kUnitFloats]
-  SplitRing *rings =
-      reinterpret_cast<SplitRing *>(s_unit + kSplitWarps * kMaxUnits *
-                                                 kUnitFloats);
+  // the rings hold float4s: 16-byte aligned base
+  size_t ring_off =
+      ((size_t)(s_unit + kSplitWarps * kMaxUnits * kUnitFloats - sms) *
+           sizeof(float) + 15) & ~(size_t)15;
+  SplitRing *rings = reinterpret_cast<SplitRing *>(
+      reinterpret_cast<char *>(sms) + ring_off);
   float *s_state = reinterpret_cast<float *>(rings + kSplitWarps);
   int *s_cring =
       reinterpret_cast<int *>(s_state + kSplitWarps * 32 * kStateStride);
@@ -262,12 +268,10 @@ __global__ void __launch_bounds__(kSplitThreads, 6)
               float y = df[0] * bv[0] + df[1] * bv[1] + df[2] * bv[2];
               w *= 0.5f * (1.f + c2 * c2 - kahn * (x * x - y * y));
             }
-#pragma unroll
-            for (int x = 0; x < 3; ++x) {
-              q.f[x][e] = fr[x];
-              q.n[x][e] = __float2int_rn(n0[x] + nf[x]) - a.hmin[x];
-            }
-            q.w[e] = w;
+            q.fw[e] = make_float4(fr[0], fr[1], fr[2], w);
+            q.n[e] = make_int4(__float2int_rn(n0[0] + nf[0]) - a.hmin[0],
+                               __float2int_rn(n0[1] + nf[1]) - a.hmin[1],
+                               __float2int_rn(n0[2] + nf[2]) - a.hmin[2], 0);
           }
           tail += __popc(m);
           if (tail - head >= 32) {
@@ -322,14 +326,17 @@ __global__ void __launch_bounds__(kSplitThreads, 6)
             const float *src = s_src + k * SRC32_STRIDE;
             const float dl = src[SRC32_DL];
             int e = (tail + __popc(m & lt_mask)) & (kRing - 1);
+            float f[3];
+            int nn[3];
 #pragma unroll
             for (int x = 0; x < 3; ++x) {
               float sx = fmaf(o[x], dh, __fsub_rn(o[6 + x], nf[x]));
               float c = fmaf(o[x], dl, fmaf(o[3 + x], dh, o[9 + x]));
-              q.f[x][e] = sx + c;
-              q.n[x][e] = __float2int_rn(o[12 + x] + nf[x]) - a.hmin[x];
+              f[x] = sx + c;
+              nn[x] = __float2int_rn(o[12 + x] + nf[x]) - a.hmin[x];
             }
-            q.w[e] = src[SRC32_W] * o[15];
+            q.fw[e] = make_float4(f[0], f[1], f[2], src[SRC32_W] * o[15]);
+            q.n[e] = make_int4(nn[0], nn[1], nn[2], 0);
           }
           tail += __popc(m);
           if (tail - head >= 32) {
@@ -472,7 +479,7 @@ size_t split_smem_bytes(const SpotArgs &a) {
   int nblk = (a.S + kSrcBlock - 1) / kSrcBlock;
   return (size_t)(2 * a.PM * 9 + a.S * SRC32_STRIDE +
                   kSplitWarps * kMaxUnits * kUnitFloats) * sizeof(float) +
-         kSplitWarps * sizeof(SplitRing) +
+         16 /* alignment of the rings */ + kSplitWarps * sizeof(SplitRing) +
          (size_t)kSplitWarps * 32 * kStateStride * sizeof(float) +
          (size_t)kSplitWarps * kCandRing * sizeof(int) +
          (size_t)(2 * nblk + a.S) * sizeof(float);
