@@ -93,8 +93,8 @@ struct nb_sim {
   bool have_params = false;
   double pU[9] = {0}, pcell[3] = {0}, prot[3] = {0};
   double daxes[6][9];  // d(lab axes)/d(tx, ty, tz, a, b, c)
-  DevBuf d_dax, d_part, d_grad, d_F4;
-  bool F4_valid = false;
+  DevBuf d_dax, d_part, d_grad, d_F4, d_C4;
+  bool F4_valid = false, C4_valid = false;
   int has_div = 0;
   double u0 = 0;
   bool tables_dirty = true;
@@ -454,6 +454,7 @@ static void fill_args(const nb_sim *s, SpotArgs &a) {
   a.interp = s->interp;
   a.F = (const float *)s->d_F.p;
   a.F4 = s->F4_valid ? (const float4 *)s->d_F4.p : nullptr;
+  a.C4 = s->C4_valid ? (const float4 *)s->d_C4.p : nullptr;
   a.defF = (float)s->defF;
   a.defF64 = s->defF;
   a.S = s->n_src;
@@ -519,7 +520,8 @@ int nb_free(nb_sim *sim) {
                       &sim->d_divh,   &sim->d_divl,  &sim->d_F,
                       &sim->d_image,  &sim->d_list,  &sim->d_tmp,
                       &sim->d_stats,  &sim->d_work,  &sim->d_dax,
-                      &sim->d_part,   &sim->d_grad,  &sim->d_F4};
+                      &sim->d_part,   &sim->d_grad,  &sim->d_F4,
+                      &sim->d_C4};
     for (DevBuf *b : bufs) b->release();
   }
   delete sim;
@@ -587,6 +589,7 @@ int nb_set_crystal(nb_sim *s, const double axes[9], const double *umats,
     s->defF = default_F;
     s->have_F = true;
     s->F4_valid = false;
+    s->C4_valid = false;
   } else {
     if (interp == NB_INTERP_NEAREST || interp == NB_INTERP_TRICUBIC)
       s->interp = interp;
@@ -759,6 +762,26 @@ static void ensure_sliding_table(nb_sim *s) {
     s->F4_valid = true;
 }
 
+// the tricubic polynomial of every table cell (64 floats per cell) for the
+// warp-per-pixel kernel; skipped above 2 GB or if the allocation fails
+static void ensure_cell_polynomials(nb_sim *s) {
+  if (s->C4_valid || s->interp != NB_INTERP_TRICUBIC ||
+      s->precision != NB_MIXED)
+    return;
+  if (s->hn[0] < 4 || s->hn[1] < 4 || s->hn[2] < 4) return;
+  size_t cells = (size_t)(s->hn[0] - 3) * (s->hn[1] - 3) * (s->hn[2] - 3);
+  size_t bytes = cells * 16 * sizeof(float4);
+  if (bytes > (size_t)2 << 30) return;
+  if (s->d_C4.ensure(bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  if (nbgb::build_cell_polynomials((const float *)s->d_F.p, s->hn,
+                                   (float4 *)s->d_C4.p,
+                                   s->stream) == cudaSuccess)
+    s->C4_valid = true;
+}
+
 static int launch(nb_sim *s, const long long *dev_list, long long n_list) {
   if (!s->have_crystal || !s->have_beam || !s->have_det || !s->have_F)
     return fail(s, NB_ESTATE, "crystal, beam and detector must be set first");
@@ -796,6 +819,8 @@ static int launch(nb_sim *s, const long long *dev_list, long long n_list) {
   if (s->precision == NB_F64) {
     e = nbgb::launch_spots_f64(a, s->stream);
   } else if (warp_variant) {
+    ensure_cell_polynomials(s);
+    a.C4 = s->C4_valid ? (const float4 *)s->d_C4.p : nullptr;
     e = s->d_work.ensure(sizeof(unsigned long long));
     if (e != cudaSuccess) return fail(s, NB_ENOMEM, "work counter");
     e = cudaMemsetAsync(s->d_work.p, 0, sizeof(unsigned long long),

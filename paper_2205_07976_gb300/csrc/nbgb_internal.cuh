@@ -71,6 +71,10 @@ struct SpotArgs {
   // optional copy of F for tricubic lookups: F4[i][j][l] holds
   // F[i][j][l..l+3] (zero past the end), one 16-byte load per stencil row
   const float4 *F4;
+  // optional tricubic cell polynomials: for the cell whose 4x4x4 stencil
+  // starts at table node (i, j, k), 16 float4 = 64 monomial coefficients
+  // C[a][b][c] of x^a y^b z^c (c fastest), x in [0, 1) from node + 1
+  const float4 *C4;
   int hmin[3], hn[3];
   float defF;
   double defF64;
@@ -230,6 +234,8 @@ void rotated_axes_table(const double *lab, const double *umats, int n_mosaic,
 cudaError_t launch_spots_f64(const SpotArgs &a, cudaStream_t st);
 cudaError_t build_sliding_table(const float *F, const int hn[3], float4 *F4,
                                 cudaStream_t st);
+cudaError_t build_cell_polynomials(const float *F, const int hn[3], float4 *C4,
+                                   cudaStream_t st);
 size_t adjoint_smem_bytes(const SpotArgs &a);
 long long adjoint_blocks(const SpotArgs &a);
 int loss_blocks(long long n);

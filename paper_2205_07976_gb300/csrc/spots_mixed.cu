@@ -89,6 +89,64 @@ cudaError_t build_sliding_table(const float *F, const int hn[3], float4 *F4,
   return cudaGetLastError();
 }
 
+// monomial coefficients of the 4-point Lagrange basis on nodes -1, 0, 1, 2
+// (row: node, column: power of x), exact in binary except the thirds and
+// sixths
+__constant__ float kLagrangeMono[4][4] = {{0.f, -1.f / 3.f, 0.5f, -1.f / 6.f},
+                                          {1.f, -0.5f, -1.f, 0.5f},
+                                          {0.f, 1.f, 0.5f, -0.5f},
+                                          {0.f, -1.f / 6.f, 0.f, 1.f / 6.f}};
+
+__global__ void cell_polynomials_kernel(const float *F, int nh, int nk,
+                                        int nl, float4 *C4) {
+  const int ch = nh - 3, ck = nk - 3, cl = nl - 3;
+  const long long ncell = (long long)ch * ck * cl;
+  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+       c < ncell; c += (long long)gridDim.x * blockDim.x) {
+    int i = (int)(c / ((long long)ck * cl));
+    int j = (int)((c / cl) % ck);
+    int k = (int)(c % cl);
+    float T[4][4][4];  // stencil, then transformed axis by axis
+    for (int p = 0; p < 4; ++p)
+      for (int q = 0; q < 4; ++q)
+        for (int r = 0; r < 4; ++r)
+          T[p][q][r] = F[((long long)(i + p) * nk + (j + q)) * nl + (k + r)];
+    float U[4][4][4];
+    for (int a = 0; a < 4; ++a)  // along h
+      for (int q = 0; q < 4; ++q)
+        for (int r = 0; r < 4; ++r) {
+          float v = 0.f;
+          for (int p = 0; p < 4; ++p) v = fmaf(kLagrangeMono[p][a], T[p][q][r], v);
+          U[a][q][r] = v;
+        }
+    for (int a = 0; a < 4; ++a)  // along k
+      for (int b = 0; b < 4; ++b)
+        for (int r = 0; r < 4; ++r) {
+          float v = 0.f;
+          for (int q = 0; q < 4; ++q) v = fmaf(kLagrangeMono[q][b], U[a][q][r], v);
+          T[a][b][r] = v;
+        }
+    float4 *out = C4 + c * 16;
+    for (int a = 0; a < 4; ++a)  // along l
+      for (int b = 0; b < 4; ++b) {
+        float v[4];
+        for (int cc = 0; cc < 4; ++cc) {
+          float t = 0.f;
+          for (int r = 0; r < 4; ++r) t = fmaf(kLagrangeMono[r][cc], T[a][b][r], t);
+          v[cc] = t;
+        }
+        out[a * 4 + b] = make_float4(v[0], v[1], v[2], v[3]);
+      }
+  }
+}
+
+cudaError_t build_cell_polynomials(const float *F, const int hn[3], float4 *C4,
+                                   cudaStream_t st) {
+  if (hn[0] < 4 || hn[1] < 4 || hn[2] < 4) return cudaErrorInvalidValue;
+  cell_polynomials_kernel<<<2432, 128, 0, st>>>(F, hn[0], hn[1], hn[2], C4);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_spots_mixed(const SpotArgs &a, int precision,
                                cudaStream_t st) {
   size_t smem = (size_t)(2 * a.PM * 9 + a.S * SRC32_STRIDE) * sizeof(float);

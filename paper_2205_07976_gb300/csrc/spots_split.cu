@@ -53,7 +53,36 @@ __device__ __forceinline__ void eval_term(const SpotArgs &a,
   rad2 = fmaf(a.N[2] * a.N[2], fr[2] * fr[2], rad2);
   // fast exp: a few ulp for the significant terms (|argument| < ~20)
   float fl2 = a.N6 * __expf(-2.f * rad2 * (1.f / 0.63f));
-  float fc = fcell_f32<INTERP>(a, n, fr);
+  float fc;
+  int fl[3];
+  float x[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    int neg = fr[c] < 0.f;
+    fl[c] = n[c] - neg;
+    x[c] = neg ? 1.f + fr[c] : fr[c];
+  }
+  if (INTERP == 1 && a.C4 && fl[0] >= 1 && fl[0] + 2 < a.hn[0] &&
+      fl[1] >= 1 && fl[1] + 2 < a.hn[1] && fl[2] >= 1 && fl[2] + 2 < a.hn[2]) {
+    // the cell's tricubic polynomial, nested Horner in l, k, h (63 FMAs)
+    const float4 *cp =
+        a.C4 + (((long long)(fl[0] - 1) * (a.hn[1] - 3) + (fl[1] - 1)) *
+                    (a.hn[2] - 3) + (fl[2] - 1)) * 16;
+    float qa[4];
+#pragma unroll
+    for (int ia = 0; ia < 4; ++ia) {
+      float pb[4];
+#pragma unroll
+      for (int ib = 0; ib < 4; ++ib) {
+        float4 c4 = __ldg(cp + ia * 4 + ib);
+        pb[ib] = fmaf(fmaf(fmaf(c4.w, x[2], c4.z), x[2], c4.y), x[2], c4.x);
+      }
+      qa[ia] = fmaf(fmaf(fmaf(pb[3], x[1], pb[2]), x[1], pb[1]), x[1], pb[0]);
+    }
+    fc = fmaf(fmaf(fmaf(qa[3], x[0], qa[2]), x[0], qa[1]), x[0], qa[0]);
+  } else {
+    fc = fcell_f32<INTERP>(a, n, fr);
+  }
   acc.add(fc * fc * fl2 * fw.w);
 }
 
