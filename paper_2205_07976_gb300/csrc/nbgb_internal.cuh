@@ -251,6 +251,7 @@ size_t split_smem_bytes(const SpotArgs &a);
 bool split_supported(const SpotArgs &a);
 cudaError_t launch_spots_split(const SpotArgs &a, unsigned long long *work,
                                int sm_count, cudaStream_t st);
+size_t serve_warp_smem_bytes();
 cudaError_t launch_spots_mixed(const SpotArgs &a, int precision,
                                cudaStream_t st);
 

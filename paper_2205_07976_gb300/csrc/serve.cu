@@ -33,12 +33,14 @@
 
 #include "../../include/nbgb.h"
 #include "mixed_pixel.cuh"
+#include "split_pixel.cuh"
 
 namespace nbgb {
 
 constexpr int kServeMaxPM = 64;
 constexpr int kServeMaxSrc = 128;
 constexpr int kServeItemPixels = kTileThreads;  // one pixel per thread
+constexpr int kServeWarpItemPixels = 32;  // warp kernel: 8 pixels per warp
 constexpr int kServeMaxItems = 16384;
 
 struct SlotParams {
@@ -107,6 +109,54 @@ __global__ void __launch_bounds__(kTileThreads, 4)
   }
 }
 
+// The warp-per-pixel form for requests the stand-alone library would also
+// run one warp per pixel (tricubic lookup, >= 16 subpixel x mosaic items):
+// each work item stages its request's tables once, then each warp sums its
+// pixels with the same device function as the stand-alone kernel.
+template <int INTERP>
+__global__ void __launch_bounds__(kSplitThreads, 6)
+    serve_warp_kernel(SpotArgs base, const SlotParams *slots,
+                      const WorkList *wl, unsigned *counter, double *pool) {
+  extern __shared__ float sms[];
+  __shared__ int s_item;
+  const DevPanel &P = base.panels[0];
+  const int n = wl->n;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int staged = -1;
+  SplitBlock b;
+  unsigned long long evals = 0;
+  while (true) {
+    if (threadIdx.x == 0) s_item = (int)atomicAdd(counter, 1u);
+    __syncthreads();
+    int it = s_item;
+    __syncthreads();
+    if (it >= n) break;
+    const WorkItem w = wl->items[it];
+    const SlotParams &sp = slots[w.slot];
+    if (w.slot != staged) {
+      split_stage(b, sms, base, sp.axh, sp.axl, sp.src32, sp.PM, sp.S, sp.u0h,
+                  sp.u0l);
+      staged = w.slot;
+    }
+    for (int j = warp; j < w.count; j += kSplitWarps) {
+      long long p = w.first + j;
+      int s = sp.s0 + (int)(p / sp.nf);
+      int f = sp.f0 + (int)(p % sp.nf);
+      double v = split_pixel<INTERP, 0>(base, b, P, s, f, evals);
+      if (lane == 0) pool[sp.img_off + p] = sp.prefactor * v;
+    }
+    __syncthreads();  // the tables may be restaged for the next item
+  }
+}
+
+size_t serve_warp_smem_bytes() {
+  SpotArgs a;
+  memset(&a, 0, sizeof a);
+  a.PM = kServeMaxPM;
+  a.S = kServeMaxSrc;
+  return split_smem_bytes(a);
+}
+
 }  // namespace nbgb
 
 using nbgb::SlotParams;
@@ -138,6 +188,7 @@ struct Request {
   long long pool_off = -1;
   int state = NB_REQ_QUEUED;
   int blocked_steps = 0;
+  bool warp = false;  // computed by the warp-per-pixel kernel
 };
 
 }  // namespace
@@ -161,8 +212,11 @@ struct nb_server {
   int hmin[3], hn[3];
   double defF = 0;
   double fluence = 0, kahn = 0, evec[3] = {1, 0, 0}, dir[3] = {0, 0, 1};
-  Buf d_F, d_F4, d_panel, d_slots, d_pool, d_work, d_counter;
-  WorkList *h_work = nullptr;  // pinned staging of the work list
+  Buf d_F, d_F4, d_C4, d_panel, d_slots, d_pool, d_work, d_work_w, d_counter;
+  WorkList *h_work = nullptr;    // pinned staging: thread-kernel items
+  WorkList *h_work_w = nullptr;  // pinned staging: warp-kernel items
+  int blocks_w = 0;
+  size_t smem_w = 0;
   nbgb::SpotArgs base;
   cudaGraphExec_t graph = nullptr;
   cudaEvent_t done_ev = nullptr;
@@ -218,13 +272,22 @@ static int build_graph(nb_server *s) {
   if (e != cudaSuccess) return sfail(s, NB_ECUDA, "graph capture begin");
   cudaMemcpyAsync(s->d_work.p, s->h_work, sizeof(WorkList),
                   cudaMemcpyHostToDevice, s->stream);
-  cudaMemsetAsync(s->d_counter.p, 0, sizeof(unsigned), s->stream);
+  cudaMemcpyAsync(s->d_work_w.p, s->h_work_w, sizeof(WorkList),
+                  cudaMemcpyHostToDevice, s->stream);
+  cudaMemsetAsync(s->d_counter.p, 0, 2 * sizeof(unsigned), s->stream);
   void (*kern)(nbgb::SpotArgs, const SlotParams *, const WorkList *,
                unsigned *, double *) =
       s->interp ? nbgb::serve_kernel<1> : nbgb::serve_kernel<0>;
   kern<<<s->blocks, nbgb::kTileThreads, 0, s->stream>>>(
       s->base, (const SlotParams *)s->d_slots.p, (const WorkList *)s->d_work.p,
       (unsigned *)s->d_counter.p, (double *)s->d_pool.p);
+  if (s->interp == NB_INTERP_TRICUBIC) {
+    nbgb::serve_warp_kernel<1><<<s->blocks_w, nbgb::kSplitThreads, s->smem_w,
+                                 s->stream>>>(
+        s->base, (const SlotParams *)s->d_slots.p,
+        (const WorkList *)s->d_work_w.p, (unsigned *)s->d_counter.p + 1,
+        (double *)s->d_pool.p);
+  }
   cudaGraph_t g = nullptr;
   e = cudaStreamEndCapture(s->stream, &g);
   if (e != cudaSuccess) return sfail(s, NB_ECUDA, "graph capture end");
@@ -321,14 +384,18 @@ int nb_server_create(nb_server **out, int device, void *cuda_stream,
         s->d_pool.alloc((size_t)s->pool_elems * sizeof(double)) !=
             cudaSuccess ||
         s->d_work.alloc(sizeof(WorkList)) != cudaSuccess ||
-        s->d_counter.alloc(sizeof(unsigned)) != cudaSuccess ||
+        s->d_work_w.alloc(sizeof(WorkList)) != cudaSuccess ||
+        s->d_counter.alloc(2 * sizeof(unsigned)) != cudaSuccess ||
         cudaHostAlloc((void **)&s->h_work, sizeof(WorkList),
+                      cudaHostAllocDefault) != cudaSuccess ||
+        cudaHostAlloc((void **)&s->h_work_w, sizeof(WorkList),
                       cudaHostAllocDefault) != cudaSuccess) {
       cudaGetLastError();
       rc = sfail(s, NB_ENOMEM, "server buffers");
       break;
     }
     std::memset(s->h_work, 0, sizeof(WorkList));
+    std::memset(s->h_work_w, 0, sizeof(WorkList));
     cudaMemcpy(s->d_F.p, F, nF * 4, cudaMemcpyHostToDevice);
     nbgb::DevPanel P;
     std::memset(&P, 0, sizeof P);
@@ -389,6 +456,22 @@ int nb_server_create(nb_server **out, int device, void *cuda_stream,
       a.F4 = (const float4 *)s->d_F4.p;
     }
     cudaGetLastError();
+    // the tricubic polynomial of every cell, as the stand-alone warp
+    // kernel uses it (same results bit for bit)
+    if (interp == NB_INTERP_TRICUBIC && hkl_n[0] >= 4 && hkl_n[1] >= 4 &&
+        hkl_n[2] >= 4) {
+      size_t cells =
+          (size_t)(hkl_n[0] - 3) * (hkl_n[1] - 3) * (hkl_n[2] - 3);
+      if (cells * 16 * sizeof(float4) <= ((size_t)2 << 30) &&
+          s->d_C4.alloc(cells * 16 * sizeof(float4)) == cudaSuccess &&
+          nbgb::build_cell_polynomials((const float *)s->d_F.p, s->hn,
+                                       (float4 *)s->d_C4.p,
+                                       s->stream) == cudaSuccess) {
+        cudaStreamSynchronize(s->stream);
+        a.C4 = (const float4 *)s->d_C4.p;
+      }
+      cudaGetLastError();
+    }
     a.defF = (float)default_F;
     a.defF64 = default_F;
     a.kahn = (float)kahn_K;
@@ -398,6 +481,17 @@ int nb_server_create(nb_server **out, int device, void *cuda_stream,
         &per_sm, interp ? nbgb::serve_kernel<1> : nbgb::serve_kernel<0>,
         nbgb::kTileThreads, 0);
     s->blocks = s->sm_count * (per_sm > 0 ? per_sm : 1);
+    if (interp == NB_INTERP_TRICUBIC) {
+      s->smem_w = nbgb::serve_warp_smem_bytes();
+      cudaFuncSetAttribute(nbgb::serve_warp_kernel<1>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)s->smem_w);
+      int per_sm_w = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+          &per_sm_w, nbgb::serve_warp_kernel<1>, nbgb::kSplitThreads,
+          s->smem_w);
+      s->blocks_w = s->sm_count * (per_sm_w > 0 ? per_sm_w : 1);
+    }
     for (int i = max_slots - 1; i >= 0; --i) s->free_slots.push_back(i);
     s->free_ranges[0] = s->pool_elems;
     if (cudaEventCreateWithFlags(&s->done_ev, cudaEventDisableTiming) !=
@@ -426,10 +520,12 @@ int nb_server_free(nb_server *s) {
   if (s->graph) cudaGraphExecDestroy(s->graph);
   if (s->done_ev) cudaEventDestroy(s->done_ev);
   if (s->h_work) cudaFreeHost(s->h_work);
+  if (s->h_work_w) cudaFreeHost(s->h_work_w);
   if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
   {
-    Buf *bufs[] = {&s->d_F,    &s->d_F4,   &s->d_panel,  &s->d_slots,
-                   &s->d_pool, &s->d_work, &s->d_counter};
+    Buf *bufs[] = {&s->d_F,    &s->d_F4,     &s->d_C4,     &s->d_panel,
+                   &s->d_slots, &s->d_pool, &s->d_work, &s->d_work_w,
+                   &s->d_counter};
     for (Buf *b : bufs) {
       if (b->p) cudaFree(b->p);
       b->p = nullptr;
@@ -496,6 +592,10 @@ int nb_server_submit(nb_server *s, const double axes[9], const double *umats,
   r.npix = npix;
   r.steps_per_pixel =
       (long long)s->os * s->os * s->T * n_src * (long long)n_mosaic;
+  // the same choice as nb_add_spots makes for this shot
+  r.warp = s->interp == NB_INTERP_TRICUBIC &&
+           (long long)s->os * s->os * s->T * n_mosaic >= 16 &&
+           s->os * s->os * s->T <= 32;
   s->queue.push_back(r.id);
   *request_id = r.id;
   s->reqs.emplace(r.id, std::move(r));
@@ -571,24 +671,27 @@ int nb_server_step(nb_server *s, double timeout_s, int *n_active) {
     for (auto &kv : s->reqs)
       if (kv.second.state == NB_REQ_RUNNING && kv.second.next < kv.second.npix)
         act.push_back(&kv.second);
-    WorkList *wl = s->h_work;
-    int n = 0;
+    WorkList *wl = s->h_work, *ww = s->h_work_w;
+    int nt = 0, nw = 0;
     long long used = 0;
     if (!act.empty()) {
       size_t start = (size_t)(s->rr_cursor % (long long)act.size());
       bool progress = true;
-      while (progress && used < s->budget && n < nbgb::kServeMaxItems) {
+      while (progress && used < s->budget) {
         progress = false;
-        for (size_t j = 0; j < act.size() && n < nbgb::kServeMaxItems &&
-                           used < s->budget;
-             ++j) {
+        for (size_t j = 0; j < act.size() && used < s->budget; ++j) {
           Request &r = *act[(start + j) % act.size()];
           if (r.next >= r.npix) continue;
+          WorkList *L = r.warp ? ww : wl;
+          int &n = r.warp ? nw : nt;
+          if (n >= nbgb::kServeMaxItems) continue;
+          long long cap = r.warp ? nbgb::kServeWarpItemPixels
+                                 : nbgb::kServeItemPixels;
           long long cnt = r.npix - r.next;
-          if (cnt > nbgb::kServeItemPixels) cnt = nbgb::kServeItemPixels;
-          wl->items[n].slot = r.slot;
-          wl->items[n].count = (int)cnt;
-          wl->items[n].first = r.next;
+          if (cnt > cap) cnt = cap;
+          L->items[n].slot = r.slot;
+          L->items[n].count = (int)cnt;
+          L->items[n].first = r.next;
           ++n;
           r.next += cnt;
           r.pending += cnt;
@@ -598,7 +701,9 @@ int nb_server_step(nb_server *s, double timeout_s, int *n_active) {
       }
       s->rr_cursor += 1;
     }
-    wl->n = n;
+    wl->n = nt;
+    ww->n = nw;
+    const int n = nt + nw;
     if (n == 0 && !s->queue.empty()) {
       // nothing runs and nothing can be admitted: the pool is held by
       // completed images that were not fetched yet

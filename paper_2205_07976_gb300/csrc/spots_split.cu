@@ -20,148 +20,19 @@
 // The order of every operation depends only on the pixel's own inputs, so
 // a pixel's value does not depend on what else is in the launch.
 // Pixels are handed to warps through an atomic counter in a scratch word.
-#include "mixed_common.cuh"
+#include "split_pixel.cuh"
 
 namespace nbgb {
-
-constexpr int kSplitWarps = 4;
-constexpr int kSplitThreads = kSplitWarps * 32;
-constexpr int kRing = 64;
-constexpr int kMaxUnits = 32;
-constexpr int kUnitFloats = 10;  // vh[3], vl[3], scal, df[3]
-constexpr int kStateStride = 17;  // per-lane item state: G, r, n0, scal
-                                  // (odd: distinct owners hit distinct banks)
-constexpr int kCandRing = 64;     // per-warp ring of (lane, source block)
-constexpr int kSrcBlock = 8;      // sources per pruning block
-
-struct SplitRing {
-  float4 fw[kRing];  // f_h, f_k, f_l, weight: one 16-byte store / load
-  int4 n[kRing];     // table-relative nearest index (h, k, l), unused
-};
-static_assert(sizeof(SplitRing) % 16 == 0, "rings stay 16-byte aligned");
-
-template <int INTERP>
-__device__ __forceinline__ void eval_term(const SpotArgs &a,
-                                          const SplitRing &q, int e,
-                                          Kahan &acc) {
-  const float4 fw = q.fw[e];
-  const int4 ni = q.n[e];
-  float fr[3] = {fw.x, fw.y, fw.z};
-  int n[3] = {ni.x, ni.y, ni.z};
-  float rad2 = a.N[0] * a.N[0] * fr[0] * fr[0];
-  rad2 = fmaf(a.N[1] * a.N[1], fr[1] * fr[1], rad2);
-  rad2 = fmaf(a.N[2] * a.N[2], fr[2] * fr[2], rad2);
-  // fast exp: a few ulp for the significant terms (|argument| < ~20)
-  float fl2 = a.N6 * __expf(-2.f * rad2 * (1.f / 0.63f));
-  float fc;
-  int fl[3];
-  float x[3];
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    int neg = fr[c] < 0.f;
-    fl[c] = n[c] - neg;
-    x[c] = neg ? 1.f + fr[c] : fr[c];
-  }
-  if (INTERP == 1 && a.C4 && fl[0] >= 1 && fl[0] + 2 < a.hn[0] &&
-      fl[1] >= 1 && fl[1] + 2 < a.hn[1] && fl[2] >= 1 && fl[2] + 2 < a.hn[2]) {
-    // the cell's tricubic polynomial, nested Horner in l, k, h (63 FMAs)
-    const float4 *cp =
-        a.C4 + (((long long)(fl[0] - 1) * (a.hn[1] - 3) + (fl[1] - 1)) *
-                    (a.hn[2] - 3) + (fl[2] - 1)) * 16;
-    float qa[4];
-#pragma unroll
-    for (int ia = 0; ia < 4; ++ia) {
-      float pb[4];
-#pragma unroll
-      for (int ib = 0; ib < 4; ++ib) {
-        float4 c4 = __ldg(cp + ia * 4 + ib);
-        pb[ib] = fmaf(fmaf(fmaf(c4.w, x[2], c4.z), x[2], c4.y), x[2], c4.x);
-      }
-      qa[ia] = fmaf(fmaf(fmaf(pb[3], x[1], pb[2]), x[1], pb[1]), x[1], pb[0]);
-    }
-    fc = fmaf(fmaf(fmaf(qa[3], x[0], qa[2]), x[0], qa[1]), x[0], qa[0]);
-  } else {
-    fc = fcell_f32<INTERP>(a, n, fr);
-  }
-  acc.add(fc * fc * fl2 * fw.w);
-}
 
 template <int INTERP, int HASDIV>
 __global__ void __launch_bounds__(kSplitThreads, 6)
     spots_split_kernel(SpotArgs a, unsigned long long *work) {
   extern __shared__ float sms[];
-  const int PM = a.PM, S = a.S;
-  float *s_axh = sms;
-  float *s_axl = s_axh + PM * 9;
-  float *s_src = s_axl + PM * 9;
-  float *s_unit = s_src + S * SRC32_STRIDE;  // [warp][unit][kUnitFloats]
-  // the rings hold float4s: 16-byte aligned base
-  size_t ring_off =
-      ((size_t)(s_unit + kSplitWarps * kMaxUnits * kUnitFloats - sms) *
-           sizeof(float) + 15) & ~(size_t)15;
-  SplitRing *rings = reinterpret_cast<SplitRing *>(
-      reinterpret_cast<char *>(sms) + ring_off);
-  float *s_state = reinterpret_cast<float *>(rings + kSplitWarps);
-  int *s_cring =
-      reinterpret_cast<int *>(s_state + kSplitWarps * 32 * kStateStride);
-  float *s_blk = reinterpret_cast<float *>(s_cring + kSplitWarps * kCandRing);
-  const int nblk = (S + kSrcBlock - 1) / kSrcBlock;
-  float *s_dh = s_blk + 2 * nblk;  // delta_hi of every source, contiguous
-  for (int i = threadIdx.x; i < PM * 9; i += blockDim.x) {
-    s_axh[i] = a.axh[i];
-    s_axl[i] = a.axl[i];
-  }
-  for (int i = threadIdx.x; i < S * SRC32_STRIDE; i += blockDim.x)
-    s_src[i] = a.src32[i];
-  __syncthreads();
-  // delta_hi range of every block of kSrcBlock sources (the pruning test)
-  for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
-    float mn = 3.0e38f, mx = -3.0e38f;
-    for (int k = b * kSrcBlock; k < S && k < (b + 1) * kSrcBlock; ++k) {
-      float d = s_src[k * SRC32_STRIDE + SRC32_DH];
-      mn = fminf(mn, d);
-      mx = fmaxf(mx, d);
-    }
-    s_blk[2 * b] = mn;
-    s_blk[2 * b + 1] = mx;
-  }
-  for (int k = threadIdx.x; k < S; k += blockDim.x)
-    s_dh[k] = s_src[k * SRC32_STRIDE + SRC32_DH];
-  __syncthreads();
-  // exact intervals need delta_hi in ascending order (the library sorts the
-  // sources; a caller of the allocation-free entry may not)
-  int unsorted = 0;
-  for (int k = threadIdx.x; k + 1 < S; k += blockDim.x)
-    unsorted |= s_dh[k] > s_dh[k + 1];
-  const bool dh_sorted = __syncthreads_or(unsorted) == 0;
-
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float *unit = s_unit + warp * kMaxUnits * kUnitFloats;
-  SplitRing &q = rings[warp];
-  const unsigned lt_mask = (1u << lane) - 1u;
-  const int os = a.os, U = a.os * a.os * a.T, items = U * PM;
-  const float cutg = kGaussCut * 0.63f;
-  const float kahn = a.kahn;
-  const float N2[3] = {a.N[0] * a.N[0], a.N[1] * a.N[1], a.N[2] * a.N[2]};
-  // a widened cut for the conservative tests: every surviving term has
-  // sum N^2 f^2 <= cutg < cwide, so |f_x| <= sqrt(cwide) / N_x
-  const float cwide = cutg * 1.02f + 1e-4f;
-  const float cmarg[3] = {sqrtf(cwide) / a.N[0], sqrtf(cwide) / a.N[1],
-                          sqrtf(cwide) / a.N[2]};
-  // exact delta-intervals per lattice point need the ellipsoids of
-  // neighbouring lattice points to be disjoint: sqrt(cwide)/N < 1/2
-  const bool iv_ok = dh_sorted && cmarg[0] < 0.49f && cmarg[1] < 0.49f &&
-                     cmarg[2] < 0.49f;
-  const float dmin = S > 0 ? s_dh[0] : 0.f;
-  const float dmax = S > 0 ? s_dh[S - 1] : 0.f;
-  const float dmarg = 1e-3f * (dmax - dmin) / (float)(S > 1 ? S - 1 : 1);
-  int sstep = 1;
-  while (sstep * 2 <= S) sstep *= 2;
-  float *st = s_state + warp * 32 * kStateStride;
-  int *cring = s_cring + warp * kCandRing;
+  SplitBlock b;
+  split_stage(b, sms, a, a.axh, a.axl, a.src32, a.PM, a.S, a.u0h, a.u0l);
+  const int lane = threadIdx.x & 31;
   const long long n_work = a.pixlist ? a.n_list : a.npix;
   unsigned long long evals = 0;  // terms evaluated by this warp
-
   while (true) {
     long long item_pix = 0;
     if (lane == 0) item_pix = (long long)atomicAdd(work, 1ULL);
@@ -173,333 +44,9 @@ __global__ void __launch_bounds__(kSplitThreads, 6)
     long long local = gp - P.pix0;
     int s = (int)(local / P.nfast);
     int f = (int)(local - (long long)s * P.nfast);
-
-    // ---- 1. per-unit geometry (FP64) into shared memory
-    for (int u = lane; u < U; u += 32) {
-      int t = u % a.T, ij = u / a.T, i = ij / os, j = ij % os;
-      double px = P.px;
-      double cf = (f + (i + 0.5) / os) * px, cs = (s + (j + 0.5) / os) * px,
-             cn = t * a.dt;
-      double pos[3], d[3];
-#pragma unroll
-      for (int c = 0; c < 3; ++c)
-        pos[c] = P.origin[c] + cf * P.fdir[c] + cs * P.sdir[c] +
-                 cn * P.ndir[c];
-      // FP64 only where h needs it: one reciprocal of |P|, d = P / |P|
-      double R = sqrt(dot3d_m(pos, pos));
-      double inv = 1.0 / R;
-      float *ud = unit + u * kUnitFloats;
-      float df[3];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        d[c] = pos[c] * inv;
-        double v = d[c] - a.i0[c];
-        float vh = (float)v;
-        ud[c] = vh;
-        ud[3 + c] = (float)(v - (double)vh);
-        df[c] = (float)d[c];
-        ud[7 + c] = df[c];
-      }
-      float invf = (float)inv;
-      float omega = (float)(px * px) * (float)dot3d_m(P.ndir, pos) * invf *
-                    invf * invf;
-      float cap = 1.f;
-      if (a.thickness > 0.0) {
-        float rho = df[0] * (float)P.ndir[0] + df[1] * (float)P.ndir[1] +
-                    df[2] * (float)P.ndir[2];
-        float L = (float)a.atten * rho, dtf = (float)a.dt;
-        cap = expf(-t * dtf / L) - expf(-(t + 1) * dtf / L);
-      }
-      float scal = omega * cap;
-      if (!HASDIV) {
-        float c2 = df[0] * (float)a.i0[0] + df[1] * (float)a.i0[1] +
-                   df[2] * (float)a.i0[2];
-        float x = df[0] * (float)a.e0[0] + df[1] * (float)a.e0[1] +
-                  df[2] * (float)a.e0[2];
-        float y = df[0] * (float)a.b0[0] + df[1] * (float)a.b0[1] +
-                  df[2] * (float)a.b0[2];
-        scal *= 0.5f * (1.f + c2 * c2 - kahn * (x * x - y * y));
-      }
-      ud[6] = scal;
-    }
-    __syncwarp();
-
-    // ---- 2./3. scan the steps, evaluate surviving terms 32 at a time
-    Kahan acc;
-    int head = 0, tail = 0;
-    for (int base = 0; base < items; base += 32) {
-      int it = base + lane;
-      bool valid = it < items;
-      int u = valid ? it / PM : 0, pm = valid ? it - u * PM : 0;
-      const float *ud = unit + u * kUnitFloats;
-      float vh[3] = {ud[0], ud[1], ud[2]}, vl[3] = {ud[3], ud[4], ud[5]};
-      float scal = ud[6];
-      float Gh[3], Gl[3], rq[3], rl[3], n0[3];
-#pragma unroll
-      for (int x = 0; x < 3; ++x) {
-        ff_dot3(s_axh + pm * 9 + 3 * x, s_axl + pm * 9 + 3 * x, vh, vl,
-                Gh[x], Gl[x]);
-        float qh, qe;
-        two_prod(Gh[x], a.u0h, qh, qe);
-        float ql = fmaf(Gh[x], a.u0l, fmaf(Gl[x], a.u0h, qe));
-        n0[x] = rintf(qh);
-        float rh, rl0;
-        two_sum(__fsub_rn(qh, n0[x]), ql, rh, rl0);
-        // r_hi on a 2^-21 grid: r_hi - n is then exact for |n| < 7
-        rq[x] = __fmul_rn(rintf(__fmul_rn(rh, 2097152.f)), 1.f / 2097152.f);
-        rl[x] = rl0 + __fsub_rn(rh, rq[x]);
-      }
-      if (HASDIV) {
-        for (int k = 0; k < S; ++k) {
-          const float *src = s_src + k * SRC32_STRIDE;
-          const float dh = src[SRC32_DH];
-          // cut test on the cheap offset t - rint(t) (error ~1 ulp of t, which
-          // only moves terms ~1e-38 below the peak across the cut)
-          float tq[3], nf[3], fr[3];
-#pragma unroll
-          for (int x = 0; x < 3; ++x) {
-            tq[x] = fmaf(Gh[x], dh, rq[x]);
-            if (HASDIV && valid) tq[x] -= __ldg(a.divh + ((size_t)pm * S + k) * 3 + x);
-            nf[x] = rintf(tq[x]);
-            fr[x] = tq[x] - nf[x];
-          }
-          float rad2 = N2[0] * fr[0] * fr[0];
-          rad2 = fmaf(N2[1] * fr[1], fr[1], rad2);
-          rad2 = fmaf(N2[2] * fr[2], fr[2], rad2);
-          bool hit = valid && rad2 <= cutg;
-          unsigned m = __ballot_sync(0xffffffffu, hit);
-          if (m == 0u) continue;
-          if (hit) {
-            // the precise offset: G_hi d_hi + (r_q - n) in one rounding (r_q
-            // on a 2^-21 grid makes r_q - n exact) plus the small terms
-            const float dl = src[SRC32_DL];
-#pragma unroll
-            for (int x = 0; x < 3; ++x) {
-              float sx = fmaf(Gh[x], dh, __fsub_rn(rq[x], nf[x]));
-              float c = fmaf(Gh[x], dl, fmaf(Gl[x], dh, rl[x]));
-              fr[x] = sx + c;
-              if (HASDIV) {
-                // the divergence term moves h after the rint: re-centre
-                size_t e = ((size_t)pm * S + k) * 3 + x;
-                fr[x] -= __ldg(a.divh + e) + __ldg(a.divl + e);
-                float n2 = rintf(fr[x]);
-                fr[x] -= n2;
-                nf[x] += n2;
-              }
-            }
-            int e = (tail + __popc(m & lt_mask)) & (kRing - 1);
-            float w = src[SRC32_W] * scal;
-            if (HASDIV) {
-              const float *df = ud + 7, *dir = src + SRC32_DIR,
-                          *ev = src + SRC32_E, *bv = src + SRC32_B;
-              float c2 = df[0] * dir[0] + df[1] * dir[1] + df[2] * dir[2];
-              float x = df[0] * ev[0] + df[1] * ev[1] + df[2] * ev[2];
-              float y = df[0] * bv[0] + df[1] * bv[1] + df[2] * bv[2];
-              w *= 0.5f * (1.f + c2 * c2 - kahn * (x * x - y * y));
-            }
-            q.fw[e] = make_float4(fr[0], fr[1], fr[2], w);
-            q.n[e] = make_int4(__float2int_rn(n0[0] + nf[0]) - a.hmin[0],
-                               __float2int_rn(n0[1] + nf[1]) - a.hmin[1],
-                               __float2int_rn(n0[2] + nf[2]) - a.hmin[2], 0);
-          }
-          tail += __popc(m);
-          if (tail - head >= 32) {
-            __syncwarp();
-            eval_term<INTERP>(a, q, (head + lane) & (kRing - 1), acc);
-            head += 32;
-            __syncwarp();
-          }
-        }
-      } else {
-        // ---- pruned scan: h_x = G_x delta + r_x is linear in delta, so a
-        // block of sources whose delta range [dmin, dmax] keeps some axis
-        // farther than sqrt(cut)/N_x from every integer holds no surviving
-        // term.  Surviving (lane, block) pairs go into a ring; the warp
-        // then runs 4 blocks x 8 sources = 32 steps at a time.
-        float *my = st + lane * kStateStride;
-#pragma unroll
-        for (int x = 0; x < 3; ++x) {
-          my[x] = Gh[x];
-          my[3 + x] = Gl[x];
-          my[6 + x] = rq[x];
-          my[9 + x] = rl[x];
-          my[12 + x] = n0[x];
-        }
-        my[15] = scal;
-        __syncwarp();
-        int ch = 0, ct = 0;
-        auto run_cands = [&](int nc) {
-          // ring entry: owner lane | first source << 5 | count << 16
-          const int ci = lane >> 3, kk = lane & 7;
-          bool ok = ci < nc;
-          int ent = ok ? cring[(ch + ci) & (kCandRing - 1)] : 0;
-          int own = ent & 31, k0 = (ent >> 5) & 2047, cnt = (ent >> 16) & 15;
-          int k = k0 + kk;
-          ok = ok && kk < cnt && k < S;
-          const float *o = st + own * kStateStride;
-          const float dh = s_dh[ok ? k : 0];
-          float fr[3], nf[3];
-#pragma unroll
-          for (int x = 0; x < 3; ++x) {
-            float tq = fmaf(o[x], dh, o[6 + x]);
-            nf[x] = rintf(tq);
-            fr[x] = tq - nf[x];
-          }
-          float rad2 = N2[0] * fr[0] * fr[0];
-          rad2 = fmaf(N2[1] * fr[1], fr[1], rad2);
-          rad2 = fmaf(N2[2] * fr[2], fr[2], rad2);
-          bool hit = ok && rad2 <= cutg;
-          unsigned m = __ballot_sync(0xffffffffu, hit);
-          if (m == 0u) return;
-          if (hit) {
-            const float *src = s_src + k * SRC32_STRIDE;
-            const float dl = src[SRC32_DL];
-            int e = (tail + __popc(m & lt_mask)) & (kRing - 1);
-            float f[3];
-            int nn[3];
-#pragma unroll
-            for (int x = 0; x < 3; ++x) {
-              float sx = fmaf(o[x], dh, __fsub_rn(o[6 + x], nf[x]));
-              float c = fmaf(o[x], dl, fmaf(o[3 + x], dh, o[9 + x]));
-              f[x] = sx + c;
-              nn[x] = __float2int_rn(o[12 + x] + nf[x]) - a.hmin[x];
-            }
-            q.fw[e] = make_float4(f[0], f[1], f[2], src[SRC32_W] * o[15]);
-            q.n[e] = make_int4(nn[0], nn[1], nn[2], 0);
-          }
-          tail += __popc(m);
-          if (tail - head >= 32) {
-            __syncwarp();
-            eval_term<INTERP>(a, q, (head + lane) & (kRing - 1), acc);
-            head += 32;
-            __syncwarp();
-          }
-        };
-        // lattice points the item's sweep can come near: per axis the
-        // integers within sqrt(cwide)/N_x of [h(dmin), h(dmax)]
-        int ml[3] = {0, 0, 0}, nm[3] = {0, 0, 0}, ncomb = 0;
-        if (iv_ok && valid) {
-          ncomb = 1;
-#pragma unroll
-          for (int x = 0; x < 3; ++x) {
-            float u = fmaf(Gh[x], dmin, rq[x]), v = fmaf(Gh[x], dmax, rq[x]);
-            ml[x] = (int)ceilf(fminf(u, v) - cmarg[x]);
-            nm[x] = (int)floorf(fmaxf(u, v) + cmarg[x]) - ml[x] + 1;
-            if (nm[x] < 0) nm[x] = 0;
-            ncomb *= nm[x];
-          }
-        }
-        if (iv_ok && __all_sync(0xffffffffu, ncomb <= 8)) {
-          // exact intervals: for lattice point m the exponent sum along
-          // the sweep is A d^2 + 2 B d + C, below cwide on one interval
-          const int maxc = (int)__reduce_max_sync(0xffffffffu, (unsigned)ncomb);
-          for (int c = 0; c < maxc; ++c) {
-            int k1 = 0, k2 = 0;
-            if (c < ncomb) {
-              float dx[3];
-              int cc = c;
-#pragma unroll
-              for (int x = 0; x < 3; ++x) {
-                int mx = ml[x] + cc % nm[x];
-                cc /= nm[x];
-                dx[x] = rq[x] - (float)mx;  // exact: r_q on a 2^-21 grid
-              }
-              float A = N2[0] * Gh[0] * Gh[0];
-              A = fmaf(N2[1] * Gh[1], Gh[1], A);
-              A = fmaf(N2[2] * Gh[2], Gh[2], A);
-              float B = N2[0] * Gh[0] * dx[0];
-              B = fmaf(N2[1] * Gh[1], dx[1], B);
-              B = fmaf(N2[2] * Gh[2], dx[2], B);
-              float C0 = N2[0] * dx[0] * dx[0];
-              C0 = fmaf(N2[1] * dx[1], dx[1], C0);
-              C0 = fmaf(N2[2] * dx[2], dx[2], C0);
-              if (A > 0.f) {
-                float disc = fmaf(B, B, -A * (C0 - cwide));
-                if (disc >= 0.f) {
-                  float sq = sqrtf(disc);
-                  float lo = (-B - sq) / A, hi = (-B + sq) / A;
-                  float mg = 1e-4f * (fabsf(lo) + fabsf(hi)) + dmarg;
-                  lo -= mg;
-                  hi += mg;
-                  // k1 = #{delta < lo}, k2 = #{delta <= hi} (sorted table)
-                  for (int st = sstep; st > 0; st >>= 1) {
-                    if (k1 + st <= S && s_dh[k1 + st - 1] < lo) k1 += st;
-                    if (k2 + st <= S && s_dh[k2 + st - 1] <= hi) k2 += st;
-                  }
-                }
-              } else if (C0 <= cwide) {
-                k2 = S;  // the sweep does not move: all or nothing
-              }
-            }
-            const int nch = k2 > k1 ? (k2 - k1 + kSrcBlock - 1) / kSrcBlock : 0;
-            const int maxch =
-                (int)__reduce_max_sync(0xffffffffu, (unsigned)nch);
-            for (int j = 0; j < maxch; ++j) {
-              bool has = j < nch;
-              unsigned mm = __ballot_sync(0xffffffffu, has);
-              if (has) {
-                int st0 = k1 + j * kSrcBlock;
-                int cnt = min(kSrcBlock, k2 - st0);
-                cring[(ct + __popc(mm & lt_mask)) & (kCandRing - 1)] =
-                    lane | (st0 << 5) | (cnt << 16);
-              }
-              ct += __popc(mm);
-              __syncwarp();
-              while (ct - ch >= 4) {
-                run_cands(4);
-                ch += 4;
-              }
-            }
-          }
-        } else {
-          for (int b = 0; b < nblk; ++b) {
-            bool pass = false;
-            if (valid) {
-              const float dmn = s_blk[2 * b], dmx = s_blk[2 * b + 1];
-              pass = true;
-#pragma unroll
-              for (int x = 0; x < 3; ++x) {
-                float u = fmaf(Gh[x], dmn, rq[x]), v = fmaf(Gh[x], dmx, rq[x]);
-                float lo = fminf(u, v) - cmarg[x],
-                      hi = fmaxf(u, v) + cmarg[x];
-                pass = pass && floorf(hi) >= ceilf(lo);
-              }
-            }
-            unsigned m = __ballot_sync(0xffffffffu, pass);
-            if (m == 0u) continue;
-            if (pass) {
-              int st0 = b * kSrcBlock;
-              int cnt = min(kSrcBlock, S - st0);
-              cring[(ct + __popc(m & lt_mask)) & (kCandRing - 1)] =
-                  lane | (st0 << 5) | (cnt << 16);
-            }
-            ct += __popc(m);
-            __syncwarp();
-            while (ct - ch >= 4) {
-              run_cands(4);
-              ch += 4;
-            }
-          }
-        }
-        if (ct > ch) {
-          run_cands(ct - ch);
-          ch = ct;
-        }
-        __syncwarp();  // the state area is rewritten by the next round
-      }
-    }
-    __syncwarp();
-    if (lane < tail - head)
-      eval_term<INTERP>(a, q, (head + lane) & (kRing - 1), acc);
-    evals += tail;
-    __syncwarp();
-
-    // ---- 4. warp reduction in FP64, fused accumulate into the image
-    double v = acc.value();
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    double v = split_pixel<INTERP, HASDIV>(a, b, P, s, f, evals);
+    // fused accumulate into the image
     if (lane == 0) a.image[gp] += a.prefactor * v;
-    __syncwarp();
   }
   if (lane == 0 && a.stats && evals) atomicAdd(a.stats, evals);
 }

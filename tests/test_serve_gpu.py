@@ -19,7 +19,7 @@ def base():
 
 
 def small_requests(n, seed):
-    return W.serving_requests(n, seed=seed, max_src=12, max_mosaic=9,
+    return W.serving_requests(n, seed=seed, max_src=12, max_mosaic=30,
                               min_pix=40, max_pix=2500)
 
 
@@ -57,8 +57,14 @@ def test_alone_equals_in_the_mix(base):
     srv.close()
 
 
-def test_server_equals_thread_kernel_on_the_same_pixels(base):
-    reqs = small_requests(4, 12)
+def test_server_equals_standalone_kernel_on_the_same_pixels(base):
+    """The server runs each request with the kernel nb_add_spots would pick
+    (one warp per pixel for >= 16 mosaic domains, else one thread per
+    pixel): its images equal the stand-alone ones bit for bit."""
+    reqs = W.serving_requests(6, seed=12, max_src=20, max_mosaic=40,
+                              min_pix=40, max_pix=1500)
+    assert any(r.umats.shape[0] >= 16 for r in reqs)
+    assert any(r.umats.shape[0] < 16 for r in reqs)
     got = run_alone(base, reqs)
     for r, g in zip(reqs, got):
         s = base.copy()
@@ -68,7 +74,7 @@ def test_server_equals_thread_kernel_on_the_same_pixels(base):
         f0, s0, nf, ns = r.roi
         pix = ((s0 + np.arange(ns))[:, None] * 3072
                + (f0 + np.arange(nf))[None, :]).ravel()
-        sim = nbgb.Sim("mixed").set_shot(s).set_variant("thread")
+        sim = nbgb.Sim("mixed").set_shot(s)
         sim.add_spots(pix)
         ref = sim.image()[pix]
         sim.close()
