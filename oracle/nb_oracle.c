@@ -45,7 +45,8 @@
  * lengths a, b, c, a fixed orientation U and three small rotation angles,
  * and returns the Poisson loss L = sum_p (I_p + bkg - y_p log(I_p + bkg))
  * with its gradient w.r.t. (tx, ty, tz, a, b, c, Na, Nb, Nc, scale) and
- * every structure factor (nearest lookup, Gaussian shape).
+ * every structure factor (Gaussian shape; nearest or tricubic lookup, the
+ * latter through the derivative of the Lagrange weights).
  */
 #include <math.h>
 #include <stdint.h>
@@ -187,6 +188,73 @@ static void lagrange4(double x, double *w)
     w[1] = (x + 1.0) * (x - 1.0) * (x - 2.0) / 2.0;
     w[2] = -(x + 1.0) * x * (x - 2.0) / 2.0;
     w[3] = (x + 1.0) * x * (x - 1.0) / 6.0;
+}
+
+/* derivatives of the 4-point Lagrange weights at x */
+static void lagrange4_deriv(double x, double *w)
+{
+    w[0] = -(3.0 * x * x - 6.0 * x + 2.0) / 6.0;
+    w[1] = (3.0 * x * x - 4.0 * x - 1.0) / 2.0;
+    w[2] = -(3.0 * x * x - 2.0 * x - 2.0) / 2.0;
+    w[3] = (3.0 * x * x - 1.0) / 6.0;
+}
+
+static size_t table_index(const orc_params *p, long ih, long ik, long il)
+{
+    return ((size_t)(ih - p->hkl_min[0]) * p->hkl_n[1] +
+            (size_t)(ik - p->hkl_min[1])) * p->hkl_n[2] +
+           (size_t)(il - p->hkl_min[2]);
+}
+
+/* F_cell at hkl with its gradient dF[3] = dF_cell/dh, and the table
+ * entries F_cell is a linear combination of: idx[n], coef[n] (n <= 64; n = 0
+ * for default_F).  Returns n. */
+int orc_fcell_lin(const orc_params *p, const double *hkl, double *Fc,
+                  double *dF, size_t *idx, double *coef)
+{
+    dF[0] = dF[1] = dF[2] = 0.0;
+    if (p->interp == 1) {
+        long fl[3];
+        for (int a = 0; a < 3; ++a)
+            fl[a] = (long)floor(hkl[a]);
+        if (in_table(p, fl[0] - 1, fl[1] - 1, fl[2] - 1) &&
+            in_table(p, fl[0] + 2, fl[1] + 2, fl[2] + 2)) {
+            double w[3][4], d[3][4];
+            for (int a = 0; a < 3; ++a) {
+                lagrange4(hkl[a] - fl[a], w[a]);
+                lagrange4_deriv(hkl[a] - fl[a], d[a]);
+            }
+            int n = 0;
+            double v = 0.0;
+            for (int i = 0; i < 4; ++i)
+                for (int j = 0; j < 4; ++j)
+                    for (int k = 0; k < 4; ++k) {
+                        size_t e = table_index(p, fl[0] - 1 + i,
+                                               fl[1] - 1 + j, fl[2] - 1 + k);
+                        double F = p->F[e];
+                        double c = w[0][i] * w[1][j] * w[2][k];
+                        v += c * F;
+                        dF[0] += d[0][i] * w[1][j] * w[2][k] * F;
+                        dF[1] += w[0][i] * d[1][j] * w[2][k] * F;
+                        dF[2] += w[0][i] * w[1][j] * d[2][k] * F;
+                        idx[n] = e;
+                        coef[n] = c;
+                        ++n;
+                    }
+            *Fc = v;
+            return n;
+        }
+    }
+    long h0 = (long)nearest_int(hkl[0]), k0 = (long)nearest_int(hkl[1]),
+         l0 = (long)nearest_int(hkl[2]);
+    if (in_table(p, h0, k0, l0)) {
+        idx[0] = table_index(p, h0, k0, l0);
+        coef[0] = 1.0;
+        *Fc = p->F[idx[0]];
+        return 1;
+    }
+    *Fc = p->default_F;
+    return 0;
 }
 
 double orc_fcell(const orc_params *p, const double *hkl)
@@ -494,37 +562,34 @@ static void pixel_grad(const orc_params *p, const double *ax,
                         double hkl[3] = {dot3(A, S), dot3(A + 3, S),
                                          dot3(A + 6, S)};
                         double Fl = orc_flatt(p, hkl);
-                        double Fc = orc_fcell(p, hkl);
+                        double Fc, dFc[3], lin_c[64];
+                        size_t lin_i[64];
+                        int nlin = orc_fcell_lin(p, hkl, &Fc, dFc, lin_i,
+                                                 lin_c);
                         double term = Fc * Fc * Fl * Fl * wfac;
-                        double fr[3], dlog[3];
+                        double fr[3], dterm[3];
                         for (int a = 0; a < 3; ++a) {
                             fr[a] = hkl[a] - nearest_int(hkl[a]);
-                            /* d log(F_latt^2) / d f_a */
-                            dlog[a] = -4.0 * N[a] * N[a] * fr[a] / 0.63;
+                            /* d term / d h_a: the lattice factor through
+                             * f_a, the structure factor through h_a */
+                            dterm[a] = term * (-4.0 * N[a] * N[a] * fr[a] / 0.63) +
+                                       2.0 * Fc * dFc[a] * Fl * Fl * wfac;
                         }
                         for (int r = 0; r < 6; ++r) {
                             const double *dA = dax + ((size_t)jm * 6 + r) * 9;
-                            dacc[r] += term * (dlog[0] * dot3(dA, S) +
-                                               dlog[1] * dot3(dA + 3, S) +
-                                               dlog[2] * dot3(dA + 6, S));
+                            dacc[r] += dterm[0] * dot3(dA, S) +
+                                       dterm[1] * dot3(dA + 3, S) +
+                                       dterm[2] * dot3(dA + 6, S);
                         }
                         /* d log(F_latt^2) / d N_a */
                         for (int a = 0; a < 3; ++a)
                             dacc[6 + a] += term * (2.0 / N[a] - 4.0 * N[a] *
                                                    fr[a] * fr[a] / 0.63);
                         if (gF) {
-                            long h0 = (long)nearest_int(hkl[0]),
-                                 k0 = (long)nearest_int(hkl[1]),
-                                 l0 = (long)nearest_int(hkl[2]);
-                            if (in_table(p, h0, k0, l0)) {
-                                size_t e = ((size_t)(h0 - p->hkl_min[0]) *
-                                                p->hkl_n[1] +
-                                            (k0 - p->hkl_min[1])) *
-                                               p->hkl_n[2] +
-                                           (l0 - p->hkl_min[2]);
-                                gF[e] += w_p * Kc * p->scale * 2.0 * Fc * Fl *
-                                         Fl * wfac;
-                            }
+                            /* F_cell is linear in the table entries */
+                            for (int t = 0; t < nlin; ++t)
+                                gF[lin_i[t]] += w_p * Kc * p->scale * 2.0 *
+                                                Fc * Fl * Fl * wfac * lin_c[t];
                         }
                     }
                 }
@@ -536,15 +601,15 @@ static void pixel_grad(const orc_params *p, const double *ax,
 
 /* Poisson loss over the pixels pix[0..n) against the target y (bkg added
  * to the model) and its gradient.  p->axes is overwritten from (U, cell,
- * rot).  Gaussian shape with nearest lookup only (else returns -3).
- * grad: 10 values (tx, ty, tz, a, b, c, Na, Nb, Nc, scale); gradF: one
+ * rot).  Gaussian shape only (else returns -3); nearest or tricubic
+ * lookup.  grad: 10 values (tx, ty, tz, a, b, c, Na, Nb, Nc, scale); gradF: one
  * value per table entry (may be NULL); model: receives I_p (n values). */
 int orc_loss_grad(orc_params *p, const double *U, const double *cell,
                   const double *rot, const long long *pix, long long n,
                   const double *y, double bkg, double *loss, double *grad,
                   double *gradF, double *model, int nthreads)
 {
-    if (p->shape != 1 || p->interp != 0)
+    if (p->shape != 1)
         return -3;
     double d_axes[6 * 9];
     orc_param_axes(U, cell, rot, p->axes, d_axes);

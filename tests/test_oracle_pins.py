@@ -469,8 +469,10 @@ def test_param_axes_derivatives_match_finite_differences():
         np.testing.assert_allclose(dax[r], (ap - am) / (2 * h), atol=1e-7)
 
 
-def test_loss_gradient_matches_finite_differences():
+@pytest.mark.parametrize("interp", [W.INTERP_NEAREST, W.INTERP_TRICUBIC])
+def test_loss_gradient_matches_finite_differences(interp):
     s = _grad_shot()
+    s.interp = interp
     U, cell, rot = _params(s)
     rng = np.random.default_rng(9)
     y = rng.poisson(2.0, size=s.npix).astype(np.float64)
