@@ -194,9 +194,11 @@ int nb_set_crystal_params(nb_sim *sim, const double U[9], const double cell[3],
  * and, when gradF (device, hkl_n[0] hkl_n[1] hkl_n[2] doubles) is not NULL,
  * adds dL/dF of every structure factor into it (scatter-add).  Every step
  * of the forward sum is recomputed in the FP32-mixed arithmetic; nothing
- * is stored between the passes.  Blocks until done.  Needs a handle made
- * with NB_MIXED, a Gaussian shape, nearest lookup, one source direction
- * and nb_set_crystal_params.  Errors: NB_ESTATE / NB_EINVAL otherwise. */
+ * is stored between the passes.  With tricubic lookup F_cell's dependence
+ * on hkl enters the crystal gradients and dL/dF is spread over the 64
+ * stencil entries.  Blocks until done.  Needs a handle made with NB_MIXED,
+ * a Gaussian shape, one source direction and nb_set_crystal_params.
+ * Errors: NB_ESTATE / NB_EINVAL otherwise. */
 int nb_adjoint(nb_sim *sim, const double *dLdI, double grad[10],
                double *gradF);
 

@@ -6,7 +6,7 @@
 // The crystal is parametrised as lab axes = rows of Rx(tx) Ry(ty) Rz(tz) U
 // diag(a, b, c) (orthorhombic cell, fixed orientation U, three small
 // rotations), Gaussian F_latt with Na, Nb, Nc, an overall scale and the
-// structure-factor table (nearest lookup).  Given w_p = dL/dI_p for every
+// structure-factor table (nearest or tricubic lookup).  Given w_p = dL/dI_p for every
 // pixel, the kernel recomputes every step of the forward sum (nothing is
 // stored between passes) and accumulates
 //   dL/dθ_r  = Σ_p w_p K scale Σ_steps term · Σ_x dlog(F_latt^2)/df_x · dh_x/dθ_r
@@ -14,8 +14,11 @@
 //   dL/dscale = Σ_p w_p I_p / scale
 //   dL/dF[h0] += w_p K scale · 2 F_cell F_latt^2 w_k cap pol ω    (scatter-add)
 // with dh_x/dθ_r = (∂A_x/∂θ_r) · (d − i)/λ and dlog(F_latt^2)/df_x =
-// −4 N_x^2 f_x / 0.63.  The per-step arithmetic is the FP32-mixed form of
-// the forward kernel (double-float fractional offsets); the ten scalar sums
+// −4 N_x^2 f_x / 0.63; with tricubic lookup F_cell also depends on h (the
+// derivative of the Lagrange weights) and dL/dF is spread over the 64
+// stencil entries with the interpolation weights.  The per-step arithmetic
+// is the FP32-mixed form of the forward kernel (double-float fractional
+// offsets); the ten scalar sums
 // go per thread into FP64, per block into a partial row, and a second
 // kernel adds the rows in a fixed order.
 #include "mixed_common.cuh"
@@ -34,8 +37,17 @@ struct AdjointArgs {
 
 constexpr int kGradN = 10;
 
-template <int HASF>
-__global__ void __launch_bounds__(kTileThreads, 4)
+// derivatives of the 4-point Lagrange weights (nodes -1, 0, 1, 2) at x
+__device__ __forceinline__ void lagrange4_deriv(float x, float w[4]) {
+  float x2 = x * x;
+  w[0] = -(3.f * x2 - 6.f * x + 2.f) * (1.f / 6.f);
+  w[1] = (3.f * x2 - 4.f * x - 1.f) * 0.5f;
+  w[2] = -(3.f * x2 - 2.f * x - 2.f) * 0.5f;
+  w[3] = (3.f * x2 - 1.f) * (1.f / 6.f);
+}
+
+template <int HASF, int INTERP>
+__global__ void __launch_bounds__(kTileThreads, INTERP ? 2 : 4)
     spots_adjoint_kernel(AdjointArgs g) {
   const SpotArgs &a = g.a;
   extern __shared__ float smf[];
@@ -168,7 +180,48 @@ __global__ void __launch_bounds__(kTileThreads, 4)
               long long fidx =
                   inside ? ((long long)n[0] * a.hn[1] + n[1]) * a.hn[2] + n[2]
                          : -1;
-              float fc = inside ? __ldg(a.F + fidx) : a.defF;
+              float fc, dfc[3] = {0.f, 0.f, 0.f};
+              // tricubic: value and gradient of the interpolant, and the
+              // stencil (its weights feed the structure-factor gradient)
+              bool tri = false;
+              int fl[3];
+              float wv[3][4];
+              if (INTERP == 1) {
+                float xs[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                  int neg = fr[c] < 0.f;
+                  fl[c] = n[c] - neg;
+                  xs[c] = neg ? 1.f + fr[c] : fr[c];
+                }
+                tri = fl[0] >= 1 && fl[0] + 2 < a.hn[0] && fl[1] >= 1 &&
+                      fl[1] + 2 < a.hn[1] && fl[2] >= 1 && fl[2] + 2 < a.hn[2];
+                if (tri) {
+                  float wd[3][4];
+#pragma unroll
+                  for (int c = 0; c < 3; ++c) {
+                    lagrange4(xs[c], wv[c]);
+                    lagrange4_deriv(xs[c], wd[c]);
+                  }
+                  fc = 0.f;
+                  for (int i = 0; i < 4; ++i)
+                    for (int j = 0; j < 4; ++j) {
+                      const float *row =
+                          a.F + ((long long)(fl[0] - 1 + i) * a.hn[1] +
+                                 (fl[1] - 1 + j)) * a.hn[2] + (fl[2] - 1);
+#pragma unroll
+                      for (int k = 0; k < 4; ++k) {
+                        float Fv = __ldg(row + k);
+                        float wij = wv[0][i] * wv[1][j];
+                        fc = fmaf(wij * wv[2][k], Fv, fc);
+                        dfc[0] = fmaf(wd[0][i] * wv[1][j] * wv[2][k], Fv, dfc[0]);
+                        dfc[1] = fmaf(wv[0][i] * wd[1][j] * wv[2][k], Fv, dfc[1]);
+                        dfc[2] = fmaf(wij * wd[2][k], Fv, dfc[2]);
+                      }
+                    }
+                }
+              }
+              if (!tri) fc = inside ? __ldg(a.F + fidx) : a.defF;
               float w = src[SRC32_W];
               float term = fc * fc * fl2 * w;
               acc0.add(term);
@@ -178,11 +231,15 @@ __global__ void __launch_bounds__(kTileThreads, 4)
                     dl1 = -4.f * N2[1] * fr[1] * (1.f / 0.63f),
                     dl2 = -4.f * N2[2] * fr[2] * (1.f / 0.63f);
               float tu = term * uk;
+              // d term / d h_x = term dlog_x + 2 F dF/dh_x F_latt^2 w
+              float fgu = 2.f * fc * fl2 * w * uk;
+              float e0 = fmaf(tu, dl0, fgu * dfc[0]),
+                    e1 = fmaf(tu, dl1, fgu * dfc[1]),
+                    e2 = fmaf(tu, dl2, fgu * dfc[2]);
 #pragma unroll
               for (int r = 0; r < 6; ++r)
-                acc[r] = fmaf(tu, fmaf(dl0, dG[r][0],
-                                       fmaf(dl1, dG[r][1], dl2 * dG[r][2])),
-                              acc[r]);
+                acc[r] = fmaf(e0, dG[r][0],
+                              fmaf(e1, dG[r][1], fmaf(e2, dG[r][2], acc[r])));
 #pragma unroll
               for (int x = 0; x < 3; ++x)
                 acc[6 + x] = fmaf(term,
@@ -190,8 +247,22 @@ __global__ void __launch_bounds__(kTileThreads, 4)
                                       4.f * a.N[x] * fr[x] * fr[x] *
                                           (1.f / 0.63f),
                                   acc[6 + x]);
-              if (HASF && inside)
-                atomicAdd(g.gradF + fidx, fscal * (double)(2.f * fc * fl2 * w));
+              if (HASF) {
+                double gv = fscal * (double)(2.f * fc * fl2 * w);
+                if (tri) {
+                  for (int i = 0; i < 4; ++i)
+                    for (int j = 0; j < 4; ++j) {
+                      long long rowi = ((long long)(fl[0] - 1 + i) * a.hn[1] +
+                                        (fl[1] - 1 + j)) * a.hn[2] + (fl[2] - 1);
+                      float wij = wv[0][i] * wv[1][j];
+#pragma unroll
+                      for (int k = 0; k < 4; ++k)
+                        atomicAdd(g.gradF + rowi + k, gv * (double)(wij * wv[2][k]));
+                    }
+                } else if (inside) {
+                  atomicAdd(g.gradF + fidx, gv);
+                }
+              }
             }
           }
           tot[9] += (double)scal * acc0.value();
@@ -284,7 +355,8 @@ cudaError_t launch_adjoint(const SpotArgs &a, const float *dax,
   long long blocks = adjoint_blocks(a);
   if (blocks <= 0) return cudaSuccess;
   void (*kern)(AdjointArgs) =
-      gradF ? spots_adjoint_kernel<1> : spots_adjoint_kernel<0>;
+      a.interp ? (gradF ? spots_adjoint_kernel<1, 1> : spots_adjoint_kernel<0, 1>)
+               : (gradF ? spots_adjoint_kernel<1, 0> : spots_adjoint_kernel<0, 0>);
   cudaError_t e = cudaFuncSetAttribute(
       kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

@@ -929,11 +929,9 @@ int nb_adjoint(nb_sim *s, const double *dLdI, double grad[10],
     return fail(s, NB_ESTATE, "crystal, beam and detector must be set first");
   if (!s->have_params)
     return fail(s, NB_ESTATE, "nb_set_crystal_params must come first");
-  if (s->precision != NB_MIXED || s->shape != NB_SHAPE_GAUSS ||
-      s->interp != NB_INTERP_NEAREST)
+  if (s->precision != NB_MIXED || s->shape != NB_SHAPE_GAUSS)
     return fail(s, NB_EINVAL,
-                "the adjoint needs NB_MIXED, a Gaussian shape and nearest "
-                "lookup");
+                "the adjoint needs NB_MIXED and a Gaussian shape");
   DeviceGuard g(s->device);
   int rc = upload_tables(s);
   if (rc != NB_OK) return rc;

@@ -19,11 +19,15 @@ THETA = dict(rot=np.array([3e-4, -2e-4, 1e-4]),
              N=np.array([14.5, 15.5, 15.2]), scale=1.1)
 
 
-def grad_shot(n_src):
+def grad_shot(n_src, interp=W.INTERP_NEAREST, n_phi=1):
     """2x2 panels of 41x37 pixels (0.11 mm) around the brightest pixel of
     a 120x120 survey of the multi-panel shot (10 domains, N=15 Gaussian,
-    nearest lookup on [-40,40]^3)."""
+    table on [-40,40]^3), with the given lookup and phi steps of 0.02 deg
+    about the spindle."""
     s = W.multipanel_shot(n_src, tiles=(1, 1), panel=(120, 120))
+    s.interp = interp
+    s.n_phi = n_phi
+    s.phistep_deg = 0.02
     U = W.random_orientation(np.random.default_rng(3))
     img = oracle.image(s).reshape(120, 120)
     js, jf = np.unravel_index(np.argmax(img), img.shape)
@@ -48,9 +52,15 @@ def with_theta(shot, U, th):
     return t
 
 
-@pytest.fixture(scope="module", params=[1, 2])
+CASES = [(1, W.INTERP_NEAREST, 1), (2, W.INTERP_NEAREST, 1),
+         (1, W.INTERP_TRICUBIC, 1), (2, W.INTERP_TRICUBIC, 3)]
+
+
+@pytest.fixture(scope="module", params=CASES,
+                ids=["nearest-S1", "nearest-S2", "tricubic-S1",
+                     "tricubic-S2-phi3"])
 def case(request):
-    shot, U = grad_shot(request.param)
+    shot, U = grad_shot(*request.param)
     truth = oracle.image(with_theta(shot, U, THETA_TRUE))
     y = np.random.default_rng(7).poisson(truth + BKG).astype(np.float64)
     s = with_theta(shot, U, THETA)
@@ -152,10 +162,16 @@ def test_adjoint_rejects_unsupported_setups():
         sim.adjoint(buf.data_ptr())
     assert e.value.code == nbgb.NB_ESTATE  # no nb_set_crystal_params yet
     t = shot.copy()
-    t.interp = W.INTERP_TRICUBIC
+    t.shape = W.SHAPE_SINC
     sim.set_crystal(t)
     sim.set_params(U, THETA["cell"], THETA["rot"], THETA["N"], 1.0)
     with pytest.raises(nbgb.NbError) as e:
         sim.adjoint(buf.data_ptr())
-    assert e.value.code == nbgb.NB_EINVAL
+    assert e.value.code == nbgb.NB_EINVAL  # sinc F_latt has no adjoint
+    sim.close()
+    sim = nbgb.Sim("f64").set_shot(shot)
+    sim.set_params(U, THETA["cell"], THETA["rot"], THETA["N"], 1.0)
+    with pytest.raises(nbgb.NbError) as e:
+        sim.adjoint(buf.data_ptr())
+    assert e.value.code == nbgb.NB_EINVAL  # the adjoint is FP32-mixed only
     sim.close()
