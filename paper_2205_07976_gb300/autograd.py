@@ -23,7 +23,8 @@ class BraggImage(torch.autograd.Function):
     params: float64 tensor of 10 (PARAM_NAMES order); F: float32 tensor of
     the structure-factor table (uploaded when it changes; its gradient is
     float64 on the image's device); sim: an nbgb.Sim set up for a shot with
-    NB_MIXED, a Gaussian shape and nearest lookup; U: 3x3 orientation.
+    NB_MIXED and a Gaussian shape (nearest or tricubic lookup); U: 3x3
+    orientation.
     Returns the image as a float64 CUDA tensor of nb_num_pixels values.
     """
 

@@ -164,7 +164,11 @@ def test_adjoint_rejects_unsupported_setups():
     t = shot.copy()
     t.shape = W.SHAPE_SINC
     sim.set_crystal(t)
-    sim.set_params(U, THETA["cell"], THETA["rot"], THETA["N"], 1.0)
+    # sinc F_latt takes whole cell counts only
+    with pytest.raises(nbgb.NbError) as e:
+        sim.set_params(U, THETA["cell"], THETA["rot"], THETA["N"], 1.0)
+    assert e.value.code == nbgb.NB_EINVAL
+    sim.set_params(U, THETA["cell"], THETA["rot"], THETA_TRUE["N"], 1.0)
     with pytest.raises(nbgb.NbError) as e:
         sim.adjoint(buf.data_ptr())
     assert e.value.code == nbgb.NB_EINVAL  # sinc F_latt has no adjoint
