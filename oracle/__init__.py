@@ -111,6 +111,14 @@ def lib():
                                       ctypes.c_double, ctypes.c_double,
                                       ctypes.c_double]
             L.orc_capture.restype = ctypes.c_double
+            L.orc_background.argtypes = [ctypes.POINTER(_Params), _dp, _dp,
+                                         ctypes.c_int, ctypes.c_double,
+                                         _llp, ctypes.c_longlong, _dp,
+                                         ctypes.c_int]
+            L.orc_background.restype = ctypes.c_int
+            L.orc_bg_factor.argtypes = [_dp, _dp, ctypes.c_int,
+                                        ctypes.c_double]
+            L.orc_bg_factor.restype = ctypes.c_double
             L.orc_max_threads.argtypes = []
             L.orc_max_threads.restype = ctypes.c_int
             L.orc_param_axes.argtypes = [_dp, _dp, _dp, _dp, _dp]
@@ -202,6 +210,31 @@ def image(shot, pixels=None, nthreads: int = 0,
     if rc != 0:
         raise ValueError(f"orc_image failed ({rc})")
     return out
+
+
+def background(shot, bg, pixels=None, nthreads: int = 0) -> np.ndarray:
+    """FP64 amorphous-background values (photons) of the given pixels: the
+    detector and beam of ``shot`` and the table of ``bg`` (attributes
+    ``stol``, ``F``, ``n_molecules``); all pixels if None."""
+    if pixels is None:
+        pixels = np.arange(shot.npix, dtype=np.int64)
+    pix = np.ascontiguousarray(np.asarray(pixels, dtype=np.int64))
+    out = np.zeros(pix.shape[0], dtype=np.float64)
+    b = _Bound(shot)
+    st, F = _f64(bg.stol), _f64(bg.F)
+    rc = lib().orc_background(ctypes.byref(b.p), _ptr(st), _ptr(F),
+                              int(st.shape[0]), float(bg.n_molecules),
+                              _ptr(pix, _llp), pix.shape[0], _ptr(out),
+                              int(nthreads))
+    if rc != 0:
+        raise ValueError(f"orc_background failed ({rc})")
+    return out
+
+
+def background_factor(bg, stol: float) -> float:
+    st, F = _f64(bg.stol), _f64(bg.F)
+    return lib().orc_bg_factor(_ptr(st), _ptr(F), int(st.shape[0]),
+                               float(stol))
 
 
 def sincg(h: float, N: float, mode: str = "reduced") -> float:

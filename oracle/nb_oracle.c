@@ -442,6 +442,107 @@ int orc_image(const orc_params *p, const long long *pix, long long n,
     return bad ? -1 : 0;
 }
 
+/* ------------------------------------------------ amorphous background */
+/*
+ * Diffuse scatter from the air and water around the crystal (the
+ * addBackground kernel of Sec. IV).  The paper names the kernel but not its
+ * physics; the convention here is ours:
+ *
+ *   for pixel p, subpixel (i, j), thickness layer t   (P, d, omega, cap as
+ *   in the spot sum), source k:
+ *     stol  = |d - i_k| / (2 lambda_k)            sin(theta) / lambda
+ *     F_bg  = the (stol, F) table interpolated linearly between its knots,
+ *             held at the end values outside them
+ *     acc  += F_bg^2 w_k cap pol omega
+ *   I_p = r_e^2 fluence n_mol acc / os^2
+ *
+ * n_mol is the number of scattering molecules in the beam; the table holds
+ * the scattering factor of one molecule.  Nothing here depends on the
+ * crystal.
+ */
+
+double orc_bg_factor(const double *stol, const double *F, int n, double x)
+{
+    if (x <= stol[0])
+        return F[0];
+    if (x >= stol[n - 1])
+        return F[n - 1];
+    int j = 0;
+    while (stol[j + 1] <= x)
+        ++j;
+    double t = (x - stol[j]) / (stol[j + 1] - stol[j]);
+    return F[j] + t * (F[j + 1] - F[j]);
+}
+
+static double background_value(const orc_params *p, const double *stol,
+                               const double *Fbg, int nk, double n_mol,
+                               int q, long s, long f)
+{
+    const double *G = p->panel_geom + 13 * q;
+    const double *O = G, *fd = G + 3, *sd = G + 6, *nd = G + 9;
+    double px = G[12];
+    int os = p->oversample;
+    double dt = p->n_layers > 0 ? p->thickness / p->n_layers : 0.0;
+    double acc = 0.0;
+    for (int i = 0; i < os; ++i)
+        for (int j = 0; j < os; ++j)
+            for (int t = 0; t < p->n_layers; ++t) {
+                double P[3], d[3];
+                for (int c = 0; c < 3; ++c)
+                    P[c] = O[c] + (f + (i + 0.5) / os) * px * fd[c] +
+                           (s + (j + 0.5) / os) * px * sd[c] +
+                           t * dt * nd[c];
+                double R = sqrt(dot3(P, P));
+                for (int c = 0; c < 3; ++c)
+                    d[c] = P[c] / R;
+                double omega = orc_omega(px, nd, P);
+                double cap = orc_capture(t, dt, p->atten, dot3(d, nd),
+                                         p->thickness);
+                for (int k = 0; k < p->n_src; ++k) {
+                    const double *inc = p->dirs + 3 * k;
+                    double v[3];
+                    for (int c = 0; c < 3; ++c)
+                        v[c] = d[c] - inc[c];
+                    double x = sqrt(dot3(v, v)) / (2.0 * p->lambdas[k]);
+                    double Fb = orc_bg_factor(stol, Fbg, nk, x);
+                    double pol = orc_polar(d, inc, p->kahn, p->evec);
+                    acc += Fb * Fb * p->weights[k] * cap * pol * omega;
+                }
+            }
+    return ORC_RE * ORC_RE * p->fluence * n_mol * acc / ((double)os * os);
+}
+
+/* background values of the pixels pix[0..n); returns 0, or -1 on a bad
+ * pixel index or table (fewer than 2 knots, knots not increasing) */
+int orc_background(const orc_params *p, const double *stol, const double *F,
+                   int nk, double n_mol, const long long *pix, long long n,
+                   double *out, int nthreads)
+{
+    if (nk < 2)
+        return -1;
+    for (int j = 0; j + 1 < nk; ++j)
+        if (!(stol[j + 1] > stol[j]))
+            return -1;
+    int bad = 0;
+#ifdef _OPENMP
+    if (nthreads <= 0)
+        nthreads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 16) num_threads(nthreads) reduction(| : bad)
+#endif
+    for (long long i = 0; i < n; ++i) {
+        int q;
+        long s, f;
+        locate(p, pix[i], &q, &s, &f);
+        if (q < 0) {
+            bad = 1;
+            out[i] = 0.0;
+            continue;
+        }
+        out[i] = background_value(p, stol, F, nk, n_mol, q, s, f);
+    }
+    return bad ? -1 : 0;
+}
+
 /* ------------------------------------------------ differentiable form */
 
 static void rot_x(double t, double *M, int deriv)

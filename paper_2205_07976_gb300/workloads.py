@@ -116,6 +116,18 @@ class Shot:
             panels=[dataclasses.replace(p) for p in self.panels])
 
 
+@dataclasses.dataclass
+class Background:
+    """Amorphous scatter (air / water around the crystal): the scattering
+    factor F of one molecule (electrons) at increasing knots of
+    stol = sin(theta)/lambda (1/Angstrom), interpolated linearly and held
+    at the end values, and the number of molecules in the beam."""
+
+    stol: np.ndarray  # (n,) strictly increasing
+    F: np.ndarray  # (n,)
+    n_molecules: float
+
+
 # --------------------------------------------------------------------------
 # random draws
 
@@ -233,6 +245,22 @@ def tiled_detector(n_tf: int, n_ts: int, nfast: int, nslow: int,
                                 ndir=np.array([0.0, 0.0, 1.0]),
                                 pixel_m=pixel_m, nfast=nfast, nslow=nslow))
     return panels
+
+
+def amorphous_background(n_knots: int = 64, stol_max: float = 1.0,
+                         n_molecules: float = 3.3e10,
+                         uneven: bool = False) -> Background:
+    """Synthetic water-like scattering curve: a smooth ring (maximum near
+    stol = 0.16/A, the 3.1 A water ring) over a slowly falling floor, F in
+    electrons (about 2.4 at the ring), sampled at n_knots knots on
+    [0, stol_max] (uneven:
+    denser towards stol = 0).  n_molecules 3.3e10 is the water in one cubic
+    micrometre."""
+    x = np.linspace(0.0, 1.0, n_knots)
+    st = stol_max * (x ** 1.5 if uneven else x)
+    F = 2.6 * (0.35 + 0.65 * np.exp(-((st - 0.16) / 0.05) ** 2)) \
+        * np.exp(-0.5 * st)
+    return Background(stol=st, F=F, n_molecules=float(n_molecules))
 
 
 # --------------------------------------------------------------------------

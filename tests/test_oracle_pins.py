@@ -526,3 +526,139 @@ def test_loss_model_equals_image():
     t = s.copy()
     t.axes, _ = oracle.param_axes(U, cell, rot)
     np.testing.assert_allclose(model, oracle.image(t), rtol=1e-14)
+
+
+# ------------------------------------------------- amorphous background
+
+
+def bg_shot(n=64, px=1e-3, dist=0.05, os_=1, lam=1.3, kahn=0.0,
+            beam_center=None, n_src=1):
+    s = tiny_shot(n=n, os_=os_)
+    s.panels = [W.flat_detector(n, n, px, dist, beam_center=beam_center)]
+    if n_src == 1:
+        s.dirs, s.lambdas, s.weights = W.monochromatic(lam)
+    s.kahn = kahn
+    return s
+
+
+def flat_table(value, n_molecules=1.0):
+    return W.Background(stol=np.array([0.0, 10.0]),
+                        F=np.array([value, value]), n_molecules=n_molecules)
+
+
+def test_background_integrates_to_rectangle_closed_form():
+    # Constant F and an unpolarized beam along the normal through the
+    # centre of a 2a x 2a panel at distance z: the summed background is
+    # r_e^2 fluence n_mol F^2 (Omega + J) / 2 with Omega the rectangle's
+    # solid angle and J = integral of cos^2(2 theta) dOmega.  With
+    # Q(z) = Omega(z)/z = integral of 1/R^3 dx dy and d(1/R^3)/dz = -3z/R^5,
+    # J = integral of z^3/R^5 dx dy = -(z^2/3) Q'(z) = (Omega - z Omega')/3.
+    n, px, z = 64, 1e-3, 0.05
+    a = b = n * px / 2
+    s2 = math.sqrt(a * a + b * b + z * z)
+    g = a * b / (z * s2)
+    om = 4 * math.atan(g)
+    dg = -a * b * (s2 * s2 + z * z) / (z * z * s2 ** 3)
+    J = (om - z * 4 * dg / (1 + g * g)) / 3
+    F, nm = 2.5, 7.0
+    exact = R_E ** 2 * 1e24 * nm * F * F * (om + J) / 2
+    sums = []
+    for os_ in (4, 8):
+        s = bg_shot(n=n, px=px, dist=z, os_=os_)
+        sums.append(oracle.background(s, flat_table(F, nm)).sum())
+    # midpoint rule: error ~ h^2, so Richardson's extrapolation is ~h^4
+    rich = (4 * sums[1] - sums[0]) / 3
+    assert abs(sums[1] - exact) < 1e-4 * exact
+    assert abs(rich - exact) < 1e-8 * exact
+
+
+def test_background_stol_is_sin_theta_over_lambda():
+    # F = 1 up to stol*, 0 beyond: only pixels whose scattering angle is
+    # below 2 arcsin(lambda stol*) see background.
+    lam, st = 1.3, 0.25
+    two_theta = 2 * math.asin(lam * st)
+    s = bg_shot(n=48, px=2e-3, dist=0.05, lam=lam)
+    bg = W.Background(stol=np.array([0.0, st, st * (1 + 1e-9), 5.0]),
+                      F=np.array([1.0, 1.0, 0.0, 0.0]), n_molecules=1.0)
+    img = oracle.background(s, bg).reshape(48, 48)
+    idx = np.arange(48) + 0.5 - 24
+    X, Y = np.meshgrid(idx * 2e-3, idx * 2e-3)
+    ang = np.arctan2(np.hypot(X, Y), 0.05)
+    inside = ang < two_theta - 1e-3
+    outside = ang > two_theta + 1e-3
+    assert inside.sum() > 100 and outside.sum() > 100
+    assert (img[inside] > 0).all()
+    assert (img[outside] == 0).all()
+
+
+def test_background_wavelength_scaling():
+    # stol scales as 1/lambda: doubling lambda and halving the knots of
+    # the table gives the same image
+    s1 = bg_shot(n=16, px=3e-3, dist=0.05, lam=1.0,
+                 beam_center=(-2.0, 3.0))
+    s2 = bg_shot(n=16, px=3e-3, dist=0.05, lam=2.0,
+                 beam_center=(-2.0, 3.0))
+    bg = W.amorphous_background(40)
+    bg2 = W.Background(stol=bg.stol / 2, F=bg.F, n_molecules=bg.n_molecules)
+    np.testing.assert_allclose(oracle.background(s1, bg),
+                               oracle.background(s2, bg2), rtol=1e-13)
+
+
+def test_background_table_is_piecewise_linear_and_held():
+    # a table of a straight line gives the same image for any knots; ends
+    # are held flat outside the table
+    s = bg_shot(n=12, px=4e-3, dist=0.04, lam=1.0, beam_center=(0.0, 0.0))
+    line = lambda x: 1.5 + 2.0 * x
+    two = W.Background(stol=np.array([0.0, 3.0]), F=line(np.array([0.0, 3.0])),
+                       n_molecules=2.0)
+    rng = np.random.default_rng(1)
+    knots = np.sort(np.concatenate([[0.0, 3.0], rng.uniform(0, 3, 30)]))
+    many = W.Background(stol=knots, F=line(knots), n_molecules=2.0)
+    a = oracle.background(s, two)
+    np.testing.assert_allclose(oracle.background(s, many), a, rtol=1e-13)
+    # a short table [0.1, 0.2] vs the same line held flat outside it
+    short = W.Background(stol=np.array([0.1, 0.2]),
+                         F=line(np.array([0.1, 0.2])), n_molecules=2.0)
+    held = W.Background(stol=np.array([-1.0, 0.1, 0.2, 9.0]),
+                        F=line(np.array([0.1, 0.1, 0.2, 0.2])),
+                        n_molecules=2.0)
+    np.testing.assert_allclose(oracle.background(s, short),
+                               oracle.background(s, held), rtol=1e-13)
+    assert oracle.background_factor(short, 0.15) == pytest.approx(line(0.15))
+    assert oracle.background_factor(short, -5.0) == line(0.1)
+    assert oracle.background_factor(short, 5.0) == line(0.2)
+
+
+def test_background_oversampling_equals_finer_pixels():
+    s = bg_shot(n=6, px=2e-3, dist=0.03, os_=2, beam_center=(1.0, 2.0))
+    s.n_layers, s.thickness_m, s.atten_m = 2, 5e-4, 3e-4
+    bg = W.amorphous_background(33)
+    a = oracle.background(s, bg).reshape(6, 6)
+    p = s.panels[0]
+    f = s.copy()
+    f.oversample = 1
+    f.panels = [W.Panel(origin=p.origin, fdir=p.fdir, sdir=p.sdir,
+                        ndir=p.ndir, pixel_m=p.pixel_m / 2, nfast=12,
+                        nslow=12)]
+    b = oracle.background(f, bg).reshape(12, 12)
+    np.testing.assert_allclose(a, b.reshape(6, 2, 6, 2).sum(axis=(1, 3)),
+                               rtol=1e-12)
+
+
+def test_background_sources_collapse_and_scale():
+    s = bg_shot(n=8, px=3e-3, dist=0.05, kahn=0.99,
+                beam_center=(-1.0, 2.5))
+    bg = W.amorphous_background(50)
+    a = oracle.background(s, bg)
+    m = s.copy()
+    m.dirs = np.repeat(s.dirs, 4, axis=0)
+    m.lambdas = np.repeat(s.lambdas, 4)
+    m.weights = np.full(4, 0.25)
+    np.testing.assert_allclose(oracle.background(m, bg), a, rtol=1e-14)
+    # linear in fluence and n_mol, quadratic in F; the crystal plays no part
+    t = s.copy()
+    t.fluence *= 3.0
+    t.axes = -t.axes
+    t.ncells = t.ncells * 2
+    bg3 = W.Background(stol=bg.stol, F=2 * bg.F, n_molecules=5 * bg.n_molecules)
+    np.testing.assert_allclose(oracle.background(t, bg3), 60 * a, rtol=1e-14)
