@@ -210,6 +210,35 @@ int nb_poisson_loss(nb_sim *sim, const double *y, double bkg, double *dLdI,
                     double *loss);
 
 /* ------------------------------------------------------------------ */
+/* Amorphous background: diffuse scatter from the air and water around the
+ * crystal (the addBackground kernel of Sec. IV; the paper does not write
+ * out its physics, so the convention is this library's):
+ *
+ *   I_p += r_e^2 fluence n_mol / os^2
+ *          * sum_{sub, layer, k} F_bg(stol_k)^2 w_k cap pol omega,
+ *   stol_k = |d - i_k| / (2 lambda_k)   (sin(theta)/lambda, 1/Angstrom),
+ *
+ * with cap, pol, omega, the subpixels, layers and sources those of the
+ * spot sum, and F_bg the scattering factor of one molecule, interpolated
+ * linearly between the knots of a table and held at its end values.
+ *
+ * nb_set_background copies the table: stol (host, n_knots strictly
+ * increasing values), F (host, n_knots values) and n_molecules >= 0, the
+ * number of scattering molecules in the beam.  Errors: NB_EINVAL for NULL,
+ * n_knots outside [2, 4096], knots not increasing, non-finite values.
+ *
+ * nb_add_background queues one launch that adds the background of every
+ * pixel into the handle's image (after, before or without the spots; the
+ * crystal is not needed).  NB_F64 handles evaluate it in FP64, NB_MIXED
+ * and NB_F32 handles in FP32 per source with a compensated sum (geometry in
+ * FP64).  Errors: NB_ESTATE before nb_set_beam, nb_set_detector and
+ * nb_set_background; NB_EINVAL if the knot and source tables exceed the
+ * kernel's 200 KB of shared memory. */
+int nb_set_background(nb_sim *sim, const double *stol, const double *F,
+                      int n_knots, double n_molecules);
+int nb_add_background(nb_sim *sim);
+
+/* ------------------------------------------------------------------ */
 /* Serving: continuous batching of shot requests on one GPU.  The paper
  * hides I/O latency by sharing a GPU between several ranks, each with its
  * own batch of images (Sec. IV, Fig. 3); here one server keeps the

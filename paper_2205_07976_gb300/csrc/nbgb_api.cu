@@ -98,6 +98,11 @@ struct nb_sim {
   int has_div = 0;
   double u0 = 0;
   bool tables_dirty = true;
+  // amorphous background: knots, scattering factors, molecules in the beam
+  bool have_bg = false;
+  std::vector<double> bg_stol, bg_F;
+  double bg_nmol = 0;
+  DevBuf d_bg64, d_bg32, d_bgrng;
 };
 
 static int fail(nb_sim *s, int code, const std::string &msg) {
@@ -521,7 +526,8 @@ int nb_free(nb_sim *sim) {
                       &sim->d_image,  &sim->d_list,  &sim->d_tmp,
                       &sim->d_stats,  &sim->d_work,  &sim->d_dax,
                       &sim->d_part,   &sim->d_grad,  &sim->d_F4,
-                      &sim->d_C4};
+                      &sim->d_C4,     &sim->d_bg64,  &sim->d_bg32,
+                      &sim->d_bgrng};
     for (DevBuf *b : bufs) b->release();
   }
   delete sim;
@@ -1007,6 +1013,134 @@ int nb_get_stats(nb_sim *s, long long *evaluated_terms,
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
   if (e != cudaSuccess) return cuda_fail(s, e, "statistics read");
   *evaluated_terms = (long long)v;
+  return NB_OK;
+}
+
+int nb_set_background(nb_sim *s, const double *stol, const double *F,
+                      int n_knots, double n_molecules) {
+  if (!s) return NB_EINVAL;
+  if (!stol || !F) return fail(s, NB_EINVAL, "NULL background table");
+  if (n_knots < 2 || n_knots > nbgb::kMaxKnots)
+    return fail(s, NB_EINVAL, "need 2 <= n_knots <= 4096");
+  for (int j = 0; j < n_knots; ++j) {
+    if (!std::isfinite(stol[j]) || !std::isfinite(F[j]))
+      return fail(s, NB_EINVAL, "background table not finite");
+    if (j > 0 && !(stol[j] > stol[j - 1]))
+      return fail(s, NB_EINVAL, "background knots must increase strictly");
+  }
+  if (!(n_molecules >= 0) || !std::isfinite(n_molecules))
+    return fail(s, NB_EINVAL, "n_molecules");
+  s->bg_stol.assign(stol, stol + n_knots);
+  s->bg_F.assign(F, F + n_knots);
+  s->bg_nmol = n_molecules;
+  s->have_bg = true;
+  return NB_OK;
+}
+
+int nb_add_background(nb_sim *s) {
+  if (!s) return NB_EINVAL;
+  if (!s->have_beam || !s->have_det || !s->have_bg)
+    return fail(s, NB_ESTATE,
+                "beam, detector and background table must be set first");
+  DeviceGuard g(s->device);
+  const int S = s->n_src, n = (int)s->bg_stol.size();
+  // group the sources (already in ascending 1/lambda) by direction; the
+  // order inside a group stays ascending
+  std::vector<int> order, rng;
+  std::vector<double> grp;
+  std::vector<char> used(S, 0);
+  for (int k = 0; k < S; ++k) {
+    if (used[k]) continue;
+    const double *dk = s->dirs.data() + 3 * k;
+    int first = (int)order.size();
+    for (int l = k; l < S; ++l) {
+      const double *dl = s->dirs.data() + 3 * l;
+      if (!used[l] && dl[0] == dk[0] && dl[1] == dk[1] && dl[2] == dk[2]) {
+        used[l] = 1;
+        order.push_back(l);
+      }
+    }
+    double ep[3], bp[3];
+    pol_basis(dk, s->evec, ep, bp);
+    for (int c = 0; c < 3; ++c) grp.push_back(dk[c]);
+    for (int c = 0; c < 3; ++c) grp.push_back(ep[c]);
+    for (int c = 0; c < 3; ++c) grp.push_back(bp[c]);
+    rng.push_back(first);
+    rng.push_back((int)order.size() - first);
+  }
+  const int G = (int)rng.size() / 2;
+  const bool f64 = s->precision == NB_F64;
+  // one double blob: groups, then (F64) knots and sources; one float blob
+  std::vector<double> b64(grp);
+  std::vector<float> b32;
+  if (f64) {
+    for (int j = 0; j < n; ++j) {
+      b64.push_back(s->bg_stol[j]);
+      b64.push_back(s->bg_F[j]);
+    }
+    for (int k : order) {
+      b64.push_back(1.0 / s->lam[k]);
+      b64.push_back(s->w[k]);
+    }
+  } else {
+    for (int j = 0; j < n; ++j) {
+      double slope = j + 1 < n ? (s->bg_F[j + 1] - s->bg_F[j]) /
+                                     (s->bg_stol[j + 1] - s->bg_stol[j])
+                               : 0.0;
+      b32.push_back((float)s->bg_stol[j]);
+      b32.push_back((float)s->bg_F[j]);
+      b32.push_back((float)slope);
+    }
+    for (int k : order) {
+      b32.push_back((float)(1.0 / s->lam[k]));
+      b32.push_back((float)s->w[k]);
+    }
+  }
+  cudaError_t e;
+  if ((e = s->d_bg64.ensure(b64.size() * 8)) != cudaSuccess ||
+      (e = s->d_bg32.ensure(std::max<size_t>(b32.size(), 1) * 4)) !=
+          cudaSuccess ||
+      (e = s->d_bgrng.ensure(rng.size() * sizeof(int))) != cudaSuccess)
+    return fail(s, NB_ENOMEM, "background tables");
+  cudaMemcpyAsync(s->d_bg64.p, b64.data(), b64.size() * 8,
+                  cudaMemcpyHostToDevice, s->stream);
+  if (!b32.empty())
+    cudaMemcpyAsync(s->d_bg32.p, b32.data(), b32.size() * 4,
+                    cudaMemcpyHostToDevice, s->stream);
+  cudaMemcpyAsync(s->d_bgrng.p, rng.data(), rng.size() * sizeof(int),
+                  cudaMemcpyHostToDevice, s->stream);
+  nbgb::BgArgs b;
+  std::memset(&b, 0, sizeof b);
+  SpotArgs &a = b.geo;
+  a.panels = (const DevPanel *)s->d_panels.p;
+  a.n_panels = (int)s->panels.size();
+  a.n_tiles = s->n_tiles;
+  a.npix = s->npix;
+  a.os = s->os;
+  a.T = s->T;
+  a.dt = s->thick > 0 ? s->thick / s->T : 0.0;
+  a.thickness = s->thick;
+  a.atten = s->atten;
+  a.S = S;
+  a.kahn64 = s->kahn;
+  a.image = (double *)s->d_image.p;
+  b.n_knots = n;
+  b.n_groups = G;
+  const double *d64 = (const double *)s->d_bg64.p;
+  b.grp64 = d64;
+  b.knots64 = d64 + 9 * G;
+  b.src64 = d64 + 9 * G + 2 * n;
+  b.knots32 = (const float *)s->d_bg32.p;
+  b.src32 = b.knots32 + 3 * n;
+  b.grp_range = (const int *)s->d_bgrng.p;
+  b.prefactor = nbgb::kElectronRadius * nbgb::kElectronRadius * s->fluence *
+                s->bg_nmol / ((double)s->os * s->os);
+  if (nbgb::background_smem_bytes(b, f64) > 200 * 1024)
+    return fail(s, NB_EINVAL,
+                "background tables exceed 200 KB of shared memory");
+  e = nbgb::launch_background(b, f64, s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e, "background launch");
+  // the pageable copies above are staged before the launch returns
   return NB_OK;
 }
 

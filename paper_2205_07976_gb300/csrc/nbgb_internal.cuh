@@ -255,4 +255,22 @@ size_t serve_warp_smem_bytes();
 cudaError_t launch_spots_mixed(const SpotArgs &a, int precision,
                                cudaStream_t st);
 
+// amorphous background: the detector and beam fields of SpotArgs plus the
+// scattering table and the sources grouped by direction (ascending 1/lambda
+// within a group)
+struct BgArgs {
+  SpotArgs geo;
+  int n_knots, n_groups;
+  const double *knots64;  // [n][2] stol, F
+  const float *knots32;   // [n][3] stol, F, slope to the next knot
+  const double *grp64;    // [G][9] direction, E', B'
+  const int *grp_range;   // [G][2] first source, count
+  const double *src64;    // [S][2] 1/lambda, w (grouped order)
+  const float *src32;     // [S][2]
+  double prefactor;       // r_e^2 fluence n_mol / os^2
+};
+constexpr int kMaxKnots = 4096;
+size_t background_smem_bytes(const BgArgs &b, bool f64);
+cudaError_t launch_background(const BgArgs &b, bool f64, cudaStream_t st);
+
 }  // namespace nbgb

@@ -71,6 +71,9 @@ SIGNATURES = {
                                              ctypes.c_double]),
     "nb_adjoint": (ctypes.c_int, [_vp, _vp, _dp, _vp]),
     "nb_poisson_loss": (ctypes.c_int, [_vp, _vp, ctypes.c_double, _vp, _dp]),
+    "nb_set_background": (ctypes.c_int, [_vp, _dp, _dp, ctypes.c_int,
+                                         ctypes.c_double]),
+    "nb_add_background": (ctypes.c_int, [_vp]),
     "nb_add_spots_noalloc": (ctypes.c_int, [
         ctypes.POINTER(NbPanel), ctypes.c_int, ctypes.c_int, ctypes.c_double,
         ctypes.c_double, _vp, ctypes.c_int, ctypes.c_double, ctypes.c_double,
@@ -272,6 +275,21 @@ class Sim:
                                         _vp(dLdI_ptr), ctypes.byref(out)),
                self.h)
         return float(out.value)
+
+    def set_background(self, bg):
+        """Copies an amorphous-background table (attributes stol, F,
+        n_molecules) into the handle."""
+        st = np.ascontiguousarray(bg.stol, dtype=np.float64)
+        F = np.ascontiguousarray(bg.F, dtype=np.float64)
+        _check(self.lib.nb_set_background(self.h, _ptr(st), _ptr(F),
+                                          int(st.shape[0]),
+                                          float(bg.n_molecules)), self.h)
+        return self
+
+    def add_background(self):
+        """Queues the background of every pixel into the image."""
+        _check(self.lib.nb_add_background(self.h), self.h)
+        return self
 
     def set_variant(self, name: str):
         _check(self.lib.nb_set_option(self.h, NB_OPT_VARIANT,
