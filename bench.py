@@ -75,8 +75,8 @@ def parse():
     ap.add_argument("--window", type=int, default=0,
                     help="time an N x N window of the large shot instead "
                          "of the whole image (for profiling)")
-    ap.add_argument("--legs", default="main,e2e,f64,cpu,serve",
-                    help="comma list of main, e2e, f64, cpu, serve")
+    ap.add_argument("--legs", default="main,e2e,f64,cpu,serve,bkg",
+                    help="comma list of main, e2e, f64, cpu, serve, bkg")
     ap.add_argument("--serve-requests", type=int, default=4096)
     ap.add_argument("--serve-seq-subset", type=int, default=16)
     return ap.parse_args()
@@ -266,6 +266,10 @@ def run_ours(args):
     f64 = None
     if "f64" in legs:
         f64 = run_f64(args, shot, local, stream, torch, nbgb, W)
+    background = None
+    if "bkg" in legs:
+        background = run_background(args, shot, local, stream, flush, torch,
+                                    nbgb, W)
 
     if rank != 0:
         return
@@ -291,6 +295,7 @@ def run_ours(args):
         "e2e": e2e,
         "f64": f64,
         "serving": serving,
+        "background": background,
         "gpu_launches": args.steps,
         "roofline": {"bound": "alu", "achieved": achieved,
                      "peak": peak_fp32, "unit": "TFLOP/s",
@@ -367,6 +372,38 @@ def run_f64(args, shot, local, stream, torch, nbgb, W):
     return {"value": len(rows) * shot.steps_per_pixel / t64, "unit": UNIT,
             "sample": f"every {args.f64_rows_every}th row "
                       f"({len(rows)} pixels)", "ms": t64 * 1e3}
+
+
+def run_background(args, shot, local, stream, flush, torch, nbgb, W):
+    """The amorphous-background kernel over the same detector, sources,
+    oversampling and layers (64-knot water-like table), both forms."""
+    bg = W.amorphous_background(64)
+    units = shot.npix * shot.oversample ** 2 * shot.n_layers * shot.n_src
+    out = {"unit": "background pixel-steps/s",
+           "pixel_steps_per_image": units,
+           "table": "64 knots on [0, 1]/A"}
+    for prec, reps in (("mixed", max(args.steps, 1)), ("f64", 1)):
+        sim = nbgb.Sim(prec, device=local, stream=stream).set_shot(shot)
+        sim.set_background(bg)
+        sim.add_background()
+        stream.synchronize()
+        times = []
+        for _ in range(reps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            sim.add_background()
+            ev1.record(stream)
+            stream.synchronize()
+            times.append(ev0.elapsed_time(ev1) / 1e3)
+        sim.close()
+        t = sum(times) / len(times)
+        key = "value" if prec == "mixed" else "f64_value"
+        out[key] = units / t
+        out["ms" if prec == "mixed" else "f64_ms"] = t * 1e3
+    return out
 
 
 def run_serving(args, local, torch, nbgb, W):

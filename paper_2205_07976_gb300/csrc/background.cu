@@ -13,8 +13,8 @@
 // per (subpixel, layer, group) the scattering vector |d - i|, the
 // polarization and the knot search are done once: stol grows with 1/lambda,
 // and the knot bracket of each further source is found by walking forward
-// from the previous one.  Geometry is FP64 in both forms; the per-source
-// work is FP64 (F64 form) or FP32 with a compensated sum (mixed form).
+// from the previous one.  The F64 form is FP64 throughout; the mixed form
+// is FP32 after the pixel's corner, with a compensated sum per group.
 #include "nbgb_internal.cuh"
 
 namespace nbgb {
@@ -38,32 +38,24 @@ __device__ __forceinline__ int bg_search(const T *st, int stride, int n,
   return lo;
 }
 
-template <int F64>
+// ------------------------------------------------------------ FP64 form
+
 __global__ void __launch_bounds__(kTileThreads)
-    background_kernel(BgArgs b) {
+    background_f64_kernel(BgArgs b) {
   const SpotArgs &a = b.geo;
   extern __shared__ double smd[];
-  double *s_grp = smd;                         // [G][9] dir, E', B'
-  double *s_k64 = s_grp + b.n_groups * 9;      // [n][2] stol, F  (F64)
-  double *s_src64 = s_k64 + (F64 ? 2 * b.n_knots : 0);  // [S][2] u, w
-  float *s_k32 = (float *)(s_src64 + (F64 ? 2 * a.S : 0));  // [n][3]
-  float *s_src32 = s_k32 + (F64 ? 0 : 3 * b.n_knots);       // [S][2]
-  int *s_rng = (int *)(s_src32 + (F64 ? 0 : 2 * a.S));      // [G][2]
+  double *s_grp = smd;                     // [G][9] dir, E', B'
+  double *s_k64 = s_grp + b.n_groups * 9;  // [n][2] stol, F
+  double *s_src = s_k64 + 2 * b.n_knots;   // [S][2] 1/lambda, w
+  int *s_rng = (int *)(s_src + 2 * a.S);   // [G][2]
   for (int i = threadIdx.x; i < b.n_groups * 9; i += blockDim.x)
     s_grp[i] = b.grp64[i];
   for (int i = threadIdx.x; i < 2 * b.n_groups; i += blockDim.x)
     s_rng[i] = b.grp_range[i];
-  if (F64) {
-    for (int i = threadIdx.x; i < 2 * b.n_knots; i += blockDim.x)
-      s_k64[i] = b.knots64[i];
-    for (int i = threadIdx.x; i < 2 * a.S; i += blockDim.x)
-      s_src64[i] = b.src64[i];
-  } else {
-    for (int i = threadIdx.x; i < 3 * b.n_knots; i += blockDim.x)
-      s_k32[i] = b.knots32[i];
-    for (int i = threadIdx.x; i < 2 * a.S; i += blockDim.x)
-      s_src32[i] = b.src32[i];
-  }
+  for (int i = threadIdx.x; i < 2 * b.n_knots; i += blockDim.x)
+    s_k64[i] = b.knots64[i];
+  for (int i = threadIdx.x; i < 2 * a.S; i += blockDim.x)
+    s_src[i] = b.src64[i];
   __syncthreads();
 
   long long gp;
@@ -72,6 +64,7 @@ __global__ void __launch_bounds__(kTileThreads)
   const DevPanel &P = a.panels[q];
   const double px = P.px;
   const int os = a.os, n = b.n_knots;
+  const double s0 = s_k64[0], sn = s_k64[2 * (n - 1)];
   double acc = 0.0;
   for (int i = 0; i < os; ++i)
     for (int j = 0; j < os; ++j)
@@ -101,52 +94,25 @@ __global__ void __launch_bounds__(kTileThreads)
                  y = bg_dot3(d, dir + 6);
           double pol = 0.5 * (1.0 + c2 * c2 - a.kahn64 * (x * x - y * y));
           const int k0 = s_rng[2 * g], k1 = k0 + s_rng[2 * g + 1];
-          double gsum;
-          if (F64) {
-            const double s0 = s_k64[0], sn = s_k64[2 * (n - 1)];
-            int jk = -1;
-            gsum = 0.0;
-            for (int k = k0; k < k1; ++k) {
-              double st = half * s_src64[2 * k];
-              double Fb;
-              if (st <= s0) {
-                Fb = s_k64[1];
-              } else if (st >= sn) {
-                Fb = s_k64[2 * (n - 1) + 1];
-              } else {
-                if (jk < 0)
-                  jk = bg_search(s_k64, 2, n, st);
-                else
-                  while (s_k64[2 * (jk + 1)] <= st) ++jk;
-                const double *kn = s_k64 + 2 * jk;
-                double tt = (st - kn[0]) / (kn[2] - kn[0]);
-                Fb = kn[1] + tt * (kn[3] - kn[1]);
-              }
-              gsum += Fb * Fb * s_src64[2 * k + 1];
+          int jk = -1;
+          double gsum = 0.0;
+          for (int k = k0; k < k1; ++k) {
+            double st = half * s_src[2 * k];
+            double Fb;
+            if (st <= s0) {
+              Fb = s_k64[1];
+            } else if (st >= sn) {
+              Fb = s_k64[2 * (n - 1) + 1];
+            } else {
+              if (jk < 0)
+                jk = bg_search(s_k64, 2, n, st);
+              else
+                while (s_k64[2 * (jk + 1)] <= st) ++jk;
+              const double *kn = s_k64 + 2 * jk;
+              double tt = (st - kn[0]) / (kn[2] - kn[0]);
+              Fb = kn[1] + tt * (kn[3] - kn[1]);
             }
-          } else {
-            const float halff = (float)half;
-            const float s0 = s_k32[0], sn = s_k32[3 * (n - 1)];
-            int jk = -1;
-            Kahan ks;
-            for (int k = k0; k < k1; ++k) {
-              float st = halff * s_src32[2 * k];
-              float Fb;
-              if (st <= s0) {
-                Fb = s_k32[1];
-              } else if (st >= sn) {
-                Fb = s_k32[3 * (n - 1) + 1];
-              } else {
-                if (jk < 0)
-                  jk = bg_search(s_k32, 3, n, st);
-                else
-                  while (s_k32[3 * (jk + 1)] <= st) ++jk;
-                const float *kn = s_k32 + 3 * jk;
-                Fb = fmaf(st - kn[0], kn[2], kn[1]);
-              }
-              ks.add(Fb * Fb * s_src32[2 * k + 1]);
-            }
-            gsum = (double)ks.value();
+            gsum += Fb * Fb * s_src[2 * k + 1];
           }
           acc += gsum * (cap * pol * omega);
         }
@@ -155,20 +121,143 @@ __global__ void __launch_bounds__(kTileThreads)
   a.image[gp] = __dadd_rn(a.image[gp], __dmul_rn(b.prefactor, acc));
 }
 
+// ----------------------------------------------------------- mixed form
+//
+// Everything after the pixel's corner is FP32.  |d - i| is formed without
+// cancellation near the direct beam: with p = pos . i and p_perp =
+// |pos x i|, d - i has the components (p - R)/R = -p_perp^2 / (R (R + p))
+// along i and p_perp / R across it.  The knot bracket (stol_j, F_j, slope_j,
+// stol_j+1) is one float4 and stays in registers while stol stays inside it.
+
+__device__ __forceinline__ float bg_dot3f(const float *a, const float *b) {
+  return fmaf(a[0], b[0], fmaf(a[1], b[1], a[2] * b[2]));
+}
+
+__global__ void __launch_bounds__(kTileThreads)
+    background_mixed_kernel(BgArgs b) {
+  const SpotArgs &a = b.geo;
+  extern __shared__ float4 smq[];
+  float4 *s_k4 = smq;                                 // [n]
+  float2 *s_src = (float2 *)(s_k4 + b.n_knots);       // [S] 1/lambda, w
+  float *s_grp = (float *)(s_src + a.S);              // [G][9]
+  int *s_rng = (int *)(s_grp + 9 * b.n_groups);       // [G][2]
+  const int n = b.n_knots;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const float *kn = b.knots32 + 3 * i;
+    s_k4[i] = make_float4(kn[0], kn[1], kn[2],
+                          i + 1 < n ? kn[3] : __int_as_float(0x7f800000));
+  }
+  for (int i = threadIdx.x; i < a.S; i += blockDim.x)
+    s_src[i] = make_float2(b.src32[2 * i], b.src32[2 * i + 1]);
+  for (int i = threadIdx.x; i < b.n_groups * 9; i += blockDim.x)
+    s_grp[i] = (float)b.grp64[i];
+  for (int i = threadIdx.x; i < 2 * b.n_groups; i += blockDim.x)
+    s_rng[i] = b.grp_range[i];
+  __syncthreads();
+
+  long long gp;
+  int q, s, f;
+  if (!map_pixel(a, (long long)blockIdx.x, threadIdx.x, gp, q, s, f)) return;
+  const DevPanel &P = a.panels[q];
+  const double px = P.px;
+  const int os = a.os;
+  const float4 kfirst = s_k4[0], klast = s_k4[n - 1];
+  const float kahn = (float)a.kahn64;
+  const float nd[3] = {(float)P.ndir[0], (float)P.ndir[1], (float)P.ndir[2]};
+  const float px2 = (float)(px * px);
+  const float dtf = (float)a.dt, attf = (float)a.atten;
+  // the pixel's corner in FP64, the subpixel offsets from it in FP32
+  float base[3], fd[3], sd[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    base[c] = (float)(P.origin[c] + f * px * P.fdir[c] + s * px * P.sdir[c]);
+    fd[c] = (float)P.fdir[c];
+    sd[c] = (float)P.sdir[c];
+  }
+  const float sub = (float)(px / os);
+  double acc = 0.0;
+  for (int i = 0; i < os; ++i)
+    for (int j = 0; j < os; ++j)
+      for (int t = 0; t < a.T; ++t) {
+        const float cf = (i + 0.5f) * sub, cs = (j + 0.5f) * sub,
+                    cn = t * dtf;
+        float pos[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          pos[c] = fmaf(cf, fd[c], fmaf(cs, sd[c], fmaf(cn, nd[c], base[c])));
+        float R2 = bg_dot3f(pos, pos);
+        float rinv = rsqrtf(R2), R = R2 * rinv;
+        float pn = bg_dot3f(nd, pos);
+        float omega = px2 * pn * (rinv * rinv * rinv);
+        float cap = 1.f;
+        if (a.thickness > 0.0) {
+          float L = attf * pn * rinv;
+          cap = __expf(-t * dtf / L) - __expf(-(t + 1) * dtf / L);
+        }
+        float fac = omega * cap;
+        for (int g = 0; g < b.n_groups; ++g) {
+          const float *dir = s_grp + 9 * g;
+          float p = bg_dot3f(pos, dir);
+          float cx = pos[1] * dir[2] - pos[2] * dir[1],
+                cy = pos[2] * dir[0] - pos[0] * dir[2],
+                cz = pos[0] * dir[1] - pos[1] * dir[0];
+          float pp2 = fmaf(cx, cx, fmaf(cy, cy, cz * cz));
+          float dd2;  // |d - i|^2
+          if (p > 0.f) {
+            float along = pp2 / (R * (R + p));
+            dd2 = fmaf(along, along, pp2 * (rinv * rinv));
+          } else {
+            float vx = pos[0] * rinv - dir[0], vy = pos[1] * rinv - dir[1],
+                  vz = pos[2] * rinv - dir[2];
+            dd2 = fmaf(vx, vx, fmaf(vy, vy, vz * vz));
+          }
+          const float half = 0.5f * sqrtf(dd2);  // sin(theta)
+          float c2 = p * rinv, x = bg_dot3f(pos, dir + 3) * rinv,
+                y = bg_dot3f(pos, dir + 6) * rinv;
+          float pol = 0.5f * (1.f + c2 * c2 - kahn * (x * x - y * y));
+          const int k0 = s_rng[2 * g], k1 = k0 + s_rng[2 * g + 1];
+          int jk = -1;
+          float4 kb = kfirst;
+          Kahan ks;
+          for (int k = k0; k < k1; ++k) {
+            const float2 uw = s_src[k];
+            const float st = half * uw.x;
+            float Fb;
+            if (st <= kfirst.x) {
+              Fb = kfirst.y;
+            } else if (st >= klast.x) {
+              Fb = klast.y;
+            } else {
+              if (jk < 0) {
+                jk = bg_search(&s_k4[0].x, 4, n, st);
+                kb = s_k4[jk];
+              }
+              while (st >= kb.w) kb = s_k4[++jk];
+              Fb = fmaf(st - kb.x, kb.z, kb.y);
+            }
+            ks.add(Fb * Fb * uw.y);
+          }
+          acc += ks.value() * (double)(fac * pol);
+        }
+      }
+  // addArray: the pixel's value is rounded first, then added (no FMA)
+  a.image[gp] = __dadd_rn(a.image[gp], __dmul_rn(b.prefactor, acc));
+}
+
 size_t background_smem_bytes(const BgArgs &b, bool f64) {
-  size_t bytes = (size_t)b.n_groups * 9 * sizeof(double) +
-                 (size_t)b.n_groups * 2 * sizeof(int);
   if (f64)
-    bytes += ((size_t)b.n_knots * 2 + (size_t)b.geo.S * 2) * sizeof(double);
-  else
-    bytes += ((size_t)b.n_knots * 3 + (size_t)b.geo.S * 2) * sizeof(float);
-  return bytes;
+    return ((size_t)b.n_groups * 9 + (size_t)b.n_knots * 2 +
+            (size_t)b.geo.S * 2) * sizeof(double) +
+           (size_t)b.n_groups * 2 * sizeof(int);
+  return (size_t)b.n_knots * sizeof(float4) + (size_t)b.geo.S * 8 +
+         (size_t)b.n_groups * 9 * sizeof(float) +
+         (size_t)b.n_groups * 2 * sizeof(int);
 }
 
 cudaError_t launch_background(const BgArgs &b, bool f64, cudaStream_t st) {
   if (b.geo.n_tiles <= 0) return cudaSuccess;
   size_t smem = background_smem_bytes(b, f64);
-  void (*kern)(BgArgs) = f64 ? background_kernel<1> : background_kernel<0>;
+  void (*kern)(BgArgs) = f64 ? background_f64_kernel : background_mixed_kernel;
   cudaError_t e = cudaFuncSetAttribute(
       kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
