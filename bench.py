@@ -377,6 +377,7 @@ def run_f64(args, shot, local, stream, torch, nbgb, W):
 def run_background(args, shot, local, stream, flush, torch, nbgb, W):
     """The amorphous-background kernel over the same detector, sources,
     oversampling and layers (64-knot water-like table), both forms."""
+    import numpy as np
     bg = W.amorphous_background(64)
     units = shot.npix * shot.oversample ** 2 * shot.n_layers * shot.n_src
     out = {"unit": "background pixel-steps/s",
@@ -403,6 +404,16 @@ def run_background(args, shot, local, stream, flush, torch, nbgb, W):
         key = "value" if prec == "mixed" else "f64_value"
         out[key] = units / t
         out["ms" if prec == "mixed" else "f64_ms"] = t * 1e3
+        if prec == "mixed":
+            from paper_2205_07976_gb300 import flops
+            ndir = len({tuple(d) for d in np.asarray(shot.dirs)})
+            alg = flops.background_flops(shot, ndir)
+            peak = flops.fp32_peak_tflops(152, 2070.0)
+            out["roofline"] = {"bound": "alu", "achieved": alg / t / 1e12,
+                               "peak": peak, "unit": "TFLOP/s",
+                               "frac": alg / t / 1e12 / peak,
+                               "kernel": "background_mixed_kernel",
+                               "algorithmic_tflop_per_launch": alg / 1e12}
     return out
 
 

@@ -126,8 +126,9 @@ __global__ void __launch_bounds__(kTileThreads)
 // Everything after the pixel's corner is FP32.  |d - i| is formed without
 // cancellation near the direct beam: with p = pos . i and p_perp =
 // |pos x i|, d - i has the components (p - R)/R = -p_perp^2 / (R (R + p))
-// along i and p_perp / R across it.  The knot bracket (stol_j, F_j, slope_j,
-// stol_j+1) is one float4 and stays in registers while stol stays inside it.
+// along i and p_perp / R across it.  The current interval (start, F,
+// slope, end) is one float4 in registers; the held ends are intervals of
+// slope 0, so each source costs one compare to stay or walk on.
 
 __device__ __forceinline__ float bg_dot3f(const float *a, const float *b) {
   return fmaf(a[0], b[0], fmaf(a[1], b[1], a[2] * b[2]));
@@ -137,15 +138,27 @@ __global__ void __launch_bounds__(kTileThreads)
     background_mixed_kernel(BgArgs b) {
   const SpotArgs &a = b.geo;
   extern __shared__ float4 smq[];
-  float4 *s_k4 = smq;                                 // [n]
-  float2 *s_src = (float2 *)(s_k4 + b.n_knots);       // [S] 1/lambda, w
+  // intervals e = 0..n: e = 0 holds F_0 below stol_0, e = j + 1 is the
+  // knot interval [stol_j, stol_j+1), e = n holds F_n-1 from stol_n-1 on;
+  // each is (start, F at start, slope, end)
+  float4 *s_k4 = smq;                                 // [n + 1]
+  float2 *s_src = (float2 *)(s_k4 + b.n_knots + 1);   // [S] 1/lambda, w
   float *s_grp = (float *)(s_src + a.S);              // [G][9]
   int *s_rng = (int *)(s_grp + 9 * b.n_groups);       // [G][2]
   const int n = b.n_knots;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const float *kn = b.knots32 + 3 * i;
-    s_k4[i] = make_float4(kn[0], kn[1], kn[2],
-                          i + 1 < n ? kn[3] : __int_as_float(0x7f800000));
+  const float inf = __int_as_float(0x7f800000);
+  for (int e = threadIdx.x; e <= n; e += blockDim.x) {
+    float4 v;
+    if (e == 0) {
+      v = make_float4(b.knots32[0], b.knots32[1], 0.f, b.knots32[0]);
+    } else if (e == n) {
+      const float *kn = b.knots32 + 3 * (n - 1);
+      v = make_float4(kn[0], kn[1], 0.f, inf);
+    } else {
+      const float *kn = b.knots32 + 3 * (e - 1);
+      v = make_float4(kn[0], kn[1], kn[2], kn[3]);
+    }
+    s_k4[e] = v;
   }
   for (int i = threadIdx.x; i < a.S; i += blockDim.x)
     s_src[i] = make_float2(b.src32[2 * i], b.src32[2 * i + 1]);
@@ -161,7 +174,7 @@ __global__ void __launch_bounds__(kTileThreads)
   const DevPanel &P = a.panels[q];
   const double px = P.px;
   const int os = a.os;
-  const float4 kfirst = s_k4[0], klast = s_k4[n - 1];
+  const float s_first = s_k4[0].x, s_last = s_k4[n].x;
   const float kahn = (float)a.kahn64;
   const float nd[3] = {(float)P.ndir[0], (float)P.ndir[1], (float)P.ndir[2]};
   const float px2 = (float)(px * px);
@@ -216,25 +229,23 @@ __global__ void __launch_bounds__(kTileThreads)
                 y = bg_dot3f(pos, dir + 6) * rinv;
           float pol = 0.5f * (1.f + c2 * c2 - kahn * (x * x - y * y));
           const int k0 = s_rng[2 * g], k1 = k0 + s_rng[2 * g + 1];
-          int jk = -1;
-          float4 kb = kfirst;
+          if (k0 >= k1) continue;
+          // interval of the group's first (smallest) stol, then walk
+          int e;
+          {
+            const float st = half * s_src[k0].x;
+            e = st < s_first ? 0
+                : st >= s_last ? n
+                               : 1 + bg_search(&s_k4[1].x, 4, n, st);
+          }
+          float4 kb = s_k4[e];
           Kahan ks;
+#pragma unroll 2
           for (int k = k0; k < k1; ++k) {
             const float2 uw = s_src[k];
             const float st = half * uw.x;
-            float Fb;
-            if (st <= kfirst.x) {
-              Fb = kfirst.y;
-            } else if (st >= klast.x) {
-              Fb = klast.y;
-            } else {
-              if (jk < 0) {
-                jk = bg_search(&s_k4[0].x, 4, n, st);
-                kb = s_k4[jk];
-              }
-              while (st >= kb.w) kb = s_k4[++jk];
-              Fb = fmaf(st - kb.x, kb.z, kb.y);
-            }
+            while (st >= kb.w) kb = s_k4[++e];
+            const float Fb = fmaf(st - kb.x, kb.z, kb.y);
             ks.add(Fb * Fb * uw.y);
           }
           acc += ks.value() * (double)(fac * pol);
@@ -249,7 +260,7 @@ size_t background_smem_bytes(const BgArgs &b, bool f64) {
     return ((size_t)b.n_groups * 9 + (size_t)b.n_knots * 2 +
             (size_t)b.geo.S * 2) * sizeof(double) +
            (size_t)b.n_groups * 2 * sizeof(int);
-  return (size_t)b.n_knots * sizeof(float4) + (size_t)b.geo.S * 8 +
+  return (size_t)(b.n_knots + 1) * sizeof(float4) + (size_t)b.geo.S * 8 +
          (size_t)b.n_groups * 9 * sizeof(float) +
          (size_t)b.n_groups * 2 * sizeof(int);
 }

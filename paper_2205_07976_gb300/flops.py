@@ -48,6 +48,22 @@ def algorithmic_flops(shot, evaluated_terms: int, pixels: int = None) -> float:
                  + ITEM * items + UNIT * units)
 
 
+# amorphous background, per (subpixel, layer, source) step: stol = sin(theta)
+# u_k (1), linear interpolation (sub + FMA, 3), F^2 w (2), accumulate (1);
+# per (subpixel, layer, direction): |d - i|, polarization (25); per
+# (subpixel, layer): position, |P|, solid angle, capture (35)
+BG_STEP = 7
+BG_GROUP = 25
+BG_UNIT = 35
+
+
+def background_flops(shot, n_directions: int = 1) -> float:
+    """FP32 flops of the amorphous background of every pixel of `shot`."""
+    units = shot.npix * shot.oversample ** 2 * shot.n_layers
+    return float(units * (BG_UNIT + BG_GROUP * n_directions
+                          + BG_STEP * shot.n_src))
+
+
 def fp32_peak_tflops(sm_count: int = 152, mhz: float = 2070.0) -> float:
     """FP32 FMA peak: SMs x 128 lanes x 2 flops x clock."""
     return sm_count * 128 * 2 * mhz * 1e6 / 1e12
