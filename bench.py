@@ -47,10 +47,11 @@ FP32_LANES_PER_SM = 128
 # DRAM bytes (read + write) of one full-size launch of the warp-per-pixel
 # kernel, from one ncu capture (profiles/spots_split_large_shot_dram.txt);
 # valid only while the kernel sources hash to the value they had then
-TRAFFIC_CAPTURE = {"bytes": 78721280 + 28223488,
+TRAFFIC_CAPTURE = {"bytes": 79241216 + 28697088,
                    "sources": ["paper_2205_07976_gb300/csrc/spots_split.cu",
+                               "paper_2205_07976_gb300/csrc/split_pixel.cuh",
                                "paper_2205_07976_gb300/csrc/mixed_common.cuh"],
-                   "sha256_16": "2aafbb68d3f83da3"}
+                   "sha256_16": "50acf676f1ee06d6"}
 
 
 def captured_traffic():
