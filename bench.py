@@ -51,7 +51,7 @@ TRAFFIC_CAPTURE = {"bytes": 79241216 + 28697088,
                    "sources": ["paper_2205_07976_gb300/csrc/spots_split.cu",
                                "paper_2205_07976_gb300/csrc/split_pixel.cuh",
                                "paper_2205_07976_gb300/csrc/mixed_common.cuh"],
-                   "sha256_16": "50acf676f1ee06d6"}
+                   "sha256_16": "aa17962f9065fda9"}
 
 
 def captured_traffic():

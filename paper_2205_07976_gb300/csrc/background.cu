@@ -14,7 +14,8 @@
 // polarization and the knot search are done once: stol grows with 1/lambda,
 // and the knot bracket of each further source is found by walking forward
 // from the previous one.  The F64 form is FP64 throughout; the mixed form
-// is FP32 after the pixel's corner, with a compensated sum per group.
+// is FP32 after the pixel's corner, with compensated sums per group and
+// per pixel.
 #include "nbgb_internal.cuh"
 
 namespace nbgb {
@@ -188,7 +189,7 @@ __global__ void __launch_bounds__(kTileThreads)
     sd[c] = (float)P.sdir[c];
   }
   const float sub = (float)(px / os);
-  double acc = 0.0;
+  Kahan acc;  // over (subpixel, layer, group) of the group sums
   for (int i = 0; i < os; ++i)
     for (int j = 0; j < os; ++j)
       for (int t = 0; t < a.T; ++t) {
@@ -248,11 +249,11 @@ __global__ void __launch_bounds__(kTileThreads)
             const float Fb = fmaf(st - kb.x, kb.z, kb.y);
             ks.add(Fb * Fb * uw.y);
           }
-          acc += ks.value() * (double)(fac * pol);
+          acc.add(__fsub_rn(ks.s, ks.c) * (fac * pol));
         }
       }
   // addArray: the pixel's value is rounded first, then added (no FMA)
-  a.image[gp] = __dadd_rn(a.image[gp], __dmul_rn(b.prefactor, acc));
+  a.image[gp] = __dadd_rn(a.image[gp], __dmul_rn(b.prefactor, acc.value()));
 }
 
 size_t background_smem_bytes(const BgArgs &b, bool f64) {

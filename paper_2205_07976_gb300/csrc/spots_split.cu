@@ -10,12 +10,19 @@
 //   1. lanes 0..U-1 set up the U = os^2 x layers sub-pixel units of the
 //      pixel in FP64 (position, direction, solid angle, capture,
 //      polarization) into shared memory;
-//   2. lanes take (unit, phi x mosaic) items round-robin, form G and r in
-//      double-float, and scan all sources with a 7-flop-per-axis fractional
-//      offset; a step whose exponent sum N^2 f^2 / 0.63 stays below the
-//      underflow cut is pushed into a per-warp ring in shared memory;
-//   3. whenever the ring holds 32 terms, every lane evaluates one of them
-//      (exp, F_cell lookup, product) into its own Kahan sum;
+//   2. lanes take (unit, phi x mosaic) items round-robin and form G and r
+//      in double-float.  h_x = G_x delta + r_x is linear in a source's
+//      delta = 1/lambda - u0, so for each lattice point near the item's
+//      sweep the sources whose exponent sum N^2 f^2 / 0.63 can stay below
+//      the underflow cut form one interval of the sorted delta table (a
+//      quadratic in delta, then a binary search); where that does not
+//      apply, blocks of 8 sources are pruned by their delta range.  The
+//      surviving (lane, source range) pairs go into a candidate ring, the
+//      warp tests 32 sources at a time, and steps below the cut are pushed
+//      into a per-warp term ring in shared memory;
+//   3. whenever the term ring holds 32 terms, every lane evaluates one of
+//      them (exp, F_cell from the cell's tricubic polynomial or the table,
+//      product) into its own Kahan sum;
 //   4. the 32 lane sums are reduced with warp shuffles in FP64.
 // The order of every operation depends only on the pixel's own inputs, so
 // a pixel's value does not depend on what else is in the launch.
