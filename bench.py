@@ -76,8 +76,9 @@ def parse():
     ap.add_argument("--window", type=int, default=0,
                     help="time an N x N window of the large shot instead "
                          "of the whole image (for profiling)")
-    ap.add_argument("--legs", default="main,e2e,f64,cpu,serve,bkg",
-                    help="comma list of main, e2e, f64, cpu, serve, bkg")
+    ap.add_argument("--legs", default="main,e2e,f64,cpu,serve,bkg,grad",
+                    help="comma list of main, e2e, f64, cpu, serve, bkg, "
+                         "grad")
     ap.add_argument("--serve-requests", type=int, default=4096)
     ap.add_argument("--serve-seq-subset", type=int, default=16)
     return ap.parse_args()
@@ -267,6 +268,9 @@ def run_ours(args):
     f64 = None
     if "f64" in legs:
         f64 = run_f64(args, shot, local, stream, torch, nbgb, W)
+    differentiation = None
+    if "grad" in legs:
+        differentiation = run_grad(args, local, stream, torch, nbgb, W)
     background = None
     if "bkg" in legs:
         background = run_background(args, shot, local, stream, flush, torch,
@@ -297,6 +301,7 @@ def run_ours(args):
         "f64": f64,
         "serving": serving,
         "background": background,
+        "differentiation": differentiation,
         "gpu_launches": args.steps,
         "roofline": {"bound": "alu", "achieved": achieved,
                      "peak": peak_fp32, "unit": "TFLOP/s",
@@ -373,6 +378,63 @@ def run_f64(args, shot, local, stream, torch, nbgb, W):
     return {"value": len(rows) * shot.steps_per_pixel / t64, "unit": UNIT,
             "sample": f"every {args.f64_rows_every}th row "
                       f"({len(rows)} pixels)", "ms": t64 * 1e3}
+
+
+def run_grad(args, local, stream, torch, nbgb, W):
+    """One refinement step of the differentiation workload (64 panels of
+    185x194, 8 sources, 10 mosaic domains, N=15 Gaussian, nearest lookup on
+    [-40,40]^3): forward image, Poisson loss with dL/dI, and the adjoint
+    with the gradients of the 10 crystal parameters and of every structure
+    factor.  The target is a seeded Poisson draw of the forward image."""
+    import numpy as np
+    shot = W.multipanel_shot(8)
+    U = W.random_orientation(np.random.default_rng(3))
+    cell, rot = np.array([79.0, 79.0, 38.0]), np.zeros(3)
+    N = np.array([15.0, 15.0, 15.0])
+    dev = torch.device("cuda", local)
+    sim = nbgb.Sim("mixed", device=local, stream=stream).set_shot(shot)
+    sim.set_params(U, cell, rot, N, 1.0)
+    sim.add_spots()
+    y = np.random.default_rng(7).poisson(sim.image() + 1.0).astype(np.float64)
+    yd = torch.from_numpy(y).to(dev)
+    dL = torch.empty_like(yd)
+    gF = torch.zeros(shot.F.size, dtype=torch.float64, device=dev)
+    torch.cuda.synchronize(dev)
+
+    def one():
+        sim.zero()
+        sim.add_spots()
+        sim.poisson_loss(yd.data_ptr(), 1.0, dL.data_ptr())
+        return sim.adjoint(dL.data_ptr(), gF.data_ptr())
+
+    for _ in range(max(args.warmup, 1)):
+        one()
+    reps = max(args.steps, 1)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    tf = tl = ta = 0.0
+    for _ in range(reps):
+        ev[0].record(stream)
+        sim.zero()
+        sim.add_spots()
+        ev[1].record(stream)
+        sim.poisson_loss(yd.data_ptr(), 1.0, dL.data_ptr())
+        ev[2].record(stream)
+        sim.adjoint(dL.data_ptr(), gF.data_ptr())
+        ev[3].record(stream)
+        stream.synchronize()
+        tf += ev[0].elapsed_time(ev[1]) / 1e3
+        tl += ev[1].elapsed_time(ev[2]) / 1e3
+        ta += ev[2].elapsed_time(ev[3]) / 1e3
+    sim.close()
+    tf, tl, ta = tf / reps, tl / reps, ta / reps
+    steps = shot.pixel_steps
+    return {"workload": "64 panels of 185x194, S=8, M=10, N=15 Gaussian, "
+                        "nearest F on [-40,40]^3",
+            "pixel_steps_per_pass": steps,
+            "forward_ms": tf * 1e3, "loss_ms": tl * 1e3,
+            "adjoint_ms": ta * 1e3, "step_ms": (tf + tl + ta) * 1e3,
+            "adjoint_pixel_steps_per_s": steps / ta,
+            "unit": "pixel-steps/s"}
 
 
 def run_background(args, shot, local, stream, flush, torch, nbgb, W):
