@@ -125,6 +125,8 @@ __global__ void __launch_bounds__(kSplitThreads, 6)
   int staged = -1;
   SplitBlock b;
   unsigned long long evals = 0;
+  const int U = base.os * base.os * base.T;
+  const int B = kMaxUnits / U;
   while (true) {
     if (threadIdx.x == 0) s_item = (int)atomicAdd(counter, 1u);
     __syncthreads();
@@ -138,12 +140,28 @@ __global__ void __launch_bounds__(kSplitThreads, 6)
                   sp.u0l);
       staged = w.slot;
     }
-    for (int j = warp; j < w.count; j += kSplitWarps) {
-      long long p = w.first + j;
-      int s = sp.s0 + (int)(p / sp.nf);
-      int f = sp.f0 + (int)(p % sp.nf);
-      double v = split_pixel<INTERP, 0>(base, b, P, s, f, evals);
-      if (lane == 0) pool[sp.img_off + p] = sp.prefactor * v;
+    // the warp's pixels j = warp, warp + 4, ...: sub-pixel units of B of
+    // them at a time in one pass (the FP64 geometry fills the lanes), then
+    // the sums one after another
+    float *unit = b.unit_base + warp * kMaxUnits * kUnitFloats;
+    const int npx = (w.count - warp + kSplitWarps - 1) / kSplitWarps;
+    for (int i0 = 0; i0 < npx; i0 += B) {
+      const int nb = min(B, npx - i0);
+      if (lane < nb * U) {
+        const int bi = lane / U;
+        const long long p = w.first + warp + (long long)(i0 + bi) * kSplitWarps;
+        const int s = sp.s0 + (int)(p / sp.nf);
+        const int f = sp.f0 + (int)(p % sp.nf);
+        split_unit<0>(base, P, s, f, lane - bi * U, unit + lane * kUnitFloats);
+      }
+      __syncwarp();
+      for (int bi = 0; bi < nb; ++bi) {
+        const long long p = w.first + warp + (long long)(i0 + bi) * kSplitWarps;
+        const double v = split_sum<INTERP, 0>(
+            base, b, unit + bi * U * kUnitFloats, evals);
+        if (lane == 0) pool[sp.img_off + p] = sp.prefactor * v;
+      }
+      __syncwarp();  // the next batch rewrites the units
     }
     __syncthreads();  // the tables may be restaged for the next item
   }

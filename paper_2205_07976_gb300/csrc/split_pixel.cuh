@@ -1,7 +1,8 @@
 // split_pixel.cuh -- the warp-per-pixel FP32-mixed Bragg-spot sum for
 // Gaussian shapes, shared by the stand-alone kernel (spots_split.cu) and the
-// serving kernel (serve.cu): table staging (split_stage) and the per-pixel
-// sum of one warp (split_pixel).  See spots_split.cu for the method.
+// serving kernel (serve.cu): table staging (split_stage), the FP64 set-up of
+// one sub-pixel unit (split_unit) and the per-pixel sum of one warp
+// (split_sum).  See spots_split.cu for the method.
 #pragma once
 
 #include "mixed_common.cuh"
@@ -165,24 +166,79 @@ __device__ __forceinline__ void split_stage(SplitBlock &b, float *sms,
   b.sstep = sstep;
 }
 
-// The sum of pixel (s, f) of panel P without the prefactor, computed by the
-// calling warp (all 32 lanes); every lane returns the same value.  Adds the
-// number of evaluated terms to `evals`.
+// Geometry of sub-pixel unit u (subpixel i, j, sensor layer t) of pixel
+// (s, f) of panel P into ud[kUnitFloats]: v = d - i0 as double-float,
+// omega cap (times the polarization for one beam direction), and d in FP32.
+template <int HASDIV>
+__device__ __forceinline__ void split_unit(const SpotArgs &a,
+                                           const DevPanel &P, int s, int f,
+                                           int u, float *ud) {
+  const int os = a.os;
+  const float kahn = a.kahn;
+  int t = u % a.T, ij = u / a.T, i = ij / os, j = ij % os;
+  double px = P.px;
+  double cf = (f + (i + 0.5) / os) * px, cs = (s + (j + 0.5) / os) * px,
+         cn = t * a.dt;
+  double pos[3], d[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+    pos[c] = P.origin[c] + cf * P.fdir[c] + cs * P.sdir[c] +
+             cn * P.ndir[c];
+  // FP64 only where h needs it: one reciprocal of |P|, d = P / |P|
+  double R = sqrt(dot3d_m(pos, pos));
+  double inv = 1.0 / R;
+  float df[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    d[c] = pos[c] * inv;
+    double v = d[c] - a.i0[c];
+    float vh = (float)v;
+    ud[c] = vh;
+    ud[3 + c] = (float)(v - (double)vh);
+    df[c] = (float)d[c];
+    ud[7 + c] = df[c];
+  }
+  float invf = (float)inv;
+  float omega = (float)(px * px) * (float)dot3d_m(P.ndir, pos) * invf *
+                invf * invf;
+  float cap = 1.f;
+  if (a.thickness > 0.0) {
+    float rho = df[0] * (float)P.ndir[0] + df[1] * (float)P.ndir[1] +
+                df[2] * (float)P.ndir[2];
+    float L = (float)a.atten * rho, dtf = (float)a.dt;
+    cap = expf(-t * dtf / L) - expf(-(t + 1) * dtf / L);
+  }
+  float scal = omega * cap;
+  if (!HASDIV) {
+    float c2 = df[0] * (float)a.i0[0] + df[1] * (float)a.i0[1] +
+               df[2] * (float)a.i0[2];
+    float x = df[0] * (float)a.e0[0] + df[1] * (float)a.e0[1] +
+              df[2] * (float)a.e0[2];
+    float y = df[0] * (float)a.b0[0] + df[1] * (float)a.b0[1] +
+              df[2] * (float)a.b0[2];
+    scal *= 0.5f * (1.f + c2 * c2 - kahn * (x * x - y * y));
+  }
+  ud[6] = scal;
+}
+
+// The sum, without the prefactor, of the pixel whose U sub-pixel units are
+// already in `unit` (split_unit), computed by the calling warp (all 32
+// lanes); every lane returns the same value.  Adds the number of evaluated
+// terms to `evals`.
 template <int INTERP, int HASDIV>
-__device__ __forceinline__ double split_pixel(const SpotArgs &a,
-                                              const SplitBlock &b,
-                                              const DevPanel &P, int s, int f,
-                                              unsigned long long &evals) {
+__device__ __forceinline__ double split_sum(const SpotArgs &a,
+                                            const SplitBlock &b,
+                                            const float *unit,
+                                            unsigned long long &evals) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int PM = b.PM, S = b.S, nblk = b.nblk, sstep = b.sstep;
   const float *s_axh = b.axh, *s_axl = b.axl, *s_src = b.src, *s_blk = b.blk,
               *s_dh = b.dh;
-  float *unit = b.unit_base + warp * kMaxUnits * kUnitFloats;
   SplitRing &q = b.rings[warp];
   float *st = b.state_base + warp * 32 * kStateStride;
   int *cring = b.cring_base + warp * kCandRing;
   const unsigned lt_mask = (1u << lane) - 1u;
-  const int os = a.os, U = a.os * a.os * a.T, items = U * PM;
+  const int U = a.os * a.os * a.T, items = U * PM;
   const float cutg = kGaussCut * 0.63f;
   const float kahn = a.kahn;
   const float N2[3] = {a.N[0] * a.N[0], a.N[1] * a.N[1], a.N[2] * a.N[2]};
@@ -191,56 +247,6 @@ __device__ __forceinline__ double split_pixel(const SpotArgs &a,
   const bool iv_ok = b.iv_ok;
   const float dmin = b.dmin, dmax = b.dmax, dmarg = b.dmarg;
   const float u0h = b.u0h, u0l = b.u0l;
-
-  // ---- 1. per-unit geometry (FP64) into shared memory
-  for (int u = lane; u < U; u += 32) {
-    int t = u % a.T, ij = u / a.T, i = ij / os, j = ij % os;
-    double px = P.px;
-    double cf = (f + (i + 0.5) / os) * px, cs = (s + (j + 0.5) / os) * px,
-           cn = t * a.dt;
-    double pos[3], d[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-      pos[c] = P.origin[c] + cf * P.fdir[c] + cs * P.sdir[c] +
-               cn * P.ndir[c];
-    // FP64 only where h needs it: one reciprocal of |P|, d = P / |P|
-    double R = sqrt(dot3d_m(pos, pos));
-    double inv = 1.0 / R;
-    float *ud = unit + u * kUnitFloats;
-    float df[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      d[c] = pos[c] * inv;
-      double v = d[c] - a.i0[c];
-      float vh = (float)v;
-      ud[c] = vh;
-      ud[3 + c] = (float)(v - (double)vh);
-      df[c] = (float)d[c];
-      ud[7 + c] = df[c];
-    }
-    float invf = (float)inv;
-    float omega = (float)(px * px) * (float)dot3d_m(P.ndir, pos) * invf *
-                  invf * invf;
-    float cap = 1.f;
-    if (a.thickness > 0.0) {
-      float rho = df[0] * (float)P.ndir[0] + df[1] * (float)P.ndir[1] +
-                  df[2] * (float)P.ndir[2];
-      float L = (float)a.atten * rho, dtf = (float)a.dt;
-      cap = expf(-t * dtf / L) - expf(-(t + 1) * dtf / L);
-    }
-    float scal = omega * cap;
-    if (!HASDIV) {
-      float c2 = df[0] * (float)a.i0[0] + df[1] * (float)a.i0[1] +
-                 df[2] * (float)a.i0[2];
-      float x = df[0] * (float)a.e0[0] + df[1] * (float)a.e0[1] +
-                df[2] * (float)a.e0[2];
-      float y = df[0] * (float)a.b0[0] + df[1] * (float)a.b0[1] +
-                df[2] * (float)a.b0[2];
-      scal *= 0.5f * (1.f + c2 * c2 - kahn * (x * x - y * y));
-    }
-    ud[6] = scal;
-  }
-  __syncwarp();
 
   // ---- 2./3. scan the steps, evaluate surviving terms 32 at a time
   Kahan acc;

@@ -7,9 +7,10 @@
 // does not underflow in FP32, and each such term needs the structure factor
 // (64 gathers for tricubic interpolation).  With one thread per pixel those
 // terms are scattered over lanes and a warp serialises them.  Here:
-//   1. lanes 0..U-1 set up the U = os^2 x layers sub-pixel units of the
-//      pixel in FP64 (position, direction, solid angle, capture,
-//      polarization) into shared memory;
+//   1. a warp takes B = 32 / U pixels at a time; its lanes set up the
+//      U = os^2 x layers sub-pixel units of all B pixels in FP64 (position,
+//      direction, solid angle, capture, polarization) into shared memory,
+//      then the warp sums the pixels one after another;
 //   2. lanes take (unit, phi x mosaic) items round-robin and form G and r
 //      in double-float.  h_x = G_x delta + r_x is linear in a source's
 //      delta = 1/lambda - u0, so for each lattice point near the item's
@@ -37,23 +38,40 @@ __global__ void __launch_bounds__(kSplitThreads, 6)
   extern __shared__ float sms[];
   SplitBlock b;
   split_stage(b, sms, a, a.axh, a.axl, a.src32, a.PM, a.S, a.u0h, a.u0l);
-  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long n_work = a.pixlist ? a.n_list : a.npix;
   unsigned long long evals = 0;  // terms evaluated by this warp
+  // a warp takes B pixels at a time and sets up all their sub-pixel units
+  // in one pass, so the FP64 geometry fills up to 32 lanes
+  const int U = a.os * a.os * a.T;
+  const int B = kMaxUnits / U;
+  float *unit = b.unit_base + warp * kMaxUnits * kUnitFloats;
   while (true) {
-    long long item_pix = 0;
-    if (lane == 0) item_pix = (long long)atomicAdd(work, 1ULL);
-    item_pix = __shfl_sync(0xffffffffu, item_pix, 0);
-    if (item_pix >= n_work) break;
-    long long gp = a.pixlist ? a.pixlist[item_pix] : item_pix;
-    int qp = panel_of_pixel(a, gp);
-    const DevPanel &P = a.panels[qp];
-    long long local = gp - P.pix0;
-    int s = (int)(local / P.nfast);
-    int f = (int)(local - (long long)s * P.nfast);
-    double v = split_pixel<INTERP, HASDIV>(a, b, P, s, f, evals);
-    // fused accumulate into the image
-    if (lane == 0) a.image[gp] += a.prefactor * v;
+    long long first = 0;
+    if (lane == 0) first = (long long)atomicAdd(work, (unsigned long long)B);
+    first = __shfl_sync(0xffffffffu, first, 0);
+    if (first >= n_work) break;
+    const int nb = (int)min((long long)B, n_work - first);
+    if (lane < nb * U) {
+      const int bi = lane / U;
+      const long long gp = a.pixlist ? a.pixlist[first + bi] : first + bi;
+      const DevPanel &P = a.panels[panel_of_pixel(a, gp)];
+      const long long local = gp - P.pix0;
+      const int s = (int)(local / P.nfast);
+      const int f = (int)(local - (long long)s * P.nfast);
+      split_unit<HASDIV>(a, P, s, f, lane - bi * U, unit + lane * kUnitFloats);
+    }
+    __syncwarp();
+    for (int bi = 0; bi < nb; ++bi) {
+      const double v = split_sum<INTERP, HASDIV>(
+          a, b, unit + bi * U * kUnitFloats, evals);
+      // fused accumulate into the image
+      if (lane == 0) {
+        const long long gp = a.pixlist ? a.pixlist[first + bi] : first + bi;
+        a.image[gp] += a.prefactor * v;
+      }
+    }
+    __syncwarp();  // the next batch rewrites the units
   }
   if (lane == 0 && a.stats && evals) atomicAdd(a.stats, evals);
 }
