@@ -328,7 +328,7 @@ int nb_server_free(nb_server *srv);
 enum {
     /* kernel variant of NB_MIXED: NB_VARIANT_AUTO (default: one warp per
      * pixel for Gaussian shapes with tricubic lookup, <= 32 subpixel x layer
-     * units and >= 16 (unit, phi x mosaic) items per pixel, else one thread
+     * units and >= 8 (unit, phi x mosaic) items per pixel, else one thread
      * per pixel), NB_VARIANT_THREAD, NB_VARIANT_WARP (Gaussian shapes with
      * <= 32 units only; falls back to NB_VARIANT_THREAD otherwise) */
     NB_OPT_VARIANT = 1

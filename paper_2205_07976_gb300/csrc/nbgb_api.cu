@@ -817,7 +817,7 @@ static int launch(nb_sim *s, const long long *dev_list, long long n_list) {
   // one warp per pixel pays off where the scattered terms are expensive
   // (tricubic lookups) and a pixel has enough items to fill the lanes
   bool auto_warp = a.interp == NB_INTERP_TRICUBIC &&
-                   (long long)a.os * a.os * a.T * a.PM >= 16;
+                   (long long)a.os * a.os * a.T * a.PM >= 8;
   bool warp_variant =
       s->precision == NB_MIXED && nbgb::split_supported(a) &&
       (s->variant == NB_VARIANT_WARP ||

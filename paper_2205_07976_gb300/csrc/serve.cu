@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(kTileThreads, 4)
 }
 
 // The warp-per-pixel form for requests the stand-alone library would also
-// run one warp per pixel (tricubic lookup, >= 16 subpixel x mosaic items):
+// run one warp per pixel (tricubic lookup, >= 8 subpixel x mosaic items):
 // each work item stages its request's tables once, then each warp sums its
 // pixels with the same device function as the stand-alone kernel.
 template <int INTERP>
@@ -612,7 +612,7 @@ int nb_server_submit(nb_server *s, const double axes[9], const double *umats,
       (long long)s->os * s->os * s->T * n_src * (long long)n_mosaic;
   // the same choice as nb_add_spots makes for this shot
   r.warp = s->interp == NB_INTERP_TRICUBIC &&
-           (long long)s->os * s->os * s->T * n_mosaic >= 16 &&
+           (long long)s->os * s->os * s->T * n_mosaic >= 8 &&
            s->os * s->os * s->T <= 32;
   s->queue.push_back(r.id);
   *request_id = r.id;
