@@ -518,12 +518,25 @@ __device__ __forceinline__ double split_sum(const SpotArgs &a,
   evals += tail;
   __syncwarp();
 
-  // ---- 4. warp reduction in FP64
-  double v = acc.value();
+  // ---- 4. warp reduction in float-float: each lane's compensated sum is
+  // the pair (s, -c); pairs are added with error-free transformations (so
+  // the butterfly gives every lane the same pair) and turned into FP64
+  // once.  FP64 instructions run at 1/64 of the FP32 rate on this part and
+  // issue per warp, so a per-pixel FP64 tree would cost as much as a
+  // pixel's sum when the pixel has few steps.
+  float hi, lo;
+  fast_two_sum(acc.s, -acc.c, hi, lo);
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  for (int o = 16; o > 0; o >>= 1) {
+    const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+    const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+    float sh, se;
+    two_sum(hi, h2, sh, se);
+    se += lo + l2;
+    fast_two_sum(sh, se, hi, lo);
+  }
   __syncwarp();
-  return v;
+  return (double)hi + (double)lo;
 }
 
 }  // namespace nbgb
