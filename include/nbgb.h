@@ -285,19 +285,24 @@ int nb_server_submit(nb_server *srv, const double axes[9],
                      int n_src, double scale, int roi_f0, int roi_s0,
                      int roi_nf, int roi_ns, long long *request_id);
 
-/* One scheduling step: finish the step in flight, admit queued requests
- * (FIFO; a request that does not fit may be passed by later ones until it
- * has waited 8 steps), cut the running requests into work items round
- * robin up to the pixel-step budget, launch, and wait for it up to
- * timeout_s seconds.  A request's slot is released when it completes;
- * its image stays in the pool until fetched.  *n_active (may be NULL) =
- * queued + running.  Errors: NB_ETIMEOUT if the step is still running
- * after timeout_s (the next call waits for it again); NB_ESTATE if
+/* One scheduling step: admit queued requests (FIFO; a request that does
+ * not fit may be passed by later ones until it has waited 8 steps), cut
+ * the running requests into work items round robin up to the pixel-step
+ * budget and queue them on the GPU, then wait (up to timeout_s seconds)
+ * for the step queued by the previous call, so that one step runs while
+ * the next is prepared.  When there is nothing new to queue, the call
+ * waits for every step in flight.  A request completes when the step
+ * holding its last work item has finished: its slot is released and its
+ * image stays in the pool until fetched.  *n_active (may be NULL) =
+ * queued + running.  Errors: NB_ETIMEOUT if a step waited for is still
+ * running after timeout_s (a later call waits for it again); NB_ESTATE if
  * requests are queued but nothing runs and none can be admitted (the pool
  * is held by unfetched results: fetch them); NB_ECUDA. */
 int nb_server_step(nb_server *srv, double timeout_s, int *n_active);
 
-/* Ids of requests completed since the last call (up to max_ids). */
+/* Ids of requests completed since the last call (up to max_ids); a
+ * request fetched with nb_server_result before it was reported is not
+ * reported. */
 int nb_server_completed(nb_server *srv, long long *ids, int max_ids,
                         int *n_out);
 

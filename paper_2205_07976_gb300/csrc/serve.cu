@@ -9,18 +9,23 @@
 //   submit  -> FIFO queue (inputs copied, tables built on the host)
 //   step    -> admit while a slot and room in the image pool exist (first
 //              fit; a blocked head request stops bypassing after 8 steps);
-//              cut the active requests into 128-pixel work items, round
-//              robin, up to a pixel-step budget; replay one CUDA graph
-//              (work list upload, counter reset, persistent kernel); wait;
-//              requests whose last item ran are complete
-//   result  -> copy the image out, free its pool range (its slot was freed
-//              when the request completed)
+//              cut the active requests into work items (128 pixels for the
+//              thread kernel, 32 for the warp kernel), round robin, up to a
+//              pixel-step budget; replay one of two CUDA graphs (work list
+//              upload from its own pinned buffer, counter reset, the two
+//              persistent kernels); then wait for the step queued by the
+//              previous call, so the GPU runs one step while the host
+//              prepares the next; requests whose last item ran in a
+//              finished step are complete
+//   result  -> copy the image out on a separate stream, free its pool
+//              range (its slot was freed when the request completed)
 //
-// The persistent kernel's blocks pull work items through an atomic
-// counter; each item stages its request's tables in shared memory and every
-// thread computes one pixel with the same per-pixel function as the
-// thread-per-pixel kernel, so a request's image does not depend on what it
-// was batched with.
+// The persistent kernels' blocks pull work items through atomic counters;
+// each item stages its request's tables in shared memory and computes its
+// pixels with the same device functions as the stand-alone kernels (one
+// thread per pixel, or one warp per pixel for the requests the stand-alone
+// library would run that way), so a request's image does not depend on
+// what it was batched with.
 #include <cuda_runtime.h>
 
 #include <chrono>
@@ -201,7 +206,7 @@ struct Request {
   SlotParams params;  // host copy (img_off set at admission)
   long long npix, steps_per_pixel;
   long long next = 0;     // next ROI pixel to schedule
-  long long pending = 0;  // pixels scheduled in the in-flight step
+  long long last_step = -1;  // the step holding its last work item
   int slot = -1;
   long long pool_off = -1;
   int state = NB_REQ_QUEUED;
@@ -231,15 +236,21 @@ struct nb_server {
   double defF = 0;
   double fluence = 0, kahn = 0, evec[3] = {1, 0, 0}, dir[3] = {0, 0, 1};
   Buf d_F, d_F4, d_C4, d_panel, d_slots, d_pool, d_work, d_work_w, d_counter;
-  WorkList *h_work = nullptr;    // pinned staging: thread-kernel items
-  WorkList *h_work_w = nullptr;  // pinned staging: warp-kernel items
+  // two host work-list buffers, each with its graph: the next step is
+  // built and queued while the previous one runs
+  WorkList *h_work[2] = {nullptr, nullptr};    // pinned: thread-kernel items
+  WorkList *h_work_w[2] = {nullptr, nullptr};  // pinned: warp-kernel items
   int blocks_w = 0;
   size_t smem_w = 0;
   nbgb::SpotArgs base;
-  cudaGraphExec_t graph = nullptr;
-  cudaEvent_t done_ev = nullptr;
-  bool in_flight = false;
-  double launched_at = 0;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  cudaEvent_t done_ev[2] = {nullptr, nullptr};
+  bool in_flight[2] = {false, false};
+  long long step_of[2] = {0, 0};
+  std::deque<int> flight;  // buffers in flight, oldest first
+  int cur = 0;             // the buffer the next step is built in
+  long long step_counter = 0;
+  cudaStream_t copy_stream = nullptr;  // result copies
   // host bookkeeping
   long long next_id = 1;
   std::deque<long long> queue;
@@ -284,13 +295,16 @@ static void pool_free(nb_server *s, long long off, long long n) {
   }
 }
 
-static int build_graph(nb_server *s) {
+// The graph of one step from host buffer b: work lists to the device (one
+// device copy serves both buffers: steps run in stream order), counters
+// reset, the two persistent kernels.
+static int build_graph(nb_server *s, int b) {
   cudaError_t e = cudaStreamBeginCapture(s->stream,
                                          cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return sfail(s, NB_ECUDA, "graph capture begin");
-  cudaMemcpyAsync(s->d_work.p, s->h_work, sizeof(WorkList),
+  cudaMemcpyAsync(s->d_work.p, s->h_work[b], sizeof(WorkList),
                   cudaMemcpyHostToDevice, s->stream);
-  cudaMemcpyAsync(s->d_work_w.p, s->h_work_w, sizeof(WorkList),
+  cudaMemcpyAsync(s->d_work_w.p, s->h_work_w[b], sizeof(WorkList),
                   cudaMemcpyHostToDevice, s->stream);
   cudaMemsetAsync(s->d_counter.p, 0, 2 * sizeof(unsigned), s->stream);
   void (*kern)(nbgb::SpotArgs, const SlotParams *, const WorkList *,
@@ -309,7 +323,7 @@ static int build_graph(nb_server *s) {
   cudaGraph_t g = nullptr;
   e = cudaStreamEndCapture(s->stream, &g);
   if (e != cudaSuccess) return sfail(s, NB_ECUDA, "graph capture end");
-  e = cudaGraphInstantiate(&s->graph, g, 0);
+  e = cudaGraphInstantiate(&s->graph[b], g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) return sfail(s, NB_ECUDA, "graph instantiate");
   return NB_OK;
@@ -404,16 +418,22 @@ int nb_server_create(nb_server **out, int device, void *cuda_stream,
         s->d_work.alloc(sizeof(WorkList)) != cudaSuccess ||
         s->d_work_w.alloc(sizeof(WorkList)) != cudaSuccess ||
         s->d_counter.alloc(2 * sizeof(unsigned)) != cudaSuccess ||
-        cudaHostAlloc((void **)&s->h_work, sizeof(WorkList),
+        cudaHostAlloc((void **)&s->h_work[0], sizeof(WorkList),
                       cudaHostAllocDefault) != cudaSuccess ||
-        cudaHostAlloc((void **)&s->h_work_w, sizeof(WorkList),
+        cudaHostAlloc((void **)&s->h_work_w[0], sizeof(WorkList),
+                      cudaHostAllocDefault) != cudaSuccess ||
+        cudaHostAlloc((void **)&s->h_work[1], sizeof(WorkList),
+                      cudaHostAllocDefault) != cudaSuccess ||
+        cudaHostAlloc((void **)&s->h_work_w[1], sizeof(WorkList),
                       cudaHostAllocDefault) != cudaSuccess) {
       cudaGetLastError();
       rc = sfail(s, NB_ENOMEM, "server buffers");
       break;
     }
-    std::memset(s->h_work, 0, sizeof(WorkList));
-    std::memset(s->h_work_w, 0, sizeof(WorkList));
+    for (int b = 0; b < 2; ++b) {
+      std::memset(s->h_work[b], 0, sizeof(WorkList));
+      std::memset(s->h_work_w[b], 0, sizeof(WorkList));
+    }
     cudaMemcpy(s->d_F.p, F, nF * 4, cudaMemcpyHostToDevice);
     nbgb::DevPanel P;
     std::memset(&P, 0, sizeof P);
@@ -512,12 +532,17 @@ int nb_server_create(nb_server **out, int device, void *cuda_stream,
     }
     for (int i = max_slots - 1; i >= 0; --i) s->free_slots.push_back(i);
     s->free_ranges[0] = s->pool_elems;
-    if (cudaEventCreateWithFlags(&s->done_ev, cudaEventDisableTiming) !=
-        cudaSuccess) {
+    if (cudaEventCreateWithFlags(&s->done_ev[0], cudaEventDisableTiming) !=
+            cudaSuccess ||
+        cudaEventCreateWithFlags(&s->done_ev[1], cudaEventDisableTiming) !=
+            cudaSuccess ||
+        cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking) !=
+            cudaSuccess) {
       rc = NB_ECUDA;
       break;
     }
-    rc = build_graph(s);
+    rc = build_graph(s, 0);
+    if (rc == NB_OK) rc = build_graph(s, 1);
   } while (false);
   if (cudaGetLastError() != cudaSuccess && rc == NB_OK) rc = NB_ECUDA;
   cudaSetDevice(prev);
@@ -535,10 +560,16 @@ int nb_server_free(nb_server *s) {
   cudaGetDevice(&prev);
   cudaSetDevice(s->device);
   if (s->stream) cudaStreamSynchronize(s->stream);
-  if (s->graph) cudaGraphExecDestroy(s->graph);
-  if (s->done_ev) cudaEventDestroy(s->done_ev);
-  if (s->h_work) cudaFreeHost(s->h_work);
-  if (s->h_work_w) cudaFreeHost(s->h_work_w);
+  if (s->copy_stream) {
+    cudaStreamSynchronize(s->copy_stream);
+    cudaStreamDestroy(s->copy_stream);
+  }
+  for (int b = 0; b < 2; ++b) {
+    if (s->graph[b]) cudaGraphExecDestroy(s->graph[b]);
+    if (s->done_ev[b]) cudaEventDestroy(s->done_ev[b]);
+    if (s->h_work[b]) cudaFreeHost(s->h_work[b]);
+    if (s->h_work_w[b]) cudaFreeHost(s->h_work_w[b]);
+  }
   if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
   {
     Buf *bufs[] = {&s->d_F,    &s->d_F4,     &s->d_C4,     &s->d_panel,
@@ -649,31 +680,40 @@ static int admit(nb_server *s) {
   return NB_OK;
 }
 
-static int finish_in_flight(nb_server *s, double timeout_s) {
-  if (!s->in_flight) return NB_OK;
+// Waits (up to timeout_s) for the oldest step in flight and completes the
+// requests whose last work item it held: their slots are free again; their
+// images stay in the pool until nb_server_result fetches them.
+static int finish_oldest(nb_server *s, double timeout_s) {
+  if (s->flight.empty()) return NB_OK;
+  const int b = s->flight.front();
   double t0 = now_s();
   while (true) {
-    cudaError_t q = cudaEventQuery(s->done_ev);
+    cudaError_t q = cudaEventQuery(s->done_ev[b]);
     if (q == cudaSuccess) break;
     if (q != cudaErrorNotReady) return sfail(s, NB_ECUDA, "step failed");
     if (now_s() - t0 > timeout_s)
       return sfail(s, NB_ETIMEOUT, "step did not finish in time");
   }
-  s->in_flight = false;
+  s->flight.pop_front();
+  s->in_flight[b] = false;
   for (auto &kv : s->reqs) {
     Request &r = kv.second;
-    if (r.state != NB_REQ_RUNNING) continue;
-    r.pending = 0;
-    if (r.next >= r.npix) {
-      // its last work item has run: the slot's tables are free again; the
-      // image stays in the pool until nb_server_result fetches it
-      r.state = NB_REQ_DONE;
-      s->free_slots.push_back(r.slot);
-      r.slot = -1;
-      s->completed.push_back(r.id);
-    }
+    if (r.state != NB_REQ_RUNNING || r.next < r.npix ||
+        r.last_step != s->step_of[b])
+      continue;
+    r.state = NB_REQ_DONE;
+    s->free_slots.push_back(r.slot);
+    r.slot = -1;
+    s->completed.push_back(r.id);
   }
   return NB_OK;
+}
+
+static bool any_schedulable(const nb_server *s) {
+  for (auto &kv : s->reqs)
+    if (kv.second.state == NB_REQ_RUNNING && kv.second.next < kv.second.npix)
+      return true;
+  return false;
 }
 
 int nb_server_step(nb_server *s, double timeout_s, int *n_active) {
@@ -681,15 +721,18 @@ int nb_server_step(nb_server *s, double timeout_s, int *n_active) {
   int prev = 0;
   cudaGetDevice(&prev);
   cudaSetDevice(s->device);
-  int rc = finish_in_flight(s, timeout_s);
+  int rc = NB_OK;
+  // the buffer this step is built in must be free (it is, unless an earlier
+  // step returned on a timeout with two steps in flight)
+  if (s->in_flight[s->cur]) rc = finish_oldest(s, timeout_s);
   if (rc == NB_OK) rc = admit(s);
   if (rc == NB_OK) {
     // round-robin cut of the active requests into work items
-    std::vector<Request *> act;
+    std::vector<Request *> act, finished;
     for (auto &kv : s->reqs)
       if (kv.second.state == NB_REQ_RUNNING && kv.second.next < kv.second.npix)
         act.push_back(&kv.second);
-    WorkList *wl = s->h_work, *ww = s->h_work_w;
+    WorkList *wl = s->h_work[s->cur], *ww = s->h_work_w[s->cur];
     int nt = 0, nw = 0;
     long long used = 0;
     if (!act.empty()) {
@@ -712,7 +755,7 @@ int nb_server_step(nb_server *s, double timeout_s, int *n_active) {
           L->items[n].first = r.next;
           ++n;
           r.next += cnt;
-          r.pending += cnt;
+          if (r.next >= r.npix) finished.push_back(&r);
           used += cnt * r.steps_per_pixel;
           progress = true;
         }
@@ -721,21 +764,33 @@ int nb_server_step(nb_server *s, double timeout_s, int *n_active) {
     }
     wl->n = nt;
     ww->n = nw;
-    const int n = nt + nw;
-    if (n == 0 && !s->queue.empty()) {
-      // nothing runs and nothing can be admitted: the pool is held by
-      // completed images that were not fetched yet
-      rc = sfail(s, NB_ESTATE,
-                 "queued requests cannot be admitted: fetch completed "
-                 "results (nb_server_result) to free the image pool");
-    } else if (n > 0) {
-      cudaError_t e = cudaGraphLaunch(s->graph, s->stream);
-      if (e == cudaSuccess) e = cudaEventRecord(s->done_ev, s->stream);
+    if (nt + nw > 0) {
+      const int b = s->cur;
+      cudaError_t e = cudaGraphLaunch(s->graph[b], s->stream);
+      if (e == cudaSuccess) e = cudaEventRecord(s->done_ev[b], s->stream);
       if (e != cudaSuccess) {
         rc = sfail(s, NB_ECUDA, "graph launch");
       } else {
-        s->in_flight = true;
-        rc = finish_in_flight(s, timeout_s);
+        s->in_flight[b] = true;
+        s->step_of[b] = ++s->step_counter;
+        for (Request *r : finished) r->last_step = s->step_of[b];
+        s->flight.push_back(b);
+        s->cur ^= 1;
+        // keep one step queued behind the running one
+        if (s->flight.size() > 1) rc = finish_oldest(s, timeout_s);
+      }
+    } else {
+      // nothing new to run: drain the steps in flight
+      while (rc == NB_OK && !s->flight.empty()) rc = finish_oldest(s, timeout_s);
+      if (rc == NB_OK && !s->queue.empty()) {
+        const size_t before = s->queue.size();
+        rc = admit(s);
+        if (rc == NB_OK && s->queue.size() == before && !any_schedulable(s))
+          // nothing runs and nothing can be admitted: the pool is held by
+          // completed images that were not fetched yet
+          rc = sfail(s, NB_ESTATE,
+                     "queued requests cannot be admitted: fetch completed "
+                     "results (nb_server_result) to free the image pool");
       }
     }
   }
@@ -782,14 +837,22 @@ int nb_server_result(nb_server *s, long long id, void *dst, size_t n_elems,
   int prev = 0;
   cudaGetDevice(&prev);
   cudaSetDevice(s->device);
+  // on the copy stream: the image is complete (its last step finished), and
+  // a step queued behind it on the server's stream need not be waited for
   cudaError_t e = cudaMemcpyAsync(
       dst, (double *)s->d_pool.p + r.pool_off, n_elems * sizeof(double),
       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
-      s->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+      s->copy_stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->copy_stream);
   cudaSetDevice(prev);
   if (e != cudaSuccess) return sfail(s, NB_ECUDA, "result copy");
   pool_free(s, r.pool_off, r.npix);
+  // a fetched request is no longer reported as completed
+  for (auto c = s->completed.begin(); c != s->completed.end(); ++c)
+    if (*c == id) {
+      s->completed.erase(c);
+      break;
+    }
   s->reqs.erase(it);
   return NB_OK;
 }

@@ -139,6 +139,9 @@ def test_step_timeout_then_recovery(base):
     srv = nbgb.Server(base, max_slots=2, pool_bytes=64 << 20,
                       step_budget=1 << 62)
     rid = submit(srv, r)
+    # the first step queues the whole request; the second has nothing new
+    # to queue and waits for it, with no time to do so
+    srv.step(timeout_s=0.0)
     with pytest.raises(nbgb.NbError) as e:
         srv.step(timeout_s=0.0)
     assert e.value.code == nbgb.NB_ETIMEOUT
