@@ -81,6 +81,8 @@ def parse():
                          "grad")
     ap.add_argument("--serve-requests", type=int, default=4096)
     ap.add_argument("--serve-seq-subset", type=int, default=16)
+    ap.add_argument("--serve-budget", type=int, default=1_000_000_000,
+                    help="pixel-steps per serving step")
     return ap.parse_args()
 
 
@@ -496,7 +498,7 @@ def run_serving(args, local, torch, nbgb, W):
 
     def serve(arrivals):
         srv = nbgb.Server(base, max_slots=256, pool_bytes=4 << 30,
-                          step_budget=500_000_000, device=local)
+                          step_budget=args.serve_budget, device=local)
         t0 = time.perf_counter()
         arr = {}
         lat = []
@@ -529,7 +531,7 @@ def run_serving(args, local, torch, nbgb, W):
 
     cap = serve(np.zeros(len(reqs)))
     out = {"requests": len(reqs), "pixel_steps": total_steps,
-           "capacity": cap, "rates": {}}
+           "step_budget": args.serve_budget, "capacity": cap, "rates": {}}
     for f in (0.5, 0.8, 1.0):
         arrivals = W.poisson_arrivals(len(reqs), f * cap["shots_per_s"],
                                       seed=int(f * 10))
