@@ -501,11 +501,16 @@ def test_loss_gradient_matches_finite_differences(interp):
         fd = (fp - fm) / (2 * h)
         assert math.isclose(g[r], fd, rel_tol=2e-5,
                             abs_tol=1e-6 * np.abs(g).max()), (r, g[r], fd)
-    # structure-factor gradient on the entries with the largest gradient
+    # structure-factor gradient: the 8 entries with the largest gradient,
+    # up to 24 other touched entries drawn at random, and an untouched one
     F64 = s.F.astype(np.float64)
     nz = np.flatnonzero(gF.ravel())
     assert nz.size >= 1
-    idx = list(nz[np.argsort(np.abs(gF.ravel()[nz]))[-3:]])
+    order = nz[np.argsort(np.abs(gF.ravel()[nz]))]
+    idx = list(order[-8:])
+    rest = order[:-8]
+    if rest.size:
+        idx += list(rng.choice(rest, size=min(24, rest.size), replace=False))
     idx.append(int(np.flatnonzero(gF.ravel() == 0)[0]))  # an untouched entry
     for e in idx:
         h = 1e-4
