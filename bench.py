@@ -389,53 +389,59 @@ def run_grad(args, local, stream, torch, nbgb, W):
     with the gradients of the 10 crystal parameters and of every structure
     factor.  The target is a seeded Poisson draw of the forward image."""
     import numpy as np
-    shot = W.multipanel_shot(8)
     U = W.random_orientation(np.random.default_rng(3))
     cell, rot = np.array([79.0, 79.0, 38.0]), np.zeros(3)
     N = np.array([15.0, 15.0, 15.0])
     dev = torch.device("cuda", local)
-    sim = nbgb.Sim("mixed", device=local, stream=stream).set_shot(shot)
-    sim.set_params(U, cell, rot, N, 1.0)
-    sim.add_spots()
-    y = np.random.default_rng(7).poisson(sim.image() + 1.0).astype(np.float64)
-    yd = torch.from_numpy(y).to(dev)
-    dL = torch.empty_like(yd)
-    gF = torch.zeros(shot.F.size, dtype=torch.float64, device=dev)
-    torch.cuda.synchronize(dev)
 
-    def one():
-        sim.zero()
+    def timed_step(shot):
+        sim = nbgb.Sim("mixed", device=local, stream=stream).set_shot(shot)
+        sim.set_params(U, cell, rot, N, 1.0)
         sim.add_spots()
-        sim.poisson_loss(yd.data_ptr(), 1.0, dL.data_ptr())
-        return sim.adjoint(dL.data_ptr(), gF.data_ptr())
+        y = np.random.default_rng(7).poisson(sim.image() + 1.0)
+        yd = torch.from_numpy(y.astype(np.float64)).to(dev)
+        dL = torch.empty_like(yd)
+        gF = torch.zeros(shot.F.size, dtype=torch.float64, device=dev)
+        torch.cuda.synchronize(dev)
+        for _ in range(max(args.warmup, 1)):
+            sim.zero()
+            sim.add_spots()
+            sim.poisson_loss(yd.data_ptr(), 1.0, dL.data_ptr())
+            sim.adjoint(dL.data_ptr(), gF.data_ptr())
+        reps = max(args.steps, 1)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        tf = tl = ta = 0.0
+        for _ in range(reps):
+            ev[0].record(stream)
+            sim.zero()
+            sim.add_spots()
+            ev[1].record(stream)
+            sim.poisson_loss(yd.data_ptr(), 1.0, dL.data_ptr())
+            ev[2].record(stream)
+            sim.adjoint(dL.data_ptr(), gF.data_ptr())
+            ev[3].record(stream)
+            stream.synchronize()
+            tf += ev[0].elapsed_time(ev[1]) / 1e3
+            tl += ev[1].elapsed_time(ev[2]) / 1e3
+            ta += ev[2].elapsed_time(ev[3]) / 1e3
+        sim.close()
+        return tf / reps, tl / reps, ta / reps
 
-    for _ in range(max(args.warmup, 1)):
-        one()
-    reps = max(args.steps, 1)
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-    tf = tl = ta = 0.0
-    for _ in range(reps):
-        ev[0].record(stream)
-        sim.zero()
-        sim.add_spots()
-        ev[1].record(stream)
-        sim.poisson_loss(yd.data_ptr(), 1.0, dL.data_ptr())
-        ev[2].record(stream)
-        sim.adjoint(dL.data_ptr(), gF.data_ptr())
-        ev[3].record(stream)
-        stream.synchronize()
-        tf += ev[0].elapsed_time(ev[1]) / 1e3
-        tl += ev[1].elapsed_time(ev[2]) / 1e3
-        ta += ev[2].elapsed_time(ev[3]) / 1e3
-    sim.close()
-    tf, tl, ta = tf / reps, tl / reps, ta / reps
+    shot = W.multipanel_shot(8)
+    tf, tl, ta = timed_step(shot)
     steps = shot.pixel_steps
+    tri = shot.copy()
+    tri.interp = W.INTERP_TRICUBIC
+    tf3, tl3, ta3 = timed_step(tri)
     return {"workload": "64 panels of 185x194, S=8, M=10, N=15 Gaussian, "
                         "nearest F on [-40,40]^3",
             "pixel_steps_per_pass": steps,
             "forward_ms": tf * 1e3, "loss_ms": tl * 1e3,
             "adjoint_ms": ta * 1e3, "step_ms": (tf + tl + ta) * 1e3,
             "adjoint_pixel_steps_per_s": steps / ta,
+            "tricubic": {"forward_ms": tf3 * 1e3, "adjoint_ms": ta3 * 1e3,
+                         "step_ms": (tf3 + tl3 + ta3) * 1e3,
+                         "adjoint_pixel_steps_per_s": steps / ta3},
             "unit": "pixel-steps/s"}
 
 
