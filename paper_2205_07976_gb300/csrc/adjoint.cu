@@ -64,6 +64,32 @@ __global__ void __launch_bounds__(kTileThreads, INTERP ? 2 : 4)
   for (int i = threadIdx.x; i < a.PM * 54; i += blockDim.x)
     s_dax[i] = g.dax[i];
   __syncthreads();
+  // tricubic dL/dF: the terms of a thread near one lattice point n use
+  // stencils starting at n-2 or n-1 along each axis, all inside the 5x5x5
+  // nodes n-2 .. n+2.  The thread sums their weighted contributions there,
+  // in its own column of shared memory (FP32), and adds the touched nodes
+  // to the FP64 gradient when n changes and at the end: far fewer global
+  // atomics than 64 per term.
+  // [125][kTileThreads] after the tables (dynamic shared memory)
+  float (*s_facc)[kTileThreads] =
+      reinterpret_cast<float (*)[kTileThreads]>(s_dax + a.PM * 54);
+  int held[3] = {0, 0, 0};  // the lattice point held (table-relative)
+  bool holding = false;
+  auto flush_node = [&]() {
+    if (!holding) return;
+    for (int e = 0; e < 125; ++e) {
+      const float v = s_facc[e][threadIdx.x];
+      if (v == 0.f) continue;  // untouched (may lie outside the table)
+      s_facc[e][threadIdx.x] = 0.f;
+      const int i = e / 25, j = (e / 5) % 5, k = e % 5;
+      atomicAdd(g.gradF + ((long long)(held[0] - 2 + i) * a.hn[1] +
+                           (held[1] - 2 + j)) * a.hn[2] + (held[2] - 2 + k),
+                (double)v);
+    }
+    holding = false;
+  };
+  if (INTERP && HASF)
+    for (int e = 0; e < 125; ++e) s_facc[e][threadIdx.x] = 0.f;
 
   double gsum[kGradN];
 #pragma unroll
@@ -250,14 +276,28 @@ __global__ void __launch_bounds__(kTileThreads, INTERP ? 2 : 4)
               if (HASF) {
                 double gv = fscal * (double)(2.f * fc * fl2 * w);
                 if (tri) {
+                  if (!holding || n[0] != held[0] || n[1] != held[1] ||
+                      n[2] != held[2]) {
+                    flush_node();
+                    held[0] = n[0];
+                    held[1] = n[1];
+                    held[2] = n[2];
+                    holding = true;
+                  }
+                  // the stencil starts at fl - 1 = n - 2 + o, o = 0 or 1
+                  const int o0 = fl[0] - n[0] + 1, o1 = fl[1] - n[1] + 1,
+                            o2 = fl[2] - n[2] + 1;
+                  const float gvf = (float)gv;
+#pragma unroll
                   for (int i = 0; i < 4; ++i)
+#pragma unroll
                     for (int j = 0; j < 4; ++j) {
-                      long long rowi = ((long long)(fl[0] - 1 + i) * a.hn[1] +
-                                        (fl[1] - 1 + j)) * a.hn[2] + (fl[2] - 1);
-                      float wij = wv[0][i] * wv[1][j];
+                      const float wij = gvf * (wv[0][i] * wv[1][j]);
+                      const int row = ((o0 + i) * 5 + (o1 + j)) * 5 + o2;
 #pragma unroll
                       for (int k = 0; k < 4; ++k)
-                        atomicAdd(g.gradF + rowi + k, gv * (double)(wij * wv[2][k]));
+                        s_facc[row + k][threadIdx.x] =
+                            fmaf(wij, wv[2][k], s_facc[row + k][threadIdx.x]);
                     }
                 } else if (inside) {
                   atomicAdd(g.gradF + fidx, gv);
@@ -273,6 +313,7 @@ __global__ void __launch_bounds__(kTileThreads, INTERP ? 2 : 4)
     for (int r = 0; r < 9; ++r) gsum[r] = wks * tot[r];
     gsum[9] = wp * g.kc * tot[9];  // dI/dscale = I / scale
   }
+  if (INTERP && HASF) flush_node();
   // block reduction in FP64, fixed order
   __shared__ double red[kTileThreads / 32][kGradN];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -329,8 +370,9 @@ __global__ void poisson_loss_kernel(const double *img, const double *y,
   }
 }
 
-size_t adjoint_smem_bytes(const SpotArgs &a) {
-  return (size_t)(2 * a.PM * 9 + a.S * SRC32_STRIDE + a.PM * 54) *
+size_t adjoint_smem_bytes(const SpotArgs &a, bool f_cache) {
+  return (size_t)(2 * a.PM * 9 + a.S * SRC32_STRIDE + a.PM * 54 +
+                  (f_cache ? 125 * kTileThreads : 0)) *
          sizeof(float);
 }
 
@@ -351,7 +393,7 @@ cudaError_t launch_adjoint(const SpotArgs &a, const float *dax,
   g.partials = partials;
   g.kc = kc;
   g.scale = scale;
-  size_t smem = adjoint_smem_bytes(a);
+  size_t smem = adjoint_smem_bytes(a, a.interp && gradF);
   long long blocks = adjoint_blocks(a);
   if (blocks <= 0) return cudaSuccess;
   void (*kern)(AdjointArgs) =

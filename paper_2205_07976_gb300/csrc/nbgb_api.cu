@@ -945,7 +945,8 @@ int nb_adjoint(nb_sim *s, const double *dLdI, double grad[10],
     return fail(s, NB_EINVAL, "the adjoint needs one source direction");
   SpotArgs a;
   fill_args(s, a);
-  if (nbgb::adjoint_smem_bytes(a) > 200 * 1024)
+  if (nbgb::adjoint_smem_bytes(a, a.interp == NB_INTERP_TRICUBIC && gradF) >
+      200 * 1024)
     return fail(s, NB_EINVAL, "tables exceed 200 KB of shared memory");
   long long blocks = nbgb::adjoint_blocks(a);
   cudaError_t e = s->d_part.ensure((size_t)(blocks + 1) * 10 * sizeof(double));

@@ -236,7 +236,7 @@ cudaError_t build_sliding_table(const float *F, const int hn[3], float4 *F4,
                                 cudaStream_t st);
 cudaError_t build_cell_polynomials(const float *F, const int hn[3], float4 *C4,
                                    cudaStream_t st);
-size_t adjoint_smem_bytes(const SpotArgs &a);
+size_t adjoint_smem_bytes(const SpotArgs &a, bool f_cache);
 long long adjoint_blocks(const SpotArgs &a);
 int loss_blocks(long long n);
 cudaError_t launch_adjoint(const SpotArgs &a, const float *dax,
