@@ -73,6 +73,8 @@ __global__ void __launch_bounds__(kTileThreads, INTERP ? 2 : 4)
   // [125][kTileThreads] after the tables (dynamic shared memory)
   float (*s_facc)[kTileThreads] =
       reinterpret_cast<float (*)[kTileThreads]>(s_dax + a.PM * 54);
+  long long near_idx = -1;  // nearest lookup: the entry being summed
+  double near_sum = 0.0;
   int held[3] = {0, 0, 0};  // the lattice point held (table-relative)
   bool holding = false;
   auto flush_node = [&]() {
@@ -300,7 +302,14 @@ __global__ void __launch_bounds__(kTileThreads, INTERP ? 2 : 4)
                             fmaf(wij, wv[2][k], s_facc[row + k][threadIdx.x]);
                     }
                 } else if (inside) {
-                  atomicAdd(g.gradF + fidx, gv);
+                  // consecutive terms mostly hit the same entry: add up
+                  // in a register, one atomic per run of equal entries
+                  if (fidx != near_idx) {
+                    if (near_idx >= 0) atomicAdd(g.gradF + near_idx, near_sum);
+                    near_idx = fidx;
+                    near_sum = 0.0;
+                  }
+                  near_sum += gv;
                 }
               }
             }
@@ -314,6 +323,7 @@ __global__ void __launch_bounds__(kTileThreads, INTERP ? 2 : 4)
     gsum[9] = wp * g.kc * tot[9];  // dI/dscale = I / scale
   }
   if (INTERP && HASF) flush_node();
+  if (HASF && near_idx >= 0) atomicAdd(g.gradF + near_idx, near_sum);
   // block reduction in FP64, fixed order
   __shared__ double red[kTileThreads / 32][kGradN];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
