@@ -45,6 +45,9 @@ def test_host_only_entry_points():
     assert lib.nb_add_spots(None) == nbgb.NB_EINVAL
     assert lib.nb_set_scale(None, 1.0) == nbgb.NB_EINVAL
     assert lib.nb_sim_create(None, 0, 1, None) == nbgb.NB_EINVAL
+    assert lib.nb_add_background(None) == nbgb.NB_EINVAL
+    assert lib.nb_set_background(None, None, None, 2, 1.0) == nbgb.NB_EINVAL
+    assert lib.nb_adjoint(None, None, None, None) == nbgb.NB_EINVAL
 
 
 @pytest.mark.skipif(gpu_available(), reason="checks the no-GPU error path")
