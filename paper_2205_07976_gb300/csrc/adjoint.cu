@@ -105,6 +105,7 @@ __global__ void __launch_bounds__(kTileThreads, INTERP ? 2 : 4)
     const DevPanel &P = a.panels[q];
     const double px = P.px;
     const int os = a.os;
+    const double inv_os = 1.0 / os;
     const float kahn = a.kahn;
     const float cutg = kGaussCut * 0.63f;
     const double wp = g.dLdI[gp];
@@ -116,24 +117,25 @@ __global__ void __launch_bounds__(kTileThreads, INTERP ? 2 : 4)
     for (int i = 0; i < os; ++i)
       for (int j = 0; j < os; ++j)
         for (int t = 0; t < a.T; ++t) {
-          double cf = (f + (i + 0.5) / os) * px,
-                 cs = (s + (j + 0.5) / os) * px, cn = t * a.dt;
+          double cf = (f + (i + 0.5) * inv_os) * px,
+                 cs = (s + (j + 0.5) * inv_os) * px, cn = t * a.dt;
           double pos[3], d[3];
           float vh[3], vl[3], v32[3];
 #pragma unroll
           for (int c = 0; c < 3; ++c)
             pos[c] = P.origin[c] + cf * P.fdir[c] + cs * P.sdir[c] +
                      cn * P.ndir[c];
-          double R = sqrt(dot3d_m(pos, pos));
+          const double inv = rsqrt(dot3d_m(pos, pos));
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
-            d[c] = pos[c] / R;
+            d[c] = pos[c] * inv;
             double v = d[c] - a.i0[c];
             vh[c] = (float)v;
             vl[c] = (float)(v - (double)vh[c]);
             v32[c] = vh[c];
           }
-          float omega = (float)(px * px * dot3d_m(P.ndir, pos) / (R * R * R));
+          float omega =
+              (float)(px * px * dot3d_m(P.ndir, pos) * (inv * inv * inv));
           float cap = 1.f;
           if (a.thickness > 0.0) {
             float rho = (float)dot3d_m(d, P.ndir);

@@ -27,6 +27,7 @@ __device__ __forceinline__ double mixed_pixel(const SpotArgs &a,
                                               unsigned &evals) {
   const double px = P.px;
   const int os = a.os;
+  const double inv_os = 1.0 / os;
   const float kahn = a.kahn;
   const float cutg = kGaussCut * 0.63f;
   double total = 0.0;
@@ -37,23 +38,25 @@ __device__ __forceinline__ double mixed_pixel(const SpotArgs &a,
         // ---- per subpixel / layer: geometry
         float df[3], vh[3], vl[3], omega, cap = 1.f;
         if (MODE == 0) {
-          double cf = (f + (i + 0.5) / os) * px, cs = (s + (j + 0.5) / os) * px,
-                 cn = t * a.dt;
+          // FP64 issues at 1/64 of the FP32 rate here: one reciprocal
+          // square root and products instead of divisions
+          double cf = (f + (i + 0.5) * inv_os) * px,
+                 cs = (s + (j + 0.5) * inv_os) * px, cn = t * a.dt;
           double pos[3], d[3];
 #pragma unroll
           for (int c = 0; c < 3; ++c)
             pos[c] = P.origin[c] + cf * P.fdir[c] + cs * P.sdir[c] +
                      cn * P.ndir[c];
-          double R = sqrt(dot3d_m(pos, pos));
+          const double inv = rsqrt(dot3d_m(pos, pos));
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
-            d[c] = pos[c] / R;
+            d[c] = pos[c] * inv;
             df[c] = (float)d[c];
             double v = d[c] - a.i0[c];
             vh[c] = (float)v;
             vl[c] = (float)(v - (double)vh[c]);
           }
-          omega = (float)(px * px * dot3d_m(P.ndir, pos) / (R * R * R));
+          omega = (float)(px * px * dot3d_m(P.ndir, pos) * (inv * inv * inv));
         } else {
           float cf = (f + (i + 0.5f) / os) * (float)px,
                 cs = (s + (j + 0.5f) / os) * (float)px, cn = t * (float)a.dt;

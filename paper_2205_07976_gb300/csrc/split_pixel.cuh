@@ -177,16 +177,16 @@ __device__ __forceinline__ void split_unit(const SpotArgs &a,
   const float kahn = a.kahn;
   int t = u % a.T, ij = u / a.T, i = ij / os, j = ij % os;
   double px = P.px;
-  double cf = (f + (i + 0.5) / os) * px, cs = (s + (j + 0.5) / os) * px,
-         cn = t * a.dt;
+  const double inv_os = 1.0 / os;
+  double cf = (f + (i + 0.5) * inv_os) * px,
+         cs = (s + (j + 0.5) * inv_os) * px, cn = t * a.dt;
   double pos[3], d[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c)
     pos[c] = P.origin[c] + cf * P.fdir[c] + cs * P.sdir[c] +
              cn * P.ndir[c];
-  // FP64 only where h needs it: one reciprocal of |P|, d = P / |P|
-  double R = sqrt(dot3d_m(pos, pos));
-  double inv = 1.0 / R;
+  // FP64 only where h needs it: one reciprocal square root, d = P / |P|
+  const double inv = rsqrt(dot3d_m(pos, pos));
   float df[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
