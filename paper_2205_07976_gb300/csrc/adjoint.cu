@@ -103,9 +103,7 @@ __global__ void __launch_bounds__(kTileThreads, INTERP ? 2 : 4)
   int q, s, f;
   if (map_pixel(a, item, threadIdx.x, gp, q, s, f)) {
     const DevPanel &P = a.panels[q];
-    const double px = P.px;
     const int os = a.os;
-    const double inv_os = 1.0 / os;
     const float kahn = a.kahn;
     const float cutg = kGaussCut * 0.63f;
     const double wp = g.dLdI[gp];
@@ -117,33 +115,21 @@ __global__ void __launch_bounds__(kTileThreads, INTERP ? 2 : 4)
     for (int i = 0; i < os; ++i)
       for (int j = 0; j < os; ++j)
         for (int t = 0; t < a.T; ++t) {
-          double cf = (f + (i + 0.5) * inv_os) * px,
-                 cs = (s + (j + 0.5) * inv_os) * px, cn = t * a.dt;
-          double pos[3], d[3];
-          float vh[3], vl[3], v32[3];
+          float vh[3], vl[3], v32[3], df[3], omega;
+          unit_geometry_ff(a, P, s, f, i, j, t, vh, vl, df, omega);
 #pragma unroll
-          for (int c = 0; c < 3; ++c)
-            pos[c] = P.origin[c] + cf * P.fdir[c] + cs * P.sdir[c] +
-                     cn * P.ndir[c];
-          const double inv = rsqrt(dot3d_m(pos, pos));
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            d[c] = pos[c] * inv;
-            double v = d[c] - a.i0[c];
-            vh[c] = (float)v;
-            vl[c] = (float)(v - (double)vh[c]);
-            v32[c] = vh[c];
-          }
-          float omega =
-              (float)(px * px * dot3d_m(P.ndir, pos) * (inv * inv * inv));
+          for (int c = 0; c < 3; ++c) v32[c] = vh[c];
           float cap = 1.f;
-          if (a.thickness > 0.0) {
-            float rho = (float)dot3d_m(d, P.ndir);
-            float L = (float)a.atten * rho, dtf = (float)a.dt;
+          if (a.dtff[0] > 0.f) {
+            float rho = df[0] * P.ffn[0][0] + df[1] * P.ffn[1][0] +
+                        df[2] * P.ffn[2][0];
+            float L = a.attenf * rho, dtf = a.dtff[0];
             cap = expf(-t * dtf / L) - expf(-(t + 1) * dtf / L);
           }
-          float c2 = (float)dot3d_m(d, a.i0), xe = (float)dot3d_m(d, a.e0),
-                ye = (float)dot3d_m(d, a.b0);
+          float c2 = df[0] * a.i0ff[0][0] + df[1] * a.i0ff[1][0] +
+                     df[2] * a.i0ff[2][0],
+                xe = df[0] * a.e0f[0] + df[1] * a.e0f[1] + df[2] * a.e0f[2],
+                ye = df[0] * a.b0f[0] + df[1] * a.b0f[1] + df[2] * a.b0f[2];
           float scal = omega * cap * 0.5f *
                        (1.f + c2 * c2 - kahn * (xe * xe - ye * ye));
           const double fscal = wks * (double)scal;  // for the F scatter

@@ -32,6 +32,87 @@ __device__ __forceinline__ void ff_dot3(const float *Ah, const float *Al,
   fast_two_sum(s2, lo, gh, gl);
 }
 
+// double-float sum and product (error-free transformations + one
+// renormalisation): about 48 significant bits in FP32 arithmetic
+__device__ __forceinline__ void ff_add(float ah, float al, float bh, float bl,
+                                       float &sh, float &sl) {
+  float s, e;
+  two_sum(ah, bh, s, e);
+  e = __fadd_rn(e, __fadd_rn(al, bl));
+  fast_two_sum(s, e, sh, sl);
+}
+
+__device__ __forceinline__ void ff_mul(float ah, float al, float bh, float bl,
+                                       float &ph, float &pl) {
+  float p, e;
+  two_prod(ah, bh, p, e);
+  e = __fmaf_rn(ah, bl, __fmaf_rn(al, bh, e));
+  fast_two_sum(p, e, ph, pl);
+}
+
+// Geometry of sub-pixel unit (i, j, layer t) of pixel (s, f) of panel P in
+// double-float FP32 arithmetic (FP64 issues at 1/64 of the FP32 rate on
+// this part): v = d - i0 as (vh, vl), d rounded to FP32, and the solid
+// angle omega = px^2 (n . P) / |P|^3 in FP32.  The reciprocal length is
+// the FP32 rsqrt estimate refined by one Newton step carried in
+// double-float, so d is good to ~1e-13.
+__device__ __forceinline__ void unit_geometry_ff(const SpotArgs &a,
+                                                 const DevPanel &P, int s,
+                                                 int f, int i, int j, int t,
+                                                 float vh[3], float vl[3],
+                                                 float df[3], float &omega) {
+  const float osf = (float)a.os;
+  // (i + 1/2) / os and (j + 1/2) / os as double-float pairs
+  const float oih = __fdiv_rn(i + 0.5f, osf);
+  const float oil = __fdiv_rn(__fmaf_rn(-oih, osf, i + 0.5f), osf);
+  const float ojh = __fdiv_rn(j + 0.5f, osf);
+  const float ojl = __fdiv_rn(__fmaf_rn(-ojh, osf, j + 0.5f), osf);
+  float uh, ul, wh, wl;
+  ff_add((float)f, 0.f, oih, oil, uh, ul);  // f, s are exact in FP32
+  ff_add((float)s, 0.f, ojh, ojl, wh, wl);
+  float cfh, cfl, csh, csl, cnh, cnl;
+  ff_mul(uh, ul, P.ffpx[0], P.ffpx[1], cfh, cfl);
+  ff_mul(wh, wl, P.ffpx[0], P.ffpx[1], csh, csl);
+  ff_mul((float)t, 0.f, a.dtff[0], a.dtff[1], cnh, cnl);
+  float ph[3], pl[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    float th, tl;
+    ph[c] = P.ffo[c][0];
+    pl[c] = P.ffo[c][1];
+    ff_mul(cfh, cfl, P.fff[c][0], P.fff[c][1], th, tl);
+    ff_add(ph[c], pl[c], th, tl, ph[c], pl[c]);
+    ff_mul(csh, csl, P.ffs[c][0], P.ffs[c][1], th, tl);
+    ff_add(ph[c], pl[c], th, tl, ph[c], pl[c]);
+    ff_mul(cnh, cnl, P.ffn[c][0], P.ffn[c][1], th, tl);
+    ff_add(ph[c], pl[c], th, tl, ph[c], pl[c]);
+  }
+  float r2h, r2l, th, tl;
+  ff_mul(ph[0], pl[0], ph[0], pl[0], r2h, r2l);
+  ff_mul(ph[1], pl[1], ph[1], pl[1], th, tl);
+  ff_add(r2h, r2l, th, tl, r2h, r2l);
+  ff_mul(ph[2], pl[2], ph[2], pl[2], th, tl);
+  ff_add(r2h, r2l, th, tl, r2h, r2l);
+  // y ~ |P|^-1; e = 1 - |P|^2 y^2 (small, 1 - qh is exact); y (1 + e/2)
+  const float y = rsqrtf(r2h);
+  float yy, yye, qh, ql;
+  two_prod(y, y, yy, yye);
+  ff_mul(r2h, r2l, yy, yye, qh, ql);
+  const float e = __fsub_rn(__fsub_rn(1.f, qh), ql);
+  float rih, ril;
+  fast_two_sum(y, 0.5f * y * e, rih, ril);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    float dh, dl;
+    ff_mul(ph[c], pl[c], rih, ril, dh, dl);
+    df[c] = dh;
+    ff_add(dh, dl, -a.i0ff[c][0], -a.i0ff[c][1], vh[c], vl[c]);
+  }
+  const float nd = P.ffn[0][0] * ph[0] + P.ffn[1][0] * ph[1] +
+                   P.ffn[2][0] * ph[2];
+  omega = P.ffpx[0] * P.ffpx[0] * nd * (rih * rih * rih);
+}
+
 // fractional offset of h = G (u0 + delta) - E relative to its nearest
 // integer, given r = G u0 - n0 (double-float).  Returns f = fh + fl and the
 // integer shift nf (h = n0 + nf + f).

@@ -27,10 +27,9 @@ __device__ __forceinline__ double mixed_pixel(const SpotArgs &a,
                                               unsigned &evals) {
   const double px = P.px;
   const int os = a.os;
-  const double inv_os = 1.0 / os;
   const float kahn = a.kahn;
   const float cutg = kGaussCut * 0.63f;
-  double total = 0.0;
+  float th = 0.f, tl = 0.f;  // the pixel's sum as a double-float pair
 
   for (int i = 0; i < os; ++i) {
     for (int j = 0; j < os; ++j) {
@@ -38,28 +37,10 @@ __device__ __forceinline__ double mixed_pixel(const SpotArgs &a,
         // ---- per subpixel / layer: geometry
         float df[3], vh[3], vl[3], omega, cap = 1.f;
         if (MODE == 0) {
-          // FP64 issues at 1/64 of the FP32 rate here: one reciprocal
-          // square root and products instead of divisions
-          double cf = (f + (i + 0.5) * inv_os) * px,
-                 cs = (s + (j + 0.5) * inv_os) * px, cn = t * a.dt;
-          double pos[3], d[3];
-#pragma unroll
-          for (int c = 0; c < 3; ++c)
-            pos[c] = P.origin[c] + cf * P.fdir[c] + cs * P.sdir[c] +
-                     cn * P.ndir[c];
-          const double inv = rsqrt(dot3d_m(pos, pos));
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            d[c] = pos[c] * inv;
-            df[c] = (float)d[c];
-            double v = d[c] - a.i0[c];
-            vh[c] = (float)v;
-            vl[c] = (float)(v - (double)vh[c]);
-          }
-          omega = (float)(px * px * dot3d_m(P.ndir, pos) * (inv * inv * inv));
+          unit_geometry_ff(a, P, s, f, i, j, t, vh, vl, df, omega);
         } else {
           float cf = (f + (i + 0.5f) / os) * (float)px,
-                cs = (s + (j + 0.5f) / os) * (float)px, cn = t * (float)a.dt;
+                cs = (s + (j + 0.5f) / os) * (float)px, cn = t * a.dtff[0];
           float pos[3];
 #pragma unroll
           for (int c = 0; c < 3; ++c)
@@ -72,24 +53,24 @@ __device__ __forceinline__ double mixed_pixel(const SpotArgs &a,
             vh[c] = df[c] - (float)a.i0[c];
             vl[c] = 0.f;
           }
-          float nd = pos[0] * (float)P.ndir[0] + pos[1] * (float)P.ndir[1] +
-                     pos[2] * (float)P.ndir[2];
+          float nd = pos[0] * P.ffn[0][0] + pos[1] * P.ffn[1][0] +
+                     pos[2] * P.ffn[2][0];
           omega = (float)px * (float)px * nd / (R * R * R);
         }
-        if (a.thickness > 0.0) {
-          float rho = df[0] * (float)P.ndir[0] + df[1] * (float)P.ndir[1] +
-                      df[2] * (float)P.ndir[2];
-          float L = (float)a.atten * rho, dtf = (float)a.dt;
+        if (a.dtff[0] > 0.f) {
+          float rho = df[0] * P.ffn[0][0] + df[1] * P.ffn[1][0] +
+                      df[2] * P.ffn[2][0];
+          float L = a.attenf * rho, dtf = a.dtff[0];
           cap = expf(-t * dtf / L) - expf(-(t + 1) * dtf / L);
         }
         float scal = omega * cap;
         if (!HASDIV) {
-          float c2 = df[0] * (float)a.i0[0] + df[1] * (float)a.i0[1] +
-                     df[2] * (float)a.i0[2];
-          float x = df[0] * (float)a.e0[0] + df[1] * (float)a.e0[1] +
-                    df[2] * (float)a.e0[2];
-          float y = df[0] * (float)a.b0[0] + df[1] * (float)a.b0[1] +
-                    df[2] * (float)a.b0[2];
+          float c2 = df[0] * a.i0ff[0][0] + df[1] * a.i0ff[1][0] +
+                     df[2] * a.i0ff[2][0];
+          float x = df[0] * a.e0f[0] + df[1] * a.e0f[1] +
+                    df[2] * a.e0f[2];
+          float y = df[0] * a.b0f[0] + df[1] * a.b0f[1] +
+                    df[2] * a.b0f[2];
           scal *= 0.5f * (1.f + c2 * c2 - kahn * (x * x - y * y));
         }
         Kahan acc;
@@ -230,11 +211,17 @@ __device__ __forceinline__ double mixed_pixel(const SpotArgs &a,
             acc.add(fc * fc * fl2 * w);
           }
         }
-        total += (double)scal * acc.value();
+        // the unit's compensated sum times scal, added in double-float
+        {
+          float uh, ul, ph, pl;
+          fast_two_sum(acc.s, -acc.c, uh, ul);
+          ff_mul(uh, ul, scal, 0.f, ph, pl);
+          ff_add(th, tl, ph, pl, th, tl);
+        }
       }
     }
   }
-  return total;
+  return (double)th + (double)tl;
 }
 
 }  // namespace nbgb

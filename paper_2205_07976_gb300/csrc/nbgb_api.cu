@@ -476,6 +476,7 @@ static void fill_args(const nb_sim *s, SpotArgs &a) {
   a.prefactor = nbgb::kElectronRadius * nbgb::kElectronRadius * s->fluence *
                 s->scale / ((double)s->os * s->os * s->n_mosaic * s->n_phi);
   a.image = (double *)s->d_image.p;
+  nbgb::args_ff(a);
 }
 
 // ------------------------------------------------------------------- ABI
@@ -720,6 +721,7 @@ int nb_set_detector(nb_sim *s, int n_panels, const nb_panel *panels,
     d.tile0 = tiles;
     d.tiles_f = (p.nfast + nbgb::kTileF - 1) / nbgb::kTileF;
     d.tiles = d.tiles_f * ((p.nslow + nbgb::kTileS - 1) / nbgb::kTileS);
+    nbgb::panel_ff(d);
     pix0[q] = npix;
     npix += (long long)p.nfast * p.nslow;
     if ((long long)tiles + d.tiles > 2000000000LL)

@@ -41,6 +41,9 @@ struct DevPanel {
   double sdir[3];
   double ndir[3];
   double px;
+  // the same vectors as double-float pairs (hi, lo) for the FP32 kernels'
+  // geometry (panel_ff fills them)
+  float ffo[3][2], fff[3][2], ffs[3][2], ffn[3][2], ffpx[2];
   long long pix0;  // global index of pixel (0, 0)
   int nfast, nslow;
   int tile0;       // first tile of this panel in the tiled launch
@@ -85,6 +88,9 @@ struct SpotArgs {
   double u0;
   float u0h, u0l;
   double i0[3];  // direction of source 0 (all sources, unless has_div)
+  float i0ff[3][2];  // i0 and dt as double-float pairs, and FP32 copies of
+  float dtff[2];     // e0, b0 and the attenuation length (args_ff)
+  float e0f[3], b0f[3], attenf;
   double e0[3], b0[3];
   float kahn;
   double kahn64;
@@ -96,6 +102,35 @@ struct SpotArgs {
   // Gaussian terms that underflow); null to skip counting
   unsigned long long *stats;
 };
+
+// host: v as a double-float pair, hi = v rounded to FP32, lo the rest
+inline void split_ff_host(double v, float ff[2]) {
+  ff[0] = (float)v;
+  ff[1] = (float)(v - (double)ff[0]);
+}
+
+// host: fills the double-float copies of a panel's vectors
+inline void panel_ff(DevPanel &d) {
+  for (int c = 0; c < 3; ++c) {
+    split_ff_host(d.origin[c], d.ffo[c]);
+    split_ff_host(d.fdir[c], d.fff[c]);
+    split_ff_host(d.sdir[c], d.ffs[c]);
+    split_ff_host(d.ndir[c], d.ffn[c]);
+  }
+  split_ff_host(d.px, d.ffpx);
+}
+
+// host: fills the double-float and FP32 copies of the beam vectors, the
+// layer thickness and the attenuation length in a filled SpotArgs
+inline void args_ff(SpotArgs &a) {
+  for (int c = 0; c < 3; ++c) {
+    split_ff_host(a.i0[c], a.i0ff[c]);
+    a.e0f[c] = (float)a.e0[c];
+    a.b0f[c] = (float)a.b0[c];
+  }
+  split_ff_host(a.dt, a.dtff);
+  a.attenf = (float)a.atten;
+}
 
 // adds v of every active lane to *ctr with one atomic per converged group
 __device__ __forceinline__ void warp_count(unsigned long long *ctr,

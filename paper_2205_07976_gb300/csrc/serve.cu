@@ -446,6 +446,7 @@ int nb_server_create(nb_server **out, int device, void *cuda_stream,
     P.px = panel->pixel_m;
     P.nfast = panel->nfast;
     P.nslow = panel->nslow;
+    nbgb::panel_ff(P);
     cudaMemcpy(s->d_panel.p, &P, sizeof P, cudaMemcpyHostToDevice);
     // shared kernel arguments
     nbgb::SpotArgs &a = s->base;
@@ -480,6 +481,7 @@ int nb_server_create(nb_server **out, int device, void *cuda_stream,
       a.e0[i] = ep[i];
       a.b0[i] = bp[i];
     }
+    nbgb::args_ff(a);
     double nn = Na * Nb * Nc;
     a.N6 = (float)(nn * nn);
     a.shape = NB_SHAPE_GAUSS;

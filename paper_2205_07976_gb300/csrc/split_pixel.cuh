@@ -176,46 +176,51 @@ __device__ __forceinline__ void split_unit(const SpotArgs &a,
   const int os = a.os;
   const float kahn = a.kahn;
   int t = u % a.T, ij = u / a.T, i = ij / os, j = ij % os;
-  double px = P.px;
-  const double inv_os = 1.0 / os;
-  double cf = (f + (i + 0.5) * inv_os) * px,
-         cs = (s + (j + 0.5) * inv_os) * px, cn = t * a.dt;
-  double pos[3], d[3];
+  float vh[3], vl[3], df[3], omega;
+  // FP64 here (one rsqrt, products): in these kernels the FP32 pipe is the
+  // busy one and the FP64 work of a batch of units overlaps with it; the
+  // double-float form (unit_geometry_ff, which the thread-per-pixel kernel
+  // uses) measured slower here
+  {
+    const double px = P.px, inv_os = 1.0 / os;
+    double cf = (f + (i + 0.5) * inv_os) * px,
+           cs = (s + (j + 0.5) * inv_os) * px, cn = t * a.dt;
+    double pos[3];
 #pragma unroll
-  for (int c = 0; c < 3; ++c)
-    pos[c] = P.origin[c] + cf * P.fdir[c] + cs * P.sdir[c] +
-             cn * P.ndir[c];
-  // FP64 only where h needs it: one reciprocal square root, d = P / |P|
-  const double inv = rsqrt(dot3d_m(pos, pos));
-  float df[3];
+    for (int c = 0; c < 3; ++c)
+      pos[c] = P.origin[c] + cf * P.fdir[c] + cs * P.sdir[c] +
+               cn * P.ndir[c];
+    const double inv = rsqrt(dot3d_m(pos, pos));
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const double d = pos[c] * inv, v = d - a.i0[c];
+      vh[c] = (float)v;
+      vl[c] = (float)(v - (double)vh[c]);
+      df[c] = (float)d;
+    }
+    omega = (float)(px * px * dot3d_m(P.ndir, pos) * (inv * inv * inv));
+  }
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    d[c] = pos[c] * inv;
-    double v = d[c] - a.i0[c];
-    float vh = (float)v;
-    ud[c] = vh;
-    ud[3 + c] = (float)(v - (double)vh);
-    df[c] = (float)d[c];
+    ud[c] = vh[c];
+    ud[3 + c] = vl[c];
     ud[7 + c] = df[c];
   }
-  float invf = (float)inv;
-  float omega = (float)(px * px) * (float)dot3d_m(P.ndir, pos) * invf *
-                invf * invf;
   float cap = 1.f;
-  if (a.thickness > 0.0) {
-    float rho = df[0] * (float)P.ndir[0] + df[1] * (float)P.ndir[1] +
-                df[2] * (float)P.ndir[2];
-    float L = (float)a.atten * rho, dtf = (float)a.dt;
+  if (a.dtff[0] > 0.f) {
+    float rho = df[0] * P.ffn[0][0] + df[1] * P.ffn[1][0] +
+                df[2] * P.ffn[2][0];
+    float L = a.attenf * rho, dtf = a.dtff[0];
     cap = expf(-t * dtf / L) - expf(-(t + 1) * dtf / L);
   }
   float scal = omega * cap;
   if (!HASDIV) {
-    float c2 = df[0] * (float)a.i0[0] + df[1] * (float)a.i0[1] +
-               df[2] * (float)a.i0[2];
-    float x = df[0] * (float)a.e0[0] + df[1] * (float)a.e0[1] +
-              df[2] * (float)a.e0[2];
-    float y = df[0] * (float)a.b0[0] + df[1] * (float)a.b0[1] +
-              df[2] * (float)a.b0[2];
+    float c2 = df[0] * a.i0ff[0][0] + df[1] * a.i0ff[1][0] +
+               df[2] * a.i0ff[2][0];
+    float x = df[0] * a.e0f[0] + df[1] * a.e0f[1] +
+              df[2] * a.e0f[2];
+    float y = df[0] * a.b0f[0] + df[1] * a.b0f[1] +
+              df[2] * a.b0f[2];
     scal *= 0.5f * (1.f + c2 * c2 - kahn * (x * x - y * y));
   }
   ud[6] = scal;

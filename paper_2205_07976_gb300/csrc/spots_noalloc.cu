@@ -193,6 +193,7 @@ extern "C" int nb_add_spots_noalloc(
   P.pix0 = 0;
   P.tiles_f = (P.nfast + kTileF - 1) / kTileF;
   P.tiles = P.tiles_f * ((P.nslow + kTileS - 1) / kTileS);
+  panel_ff(P);
   float *axh = (float *)sc;
   float *axl = axh + (size_t)n_pm * 9;
   float *src32 = axl + (size_t)n_pm * 9;
@@ -238,6 +239,7 @@ extern "C" int nb_add_spots_noalloc(
                 ((double)oversample * oversample * n_pm);
   a.image = image;
   a.stats = counters + 1;
+  args_ff(a);
   if (!split_supported(a)) return NB_EINVAL;
 
   TableArgs t;
