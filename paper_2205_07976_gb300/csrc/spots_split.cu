@@ -7,7 +7,8 @@
 // does not underflow in FP32, and each such term needs the structure factor
 // (64 gathers for tricubic interpolation).  With one thread per pixel those
 // terms are scattered over lanes and a warp serialises them.  Here:
-//   1. a warp takes B = 32 / U pixels at a time; its lanes set up the
+//   1. a warp takes B = 32 / U pixels at a time (one when it gets fewer
+//      than 256 pixels in all); its lanes set up the
 //      U = os^2 x layers sub-pixel units of all B pixels in FP64 (position,
 //      direction, solid angle, capture, polarization) into shared memory,
 //      then the warp sums the pixels one after another;
@@ -43,8 +44,11 @@ __global__ void __launch_bounds__(kSplitThreads, 6)
   unsigned long long evals = 0;  // terms evaluated by this warp
   // a warp takes B pixels at a time and sets up all their sub-pixel units
   // in one pass, so the FP64 geometry fills up to 32 lanes
+  // (one pixel at a time when a warp gets few pixels: pixels differ in
+  // cost, and grabbing several near the end of a launch leaves a tail)
   const int U = a.os * a.os * a.T;
-  const int B = kMaxUnits / U;
+  const long long per_warp = n_work / ((long long)gridDim.x * kSplitWarps);
+  const int B = per_warp >= 256 ? kMaxUnits / U : 1;
   float *unit = b.unit_base + warp * kMaxUnits * kUnitFloats;
   while (true) {
     long long first = 0;
