@@ -667,3 +667,51 @@ def test_background_sources_collapse_and_scale():
     t.ncells = t.ncells * 2
     bg3 = W.Background(stol=bg.stol, F=2 * bg.F, n_molecules=5 * bg.n_molecules)
     np.testing.assert_allclose(oracle.background(t, bg3), 60 * a, rtol=1e-14)
+
+
+# ------------------------------------------------ phi steps, divergence
+
+
+def test_phi_steps_equal_pre_rotated_axes():
+    # n_phi steps of phistep about the spindle, starting at phi0, average
+    # the images of the same crystal with its lab axes rotated by each angle
+    # beforehand (right-hand rotation about the spindle; the mosaic domains
+    # act after it)
+    Rot = pytest.importorskip("scipy.spatial.transform").Rotation
+    s = tiny_shot(n=6, n_mosaic=3, N=10.0)
+    k = np.array([0.3, 0.9, -0.2])
+    k /= np.linalg.norm(k)
+    s.spindle = k
+    s.n_phi, s.phi0_deg, s.phistep_deg = 3, 0.7, 0.35
+    got = oracle.image(s)
+    parts = []
+    for j in range(3):
+        ang = np.deg2rad(0.7 + 0.35 * j)
+        t = s.copy()
+        t.n_phi, t.phi0_deg, t.phistep_deg = 1, 0.0, 0.0
+        t.axes = Rot.from_rotvec(ang * k).apply(s.axes)
+        parts.append(oracle.image(t))
+    np.testing.assert_allclose(got, np.mean(parts, axis=0), rtol=1e-12,
+                               atol=1e-14 * got.max())
+    assert got.max() > 0
+
+
+def test_sources_of_different_directions_add_up():
+    # three sources of different directions and wavelengths: the image is
+    # the weighted sum of one-source images (each with its own direction
+    # in the scattering vector and the polarization)
+    s = tiny_shot(n=6, N=10.0)
+    s.kahn = 0.8
+    dirs = np.array([[0.0, 0.0, 1.0], [2e-3, -1e-3, 1.0], [-1.5e-3, 0.0, 1.0]])
+    dirs /= np.linalg.norm(dirs, axis=1)[:, None]
+    lam = np.array([1.30, 1.28, 1.32])
+    w = np.array([0.5, 0.3, 0.2])
+    s.dirs, s.lambdas, s.weights = dirs, lam, w
+    got = oracle.image(s)
+    want = np.zeros_like(got)
+    for k in range(3):
+        t = s.copy()
+        t.dirs, t.lambdas, t.weights = dirs[k:k + 1], lam[k:k + 1], np.ones(1)
+        want += w[k] * oracle.image(t)
+    np.testing.assert_allclose(got, want, rtol=1e-13, atol=1e-15 * got.max())
+    assert got.max() > 0
