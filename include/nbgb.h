@@ -287,8 +287,9 @@ int nb_server_submit(nb_server *srv, const double axes[9],
 
 /* One scheduling step: admit queued requests (FIFO; a request that does
  * not fit may be passed by later ones until it has waited 8 steps), cut
- * the running requests into work items round robin up to the pixel-step
- * budget and queue them on the GPU, then wait (up to timeout_s seconds)
+ * the running requests into work items up to the pixel-step budget (one
+ * item for every running request, then the oldest requests first) and
+ * queue them on the GPU, then wait (up to timeout_s seconds)
  * for the step queued by the previous call, so that one step runs while
  * the next is prepared.  When there is nothing new to queue, the call
  * waits for every step in flight.  A request completes when the step
@@ -296,8 +297,9 @@ int nb_server_submit(nb_server *srv, const double axes[9],
  * image stays in the pool until fetched.  *n_active (may be NULL) =
  * queued + running.  Errors: NB_ETIMEOUT if a step waited for is still
  * running after timeout_s (a later call waits for it again); NB_ESTATE if
- * requests are queued but nothing runs and none can be admitted (the pool
- * is held by unfetched results: fetch them); NB_ECUDA. */
+ * requests are queued but nothing runs, none can be admitted and the call
+ * completed nothing (the pool is held by unfetched results: fetch them);
+ * NB_ECUDA. */
 int nb_server_step(nb_server *srv, double timeout_s, int *n_active);
 
 /* Ids of requests completed since the last call (up to max_ids); a

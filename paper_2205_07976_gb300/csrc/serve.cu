@@ -10,8 +10,8 @@
 //   step    -> admit while a slot and room in the image pool exist (first
 //              fit; a blocked head request stops bypassing after 8 steps);
 //              cut the active requests into work items (128 pixels for the
-//              thread kernel, 32 for the warp kernel), round robin, up to a
-//              pixel-step budget; replay one of two CUDA graphs (work list
+//              thread kernel, 32 for the warp kernel) up to a pixel-step
+//              budget: one item for every request, then oldest first; replay one of two CUDA graphs (work list
 //              upload from its own pinned buffer, counter reset, the two
 //              persistent kernels); then wait for the step queued by the
 //              previous call, so the GPU runs one step while the host
@@ -258,7 +258,6 @@ struct nb_server {
   std::vector<int> free_slots;
   std::map<long long, long long> free_ranges;  // offset -> length
   std::vector<long long> completed;            // not yet reported
-  long long rr_cursor = 0;
 };
 
 static int sfail(nb_server *s, int code, const std::string &m) {
@@ -729,7 +728,6 @@ int nb_server_step(nb_server *s, double timeout_s, int *n_active) {
   if (s->in_flight[s->cur]) rc = finish_oldest(s, timeout_s);
   if (rc == NB_OK) rc = admit(s);
   if (rc == NB_OK) {
-    // round-robin cut of the active requests into work items
     std::vector<Request *> act, finished;
     for (auto &kv : s->reqs)
       if (kv.second.state == NB_REQ_RUNNING && kv.second.next < kv.second.npix)
@@ -737,19 +735,20 @@ int nb_server_step(nb_server *s, double timeout_s, int *n_active) {
     WorkList *wl = s->h_work[s->cur], *ww = s->h_work_w[s->cur];
     int nt = 0, nw = 0;
     long long used = 0;
-    if (!act.empty()) {
-      size_t start = (size_t)(s->rr_cursor % (long long)act.size());
-      bool progress = true;
-      while (progress && used < s->budget) {
-        progress = false;
-        for (size_t j = 0; j < act.size() && used < s->budget; ++j) {
-          Request &r = *act[(start + j) % act.size()];
-          if (r.next >= r.npix) continue;
-          WorkList *L = r.warp ? ww : wl;
-          int &n = r.warp ? nw : nt;
-          if (n >= nbgb::kServeMaxItems) continue;
-          long long cap = r.warp ? nbgb::kServeWarpItemPixels
-                                 : nbgb::kServeItemPixels;
+    // every active request gets one work item (none starves), then the
+    // rest of the budget goes to the oldest requests first: fewer requests
+    // per step means fewer table restagings per block, and requests finish
+    // sooner (act is in arrival order: the map is keyed by request id)
+    for (int pass = 0; pass < 2 && used < s->budget; ++pass) {
+      for (size_t j = 0; j < act.size() && used < s->budget; ++j) {
+        Request &r = *act[j];
+        WorkList *L = r.warp ? ww : wl;
+        int &n = r.warp ? nw : nt;
+        const long long cap = r.warp ? nbgb::kServeWarpItemPixels
+                                     : nbgb::kServeItemPixels;
+        for (int k = 0; r.next < r.npix && used < s->budget &&
+                        n < nbgb::kServeMaxItems && (pass == 1 || k < 1);
+             ++k) {
           long long cnt = r.npix - r.next;
           if (cnt > cap) cnt = cap;
           L->items[n].slot = r.slot;
@@ -759,10 +758,8 @@ int nb_server_step(nb_server *s, double timeout_s, int *n_active) {
           r.next += cnt;
           if (r.next >= r.npix) finished.push_back(&r);
           used += cnt * r.steps_per_pixel;
-          progress = true;
         }
       }
-      s->rr_cursor += 1;
     }
     wl->n = nt;
     ww->n = nw;
@@ -783,8 +780,11 @@ int nb_server_step(nb_server *s, double timeout_s, int *n_active) {
       }
     } else {
       // nothing new to run: drain the steps in flight
+      const size_t done_before = s->completed.size();
       while (rc == NB_OK && !s->flight.empty()) rc = finish_oldest(s, timeout_s);
-      if (rc == NB_OK && !s->queue.empty()) {
+      // a stall only when this call completed nothing the caller could fetch
+      if (rc == NB_OK && !s->queue.empty() &&
+          s->completed.size() == done_before) {
         const size_t before = s->queue.size();
         rc = admit(s);
         if (rc == NB_OK && s->queue.size() == before && !any_schedulable(s))
