@@ -10,7 +10,7 @@
 //   step    -> admit while a slot and room in the image pool exist (first
 //              fit; a blocked head request stops bypassing after 8 steps);
 //              cut the active requests into work items (128 pixels for the
-//              thread kernel, 32 for the warp kernel) up to a pixel-step
+//              thread kernel, 64 for the warp kernel) up to a pixel-step
 //              budget: one item for every request, then oldest first; replay one of two CUDA graphs (work list
 //              upload from its own pinned buffer, counter reset, the two
 //              persistent kernels); then wait for the step queued by the
@@ -45,7 +45,7 @@ namespace nbgb {
 constexpr int kServeMaxPM = 64;
 constexpr int kServeMaxSrc = 128;
 constexpr int kServeItemPixels = kTileThreads;  // one pixel per thread
-constexpr int kServeWarpItemPixels = 32;  // warp kernel: 8 pixels per warp
+constexpr int kServeWarpItemPixels = 64;  // warp kernel: 16 pixels per warp
 constexpr int kServeMaxItems = 16384;
 
 struct SlotParams {
