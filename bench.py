@@ -81,7 +81,7 @@ def parse():
                          "grad")
     ap.add_argument("--serve-requests", type=int, default=4096)
     ap.add_argument("--serve-seq-subset", type=int, default=16)
-    ap.add_argument("--serve-budget", type=int, default=1_000_000_000,
+    ap.add_argument("--serve-budget", type=int, default=2_000_000_000,
                     help="pixel-steps per serving step")
     return ap.parse_args()
 
