@@ -729,9 +729,12 @@ int nb_server_step(nb_server *s, double timeout_s, int *n_active) {
   if (rc == NB_OK) rc = admit(s);
   if (rc == NB_OK) {
     std::vector<Request *> act, finished;
+    std::vector<long long> next0;  // to undo the cut if the launch fails
     for (auto &kv : s->reqs)
-      if (kv.second.state == NB_REQ_RUNNING && kv.second.next < kv.second.npix)
+      if (kv.second.state == NB_REQ_RUNNING && kv.second.next < kv.second.npix) {
         act.push_back(&kv.second);
+        next0.push_back(kv.second.next);
+      }
     WorkList *wl = s->h_work[s->cur], *ww = s->h_work_w[s->cur];
     int nt = 0, nw = 0;
     long long used = 0;
@@ -768,6 +771,7 @@ int nb_server_step(nb_server *s, double timeout_s, int *n_active) {
       cudaError_t e = cudaGraphLaunch(s->graph[b], s->stream);
       if (e == cudaSuccess) e = cudaEventRecord(s->done_ev[b], s->stream);
       if (e != cudaSuccess) {
+        for (size_t j = 0; j < act.size(); ++j) act[j]->next = next0[j];
         rc = sfail(s, NB_ECUDA, "graph launch");
       } else {
         s->in_flight[b] = true;
