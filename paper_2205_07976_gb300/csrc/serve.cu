@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(kTileThreads, 4)
 // each work item stages its request's tables once, then each warp sums its
 // pixels with the same device function as the stand-alone kernel.
 template <int INTERP>
-__global__ void __launch_bounds__(kSplitThreads, 6)
+__global__ void __launch_bounds__(kSplitThreads, 5)
     serve_warp_kernel(SpotArgs base, const SlotParams *slots,
                       const WorkList *wl, unsigned *counter, double *pool) {
   extern __shared__ float sms[];

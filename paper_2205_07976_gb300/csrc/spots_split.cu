@@ -34,7 +34,7 @@
 namespace nbgb {
 
 template <int INTERP, int HASDIV>
-__global__ void __launch_bounds__(kSplitThreads, 6)
+__global__ void __launch_bounds__(kSplitThreads, 5)
     spots_split_kernel(SpotArgs a, unsigned long long *work) {
   extern __shared__ float sms[];
   SplitBlock b;
