@@ -287,8 +287,9 @@ int nb_server_submit(nb_server *srv, const double axes[9],
 
 /* One scheduling step: admit queued requests (FIFO; a request that does
  * not fit may be passed by later ones until it has waited 8 steps), cut
- * the running requests into work items up to the pixel-step budget (one
- * item for every running request, then the oldest requests first) and
+ * the running requests into work items up to the pixel-step budget (half
+ * of it shared equally by the running requests, at least one item each;
+ * the rest to the oldest requests first) and
  * queue them on the GPU, then wait (up to timeout_s seconds)
  * for the step queued by the previous call, so that one step runs while
  * the next is prepared.  When there is nothing new to queue, the call

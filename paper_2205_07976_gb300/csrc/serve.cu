@@ -11,7 +11,8 @@
 //              fit; a blocked head request stops bypassing after 8 steps);
 //              cut the active requests into work items (128 pixels for the
 //              thread kernel, 64 for the warp kernel) up to a pixel-step
-//              budget: one item for every request, then oldest first; replay one of two CUDA graphs (work list
+//              budget: half shared equally by the running requests, the
+//              rest to the oldest first; replay one of two CUDA graphs (work list
 //              upload from its own pinned buffer, counter reset, the two
 //              persistent kernels); then wait for the step queued by the
 //              previous call, so the GPU runs one step while the host
@@ -738,10 +739,14 @@ int nb_server_step(nb_server *s, double timeout_s, int *n_active) {
     WorkList *wl = s->h_work[s->cur], *ww = s->h_work_w[s->cur];
     int nt = 0, nw = 0;
     long long used = 0;
-    // every active request gets one work item (none starves), then the
-    // rest of the budget goes to the oldest requests first: fewer requests
-    // per step means fewer table restagings per block, and requests finish
-    // sooner (act is in arrival order: the map is keyed by request id)
+    // half of the budget is shared equally by the active requests (at
+    // least one work item each, so none starves and a new request is not
+    // stuck behind an old large one), the rest goes to the oldest requests
+    // first: fewer requests per step means fewer table restagings per
+    // block, and requests finish sooner (act is in arrival order: the map
+    // is keyed by request id)
+    const long long share =
+        act.empty() ? 0 : s->budget / (2 * (long long)act.size());
     for (int pass = 0; pass < 2 && used < s->budget; ++pass) {
       for (size_t j = 0; j < act.size() && used < s->budget; ++j) {
         Request &r = *act[j];
@@ -749,8 +754,10 @@ int nb_server_step(nb_server *s, double timeout_s, int *n_active) {
         int &n = r.warp ? nw : nt;
         const long long cap = r.warp ? nbgb::kServeWarpItemPixels
                                      : nbgb::kServeItemPixels;
+        long long mine = 0;  // pixel-steps given to r in this pass
         for (int k = 0; r.next < r.npix && used < s->budget &&
-                        n < nbgb::kServeMaxItems && (pass == 1 || k < 1);
+                        n < nbgb::kServeMaxItems &&
+                        (pass == 1 || k < 1 || mine < share);
              ++k) {
           long long cnt = r.npix - r.next;
           if (cnt > cap) cnt = cap;
@@ -761,6 +768,7 @@ int nb_server_step(nb_server *s, double timeout_s, int *n_active) {
           r.next += cnt;
           if (r.next >= r.npix) finished.push_back(&r);
           used += cnt * r.steps_per_pixel;
+          mine += cnt * r.steps_per_pixel;
         }
       }
     }
