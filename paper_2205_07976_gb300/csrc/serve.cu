@@ -12,10 +12,10 @@
 //              cut the active requests into work items (128 pixels for the
 //              thread kernel, 64 for the warp kernel) up to a pixel-step
 //              budget: half shared equally by the running requests, the
-//              rest to the oldest first; replay one of two CUDA graphs (work list
-//              upload from its own pinned buffer, counter reset, the two
-//              persistent kernels); then wait for the step queued by the
-//              previous call, so the GPU runs one step while the host
+//              rest to the oldest first; replay one of two CUDA graphs
+//              (work list upload from its own pinned buffer, counter reset,
+//              the two persistent kernels); then wait for the step queued
+//              by the previous call, so the GPU runs one step while the host
 //              prepares the next; requests whose last item ran in a
 //              finished step are complete
 //   result  -> copy the image out on a separate stream, free its pool
