@@ -168,3 +168,34 @@ def test_unfetched_results_stall_admission_instead_of_spinning(base):
     images = srv.run_all(fetch=True)
     assert len(images) >= 1
     srv.close()
+
+
+def test_new_request_is_not_stuck_behind_a_large_old_one(base):
+    """Half of each step's budget is shared equally by the running
+    requests: a request submitted after a large one finishes within a few
+    steps instead of advancing one work item per step."""
+    # 3.4e6 pixels, 30 domains, 64 sources (33 budgets of work); 24198
+    # pixels, 14 domains, 6 sources (378 warp-kernel items)
+    big = W.serving_requests(1, seed=30, max_src=100, max_mosaic=50,
+                             min_pix=2e6, max_pix=4e6)[0]
+    small = W.serving_requests(1, seed=22, max_src=20, max_mosaic=20,
+                               min_pix=2e4, max_pix=3e4)[0]
+    assert big.pixel_steps > 30 * 2 * 10 ** 8 and small.npix > 300 * 64
+    budget = 2 * 10 ** 8
+    srv = nbgb.Server(base, max_slots=4, pool_bytes=64 << 20,
+                      step_budget=budget)
+    rb = submit(srv, big)
+    srv.step()
+    rs = submit(srv, small)
+    steps = 0
+    while srv.state(rs) != nbgb.NB_REQ_DONE:
+        srv.step()
+        steps += 1
+        assert steps < 1000
+    # the small request's share is budget / 4 per step (two requests
+    # running); one more step for the pipelined completion
+    share_steps = -(-small.pixel_steps // (budget // 4))
+    assert steps <= share_steps + 3, (steps, share_steps)
+    assert srv.state(rb) in (nbgb.NB_REQ_RUNNING, nbgb.NB_REQ_DONE)
+    srv.run_all()
+    srv.close()
