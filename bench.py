@@ -189,11 +189,18 @@ def cpu_baseline(shot, every: int, threads: int = 0):
     oracle.image(shot, pix, nthreads=threads)
     dt = time.perf_counter() - t0
     steps = len(pix) * shot.steps_per_pixel
+    # one thread, on the first 1024 pixels of that sample
+    one = pix[:1024]
+    t1 = time.perf_counter()
+    oracle.image(shot, one, nthreads=1)
+    d1 = time.perf_counter() - t1
     return {"value": steps / dt, "unit": UNIT,
             "cores": threads or oracle.max_threads(), "kind": "oracle",
             "sample": f"every {every}th row of the large shot "
                       f"({len(pix)} pixels, {steps:.3e} pixel-steps, "
-                      f"{dt:.1f} s)"}
+                      f"{dt:.1f} s)",
+            "single_thread_value": len(one) * shot.steps_per_pixel / d1,
+            "single_thread_sample": f"{len(one)} of those pixels, {d1:.1f} s"}
 
 
 # ------------------------------------------------------------ our arm
