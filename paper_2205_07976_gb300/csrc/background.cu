@@ -240,14 +240,36 @@ __global__ void __launch_bounds__(kTileThreads)
                                : 1 + bg_search(&s_k4[1].x, 4, n, st);
           }
           float4 kb = s_k4[e];
-          Kahan ks;
-#pragma unroll 2
-          for (int k = k0; k < k1; ++k) {
+          // the source terms of one block of up to 32 sources go into four
+          // plain FP32 chains (at most 8 positive terms each, so the block
+          // sum is within 10 ulp); the blocks are added compensated, which
+          // keeps the bound independent of the number of sources
+          auto term = [&](int k) {
             const float2 uw = s_src[k];
             const float st = half * uw.x;
             while (st >= kb.w) kb = s_k4[++e];
             const float Fb = fmaf(st - kb.x, kb.z, kb.y);
-            ks.add(Fb * Fb * uw.y);
+            return make_float2(Fb * uw.y, Fb);
+          };
+          Kahan ks;
+          for (int k = k0; k < k1;) {
+            const int kend = min(k + 32, k1);
+            float c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
+            for (; k + 4 <= kend; k += 4) {
+              float2 t0 = term(k);
+              c0 = fmaf(t0.x, t0.y, c0);
+              float2 t1 = term(k + 1);
+              c1 = fmaf(t1.x, t1.y, c1);
+              float2 t2 = term(k + 2);
+              c2 = fmaf(t2.x, t2.y, c2);
+              float2 t3 = term(k + 3);
+              c3 = fmaf(t3.x, t3.y, c3);
+            }
+            for (; k < kend; ++k) {
+              float2 t0 = term(k);
+              c0 = fmaf(t0.x, t0.y, c0);
+            }
+            ks.add((c0 + c1) + (c2 + c3));
           }
           acc.add(__fsub_rn(ks.s, ks.c) * (fac * pol));
         }

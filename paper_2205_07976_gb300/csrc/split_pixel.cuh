@@ -14,8 +14,11 @@ constexpr int kSplitThreads = kSplitWarps * 32;
 constexpr int kRing = 64;
 constexpr int kMaxUnits = 32;
 constexpr int kUnitFloats = 10;  // vh[3], vl[3], scal, df[3]
-constexpr int kStateStride = 17;  // per-lane item state: G, r, n0, scal
-                                  // (odd: distinct owners hit distinct banks)
+// per-lane item state, 9 float2: (G_hi, r_q) and (G_lo, r_lo) per axis,
+// (n0_h, n0_k), (n0_l, scal), one unused.  Pairs halve the shared loads;
+// the odd pair stride keeps distinct owners on distinct bank pairs unless
+// they are 16 lanes apart.
+constexpr int kStateStride = 18;
 constexpr int kCandRing = 64;     // per-warp ring of (lane, source block)
 constexpr int kSrcBlock = 8;      // sources per pruning block
 
@@ -79,9 +82,9 @@ struct SplitBlock {
   int *cring_base;
   SplitRing *rings;
   int PM, S, nblk, sstep;
-  float u0h, u0l, cwide, dmin, dmax, dmarg;
+  float u0h, u0l, cwide, dmin, dmax, dmarg, inv_step;
   float cmarg[3];
-  bool iv_ok;
+  bool iv_ok, even;
 };
 
 // Stages a shot's tables (double-float axes [PM][9], source rows [S][12])
@@ -164,6 +167,37 @@ __device__ __forceinline__ void split_stage(SplitBlock &b, float *sms,
   int sstep = 1;
   while (sstep * 2 <= S) sstep *= 2;
   b.sstep = sstep;
+  // nearly even delta spacing (an equispaced spectrum): the position of a
+  // bound in the table is then guessed from the spacing and corrected by a
+  // step or two, instead of a binary search
+  const float step = S > 1 ? (b.dmax - b.dmin) / (float)(S - 1) : 0.f;
+  int uneven = !(step > 0.f);
+  for (int k = threadIdx.x; k < S && !uneven; k += blockDim.x)
+    uneven |= !(fabsf(s_dh[k] - fmaf((float)k, step, b.dmin)) <= step);
+  b.even = __syncthreads_or(uneven) == 0;
+  b.inv_step = b.even ? 1.f / step : 0.f;
+}
+
+// k1 = #{k : delta_k < lo} and k2 = #{k : delta_k <= hi} in the ascending
+// table dh[0..S): from a guess, walk down while the entry below is on the
+// wrong side, then up while the entry above is.  Exact for any guess in
+// [0, S]; the guess only sets the number of steps.
+__device__ __forceinline__ int count_below(const float *dh, int S, int k,
+                                           float lo) {
+  while (k > 0 && dh[k - 1] >= lo) --k;
+  while (k < S && dh[k] < lo) ++k;
+  return k;
+}
+__device__ __forceinline__ int count_at_most(const float *dh, int S, int k,
+                                             float hi) {
+  while (k > 0 && dh[k - 1] > hi) --k;
+  while (k < S && dh[k] <= hi) ++k;
+  return k;
+}
+__device__ __forceinline__ int guess_index(float x, float dmin, float inv,
+                                           int S) {
+  // fmaxf/fminf also map a NaN to 0
+  return (int)fminf(fmaxf(ceilf((x - dmin) * inv), 0.f), (float)S);
 }
 
 // Geometry of sub-pixel unit u (subpixel i, j, sensor layer t) of pixel
@@ -251,6 +285,8 @@ __device__ __forceinline__ double split_sum(const SpotArgs &a,
   const float cmarg[3] = {b.cmarg[0], b.cmarg[1], b.cmarg[2]};
   const bool iv_ok = b.iv_ok;
   const float dmin = b.dmin, dmax = b.dmax, dmarg = b.dmarg;
+  const bool even = b.even;
+  const float inv_step = b.inv_step;
   const float u0h = b.u0h, u0l = b.u0l;
 
   // ---- 2./3. scan the steps, evaluate surviving terms 32 at a time
@@ -345,16 +381,14 @@ __device__ __forceinline__ double split_sum(const SpotArgs &a,
       // farther than sqrt(cut)/N_x from every integer holds no surviving
       // term.  Surviving (lane, block) pairs go into a ring; the warp
       // then runs 4 blocks x 8 sources = 32 steps at a time.
-      float *my = st + lane * kStateStride;
+      float2 *my = reinterpret_cast<float2 *>(st + lane * kStateStride);
 #pragma unroll
       for (int x = 0; x < 3; ++x) {
-        my[x] = Gh[x];
-        my[3 + x] = Gl[x];
-        my[6 + x] = rq[x];
-        my[9 + x] = rl[x];
-        my[12 + x] = n0[x];
+        my[x] = make_float2(Gh[x], rq[x]);
+        my[3 + x] = make_float2(Gl[x], rl[x]);
       }
-      my[15] = scal;
+      my[6] = make_float2(n0[0], n0[1]);
+      my[7] = make_float2(n0[2], scal);
       __syncwarp();
       int ch = 0, ct = 0;
       auto run_cands = [&](int nc) {
@@ -365,12 +399,15 @@ __device__ __forceinline__ double split_sum(const SpotArgs &a,
         int own = ent & 31, k0 = (ent >> 5) & 2047, cnt = (ent >> 16) & 15;
         int k = k0 + kk;
         ok = ok && kk < cnt && k < S;
-        const float *o = st + own * kStateStride;
+        const float2 *o =
+            reinterpret_cast<const float2 *>(st + own * kStateStride);
         const float dh = s_dh[ok ? k : 0];
         float fr[3], nf[3];
+        float2 gr[3];
 #pragma unroll
         for (int x = 0; x < 3; ++x) {
-          float tq = fmaf(o[x], dh, o[6 + x]);
+          gr[x] = o[x];  // (G_hi, r_q)
+          float tq = fmaf(gr[x].x, dh, gr[x].y);
           nf[x] = rintf(tq);
           fr[x] = tq - nf[x];
         }
@@ -384,16 +421,19 @@ __device__ __forceinline__ double split_sum(const SpotArgs &a,
           const float *src = s_src + k * SRC32_STRIDE;
           const float dl = src[SRC32_DL];
           int e = (tail + __popc(m & lt_mask)) & (kRing - 1);
+          const float2 n01 = o[6], n2s = o[7];
+          const float n0o[3] = {n01.x, n01.y, n2s.x};
           float f[3];
           int nn[3];
 #pragma unroll
           for (int x = 0; x < 3; ++x) {
-            float sx = fmaf(o[x], dh, __fsub_rn(o[6 + x], nf[x]));
-            float c = fmaf(o[x], dl, fmaf(o[3 + x], dh, o[9 + x]));
+            const float2 gl = o[3 + x];  // (G_lo, r_lo)
+            float sx = fmaf(gr[x].x, dh, __fsub_rn(gr[x].y, nf[x]));
+            float c = fmaf(gr[x].x, dl, fmaf(gl.x, dh, gl.y));
             f[x] = sx + c;
-            nn[x] = __float2int_rn(o[12 + x] + nf[x]) - a.hmin[x];
+            nn[x] = __float2int_rn(n0o[x] + nf[x]) - a.hmin[x];
           }
-          q.fw[e] = make_float4(f[0], f[1], f[2], src[SRC32_W] * o[15]);
+          q.fw[e] = make_float4(f[0], f[1], f[2], src[SRC32_W] * n2s.y);
           q.n[e] = make_int4(nn[0], nn[1], nn[2], 0);
         }
         tail += __popc(m);
@@ -451,9 +491,16 @@ __device__ __forceinline__ double split_sum(const SpotArgs &a,
                 lo -= mg;
                 hi += mg;
                 // k1 = #{delta < lo}, k2 = #{delta <= hi} (sorted table)
-                for (int st = sstep; st > 0; st >>= 1) {
-                  if (k1 + st <= S && s_dh[k1 + st - 1] < lo) k1 += st;
-                  if (k2 + st <= S && s_dh[k2 + st - 1] <= hi) k2 += st;
+                if (even) {
+                  k1 = count_below(s_dh, S, guess_index(lo, dmin, inv_step, S),
+                                   lo);
+                  k2 = count_at_most(s_dh, S,
+                                     guess_index(hi, dmin, inv_step, S), hi);
+                } else {
+                  for (int st = sstep; st > 0; st >>= 1) {
+                    if (k1 + st <= S && s_dh[k1 + st - 1] < lo) k1 += st;
+                    if (k2 + st <= S && s_dh[k2 + st - 1] <= hi) k2 += st;
+                  }
                 }
               }
             } else if (C0 <= cwide) {
