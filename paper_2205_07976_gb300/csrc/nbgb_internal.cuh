@@ -5,7 +5,7 @@
 //   ax64     double[PM][9]                 U_m R_phi (a,b,c)_lab, PM = Phi*M
 //   axh/axl  float[PM][9]                  double-float split of ax64
 //   src64    double[S][SRC64_STRIDE]       lambda, w, dir, E', B'
-//   src32    float [S][SRC32_STRIDE]       delta_hi, delta_lo, w, dir, E', B'
+//   src32    float [S][SRC32_STRIDE]       delta_lo, w, delta_hi, dir, E', B'
 //   divh/l   float[PM][S][3]               divergence term (only if sources
 //                                           do not share one direction)
 //   F        float[nh][nk][nl]             structure factors, l fastest
@@ -32,7 +32,8 @@ constexpr float kGaussCut = 44.0f;
 
 enum { SRC64_LAM = 0, SRC64_W = 1, SRC64_DIR = 2, SRC64_E = 5, SRC64_B = 8,
        SRC64_STRIDE = 11 };
-enum { SRC32_DH = 0, SRC32_DL = 1, SRC32_W = 2, SRC32_DIR = 3, SRC32_E = 6,
+// (delta_lo, w) first: the warp kernel reads the pair as one float2
+enum { SRC32_DL = 0, SRC32_W = 1, SRC32_DH = 2, SRC32_DIR = 3, SRC32_E = 6,
        SRC32_B = 9, SRC32_STRIDE = 12 };
 
 struct DevPanel {

@@ -27,6 +27,33 @@ struct SplitRing {
   int4 n[kRing];     // table-relative nearest index (h, k, l), unused
 };
 static_assert(sizeof(SplitRing) % 16 == 0, "rings stay 16-byte aligned");
+static_assert(SRC32_DL % 2 == 0 && SRC32_W == SRC32_DL + 1 &&
+                  SRC32_STRIDE % 2 == 0 && kUnitFloats % 2 == 0,
+              "float2 reads of (delta_lo, w) and of the unit rows");
+
+// ff_dot3 (mixed_common.cuh) with the double-float row stored as
+// interleaved (hi, lo) pairs: the same operations, half the shared loads
+__device__ __forceinline__ void ff_dot3_pairs(const float2 *A,
+                                              const float *vh,
+                                              const float *vl, float &gh,
+                                              float &gl) {
+  const float2 a0 = A[0], a1 = A[1], a2 = A[2];
+  float p0, e0, p1, e1, p2, e2;
+  two_prod(a0.x, vh[0], p0, e0);
+  two_prod(a1.x, vh[1], p1, e1);
+  two_prod(a2.x, vh[2], p2, e2);
+  float s, t, s2, t2;
+  two_sum(p0, p1, s, t);
+  two_sum(s, p2, s2, t2);
+  float lo = e0 + e1 + e2 + t + t2;
+  lo = fmaf(a0.x, vl[0], lo);
+  lo = fmaf(a1.x, vl[1], lo);
+  lo = fmaf(a2.x, vl[2], lo);
+  lo = fmaf(a0.y, vh[0], lo);
+  lo = fmaf(a1.y, vh[1], lo);
+  lo = fmaf(a2.y, vh[2], lo);
+  fast_two_sum(s2, lo, gh, gl);
+}
 
 template <int INTERP>
 __device__ __forceinline__ void eval_term(const SpotArgs &a,
@@ -77,7 +104,8 @@ __device__ __forceinline__ void eval_term(const SpotArgs &a,
 // Per-block view of one shot's staged tables in shared memory and the
 // constants derived from them.
 struct SplitBlock {
-  const float *axh, *axl, *src, *blk, *dh;
+  const float2 *ax2;  // [PM][9] (hi, lo) pairs
+  const float *src, *blk, *dh;
   float *unit_base, *state_base;
   int *cring_base;
   SplitRing *rings;
@@ -87,17 +115,17 @@ struct SplitBlock {
   bool iv_ok, even;
 };
 
-// Stages a shot's tables (double-float axes [PM][9], source rows [S][12])
-// into the dynamic shared memory `sms` and derives the pruning constants.
-// Called by every thread of the block.
+// Stages a shot's tables (double-float axes [PM][9], interleaved into
+// (hi, lo) pairs, and source rows [S][12]) into the dynamic shared memory
+// `sms` and derives the pruning constants.  Called by every thread of the
+// block.
 __device__ __forceinline__ void split_stage(SplitBlock &b, float *sms,
                                             const SpotArgs &a,
                                             const float *axh, const float *axl,
                                             const float *src32, int PM, int S,
                                             float u0h, float u0l) {
-  float *s_axh = sms;
-  float *s_axl = s_axh + PM * 9;
-  float *s_src = s_axl + PM * 9;
+  float2 *s_ax2 = reinterpret_cast<float2 *>(sms);
+  float *s_src = sms + 2 * PM * 9;
   float *s_unit = s_src + S * SRC32_STRIDE;  // [warp][unit][kUnitFloats]
   // the rings hold float4s: 16-byte aligned base
   size_t ring_off =
@@ -111,10 +139,8 @@ __device__ __forceinline__ void split_stage(SplitBlock &b, float *sms,
   float *s_blk = reinterpret_cast<float *>(s_cring + kSplitWarps * kCandRing);
   const int nblk = (S + kSrcBlock - 1) / kSrcBlock;
   float *s_dh = s_blk + 2 * nblk;  // delta_hi of every source, contiguous
-  for (int i = threadIdx.x; i < PM * 9; i += blockDim.x) {
-    s_axh[i] = axh[i];
-    s_axl[i] = axl[i];
-  }
+  for (int i = threadIdx.x; i < PM * 9; i += blockDim.x)
+    s_ax2[i] = make_float2(axh[i], axl[i]);
   for (int i = threadIdx.x; i < S * SRC32_STRIDE; i += blockDim.x)
     s_src[i] = src32[i];
   __syncthreads();
@@ -138,8 +164,7 @@ __device__ __forceinline__ void split_stage(SplitBlock &b, float *sms,
   for (int k = threadIdx.x; k + 1 < S; k += blockDim.x)
     unsorted |= s_dh[k] > s_dh[k + 1];
   const bool dh_sorted = __syncthreads_or(unsorted) == 0;
-  b.axh = s_axh;
-  b.axl = s_axl;
+  b.ax2 = s_ax2;
   b.src = s_src;
   b.blk = s_blk;
   b.dh = s_dh;
@@ -271,7 +296,8 @@ __device__ __forceinline__ double split_sum(const SpotArgs &a,
                                             unsigned long long &evals) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int PM = b.PM, S = b.S, nblk = b.nblk, sstep = b.sstep;
-  const float *s_axh = b.axh, *s_axl = b.axl, *s_src = b.src, *s_blk = b.blk,
+  const float2 *s_ax2 = b.ax2;
+  const float *s_src = b.src, *s_blk = b.blk,
               *s_dh = b.dh;
   SplitRing &q = b.rings[warp];
   float *st = b.state_base + warp * 32 * kStateStride;
@@ -297,13 +323,15 @@ __device__ __forceinline__ double split_sum(const SpotArgs &a,
     bool valid = it < items;
     int u = valid ? it / PM : 0, pm = valid ? it - u * PM : 0;
     const float *ud = unit + u * kUnitFloats;
-    float vh[3] = {ud[0], ud[1], ud[2]}, vl[3] = {ud[3], ud[4], ud[5]};
-    float scal = ud[6];
+    // vh[3], vl[3], scal as four float2 loads (unit rows are 8-byte aligned)
+    const float2 *u2 = reinterpret_cast<const float2 *>(ud);
+    const float2 p0 = u2[0], p1 = u2[1], p2 = u2[2], p3 = u2[3];
+    float vh[3] = {p0.x, p0.y, p1.x}, vl[3] = {p1.y, p2.x, p2.y};
+    float scal = p3.x;
     float Gh[3], Gl[3], rq[3], rl[3], n0[3];
 #pragma unroll
     for (int x = 0; x < 3; ++x) {
-      ff_dot3(s_axh + pm * 9 + 3 * x, s_axl + pm * 9 + 3 * x, vh, vl,
-              Gh[x], Gl[x]);
+      ff_dot3_pairs(s_ax2 + pm * 9 + 3 * x, vh, vl, Gh[x], Gl[x]);
       float qh, qe;
       two_prod(Gh[x], u0h, qh, qe);
       float ql = fmaf(Gh[x], u0l, fmaf(Gl[x], u0h, qe));
@@ -418,8 +446,10 @@ __device__ __forceinline__ double split_sum(const SpotArgs &a,
         unsigned m = __ballot_sync(0xffffffffu, hit);
         if (m == 0u) return;
         if (hit) {
-          const float *src = s_src + k * SRC32_STRIDE;
-          const float dl = src[SRC32_DL];
+          // (delta_lo, w) of source k in one load
+          const float2 dlw = *reinterpret_cast<const float2 *>(
+              s_src + k * SRC32_STRIDE + SRC32_DL);
+          const float dl = dlw.x;
           int e = (tail + __popc(m & lt_mask)) & (kRing - 1);
           const float2 n01 = o[6], n2s = o[7];
           const float n0o[3] = {n01.x, n01.y, n2s.x};
@@ -433,7 +463,7 @@ __device__ __forceinline__ double split_sum(const SpotArgs &a,
             f[x] = sx + c;
             nn[x] = __float2int_rn(n0o[x] + nf[x]) - a.hmin[x];
           }
-          q.fw[e] = make_float4(f[0], f[1], f[2], src[SRC32_W] * n2s.y);
+          q.fw[e] = make_float4(f[0], f[1], f[2], dlw.y * n2s.y);
           q.n[e] = make_int4(nn[0], nn[1], nn[2], 0);
         }
         tail += __popc(m);
