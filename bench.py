@@ -385,9 +385,22 @@ def run_f64(args, shot, local, stream, torch, nbgb, W):
     stream.synchronize()
     t64 = ev0.elapsed_time(ev1) / 1e3
     sim64.close()
+    from paper_2205_07976_gb300 import flops
+    # roofline against the FP64 FMA rate measured on this device (the
+    # kernel issues scalar FP64 FMAs; there is no FP64 figure in the
+    # measured-peaks file)
+    peak = nbgb.fp64_peak_tflops(local)
+    achieved = flops.f64_flops(shot, len(rows)) / t64 / 1e12
     return {"value": len(rows) * shot.steps_per_pixel / t64, "unit": UNIT,
             "sample": f"every {args.f64_rows_every}th row "
-                      f"({len(rows)} pixels)", "ms": t64 * 1e3}
+                      f"({len(rows)} pixels)", "ms": t64 * 1e3,
+            "roofline": {"bound": "fp64", "achieved": achieved,
+                         "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak if peak > 0 else None,
+                         "kernel": "spots_f64_kernel",
+                         "peak_source": "measured: independent FP64 FMA "
+                                        "chains on every SM "
+                                        "(nb_fp64_peak_tflops)"}}
 
 
 def run_grad(args, local, stream, torch, nbgb, W):

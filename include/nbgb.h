@@ -393,6 +393,18 @@ int nb_add_spots_noalloc(const nb_panel *panel, int oversample, int n_layers,
 /* Wait for the handle's queued work. */
 int nb_synchronize(nb_sim *sim);
 
+/* Measured FP64 FMA throughput of `device`, in TFLOP/s (an FMA counts as
+ * two flops), written to *tflops.  Not part of the method: the ceiling
+ * against which the NB_F64 kernels, which issue scalar FP64 FMAs, are
+ * measured.  A kernel of independent FMA chains in 4 blocks of 256
+ * threads per SM runs once to warm up and three times timed with CUDA
+ * events on a private stream; the best time counts (about 10 ms per launch
+ * on a GB300).  Blocks the caller until done and restores the calling
+ * thread's current device.  Errors: NB_EINVAL for a NULL tflops or a
+ * device outside [0, device count); NB_ENOMEM if its small result buffer
+ * cannot be allocated; NB_ECUDA if a CUDA call fails (*tflops is then 0). */
+int nb_fp64_peak_tflops(int device, double *tflops);
+
 /* Free the handle and everything it owns; NULL is a no-op. */
 int nb_free(nb_sim *sim);
 

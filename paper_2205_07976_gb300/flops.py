@@ -48,6 +48,14 @@ def algorithmic_flops(shot, evaluated_terms: int, pixels: int = None) -> float:
                  + ITEM * items + UNIT * units)
 
 
+def f64_flops(shot, pixels: int) -> float:
+    """Flops of the plain FP64 form on `pixels` pixels of `shot`: the same
+    count in FP64 arithmetic, with every step a term (NB_F64 skips none)."""
+    steps = (pixels * shot.oversample ** 2 * shot.n_layers * shot.n_mosaic
+             * shot.n_phi * shot.n_src)
+    return algorithmic_flops(shot, steps, pixels)
+
+
 # amorphous background, per (subpixel, layer, source) step: stol = sin(theta)
 # u_k (1), linear interpolation (sub + FMA, 3), F^2 w (2), accumulate (1);
 # per (subpixel, layer, direction): |d - i|, polarization (25); per

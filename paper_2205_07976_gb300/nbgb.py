@@ -81,6 +81,7 @@ SIGNATURES = {
         ctypes.c_double, _vp, _vp, ctypes.c_int, _dp, ctypes.c_double,
         ctypes.c_double, _dp, _vp, _vp]),
     "nb_synchronize": (ctypes.c_int, [_vp]),
+    "nb_fp64_peak_tflops": (ctypes.c_int, [ctypes.c_int, _dp]),
     "nb_server_create": (ctypes.c_int, [
         ctypes.POINTER(_vp), ctypes.c_int, _vp, ctypes.c_int,
         ctypes.c_longlong, ctypes.c_longlong, ctypes.POINTER(NbPanel),
@@ -333,6 +334,13 @@ def simulate(shot, precision: str = "mixed", pixels=None,
         return img
     finally:
         sim.close()
+
+
+def fp64_peak_tflops(device: int = 0) -> float:
+    """Measured FP64 FMA throughput of `device` in TFLOP/s."""
+    out = ctypes.c_double(0.0)
+    _check(load().nb_fp64_peak_tflops(int(device), ctypes.byref(out)))
+    return out.value
 
 
 NB_REQ_UNKNOWN, NB_REQ_QUEUED, NB_REQ_RUNNING, NB_REQ_DONE = -1, 0, 1, 2

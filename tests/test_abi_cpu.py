@@ -48,6 +48,7 @@ def test_host_only_entry_points():
     assert lib.nb_add_background(None) == nbgb.NB_EINVAL
     assert lib.nb_set_background(None, None, None, 2, 1.0) == nbgb.NB_EINVAL
     assert lib.nb_adjoint(None, None, None, None) == nbgb.NB_EINVAL
+    assert lib.nb_fp64_peak_tflops(0, None) == nbgb.NB_EINVAL
 
 
 @pytest.mark.skipif(gpu_available(), reason="checks the no-GPU error path")
@@ -59,3 +60,8 @@ def test_create_without_gpu_fails_cleanly():
     assert not h.value
     with pytest.raises(nbgb.NbError):
         nbgb.Sim("mixed")
+    # the FP64 peak probe reports an error and no rate
+    x = ctypes.c_double(1.0)
+    rc = lib.nb_fp64_peak_tflops(0, ctypes.byref(x))
+    assert rc in (nbgb.NB_ECUDA, nbgb.NB_EINVAL)
+    assert x.value == 0.0

@@ -271,3 +271,15 @@ def test_large_shot_full_size_sampled_rows():
     for variant in ("auto", "thread"):
         got = run(s, "mixed", variant=variant)[pix]
         check_mixed(got, ref)
+
+
+def test_fp64_peak_probe_is_plausible():
+    """The FP64 roofline's denominator: GB300's nominal FP64 rate is
+    1.25 TFLOP/s (152 SMs at 2.07 GHz); the probe must land near it, and a
+    second call must agree (it times the best of three launches)."""
+    p1 = nbgb.fp64_peak_tflops(0)
+    p2 = nbgb.fp64_peak_tflops(0)
+    assert 0.3 < p1 < 3.0, p1
+    assert abs(p1 - p2) <= 0.2 * max(p1, p2), (p1, p2)
+    with pytest.raises(nbgb.NbError):
+        nbgb.fp64_peak_tflops(10_000)
