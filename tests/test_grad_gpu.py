@@ -101,6 +101,33 @@ def test_adjoint_matches_oracle_gradient(case):
     np.testing.assert_allclose(gF[big], gF0[big], rtol=1e-4)
 
 
+@pytest.mark.parametrize("interp", [W.INTERP_NEAREST, W.INTERP_TRICUBIC],
+                         ids=["nearest", "tricubic"])
+def test_adjoint_full_size_matches_oracle(interp):
+    """The differentiation workload at its full size, as the benchmark runs
+    it: 64 panels of 185x194 pixels, 8 sources, 10 domains, N=15 Gaussian,
+    table on [-40,40]^3 (2.3e6 pixels, 1.8e8 pixel-steps).  The target is a
+    Poisson draw of the oracle's image at the true parameters; loss, the 10
+    scalars and every structure-factor gradient against the oracle's."""
+    shot = W.multipanel_shot(8)
+    shot.interp = interp
+    U = W.random_orientation(np.random.default_rng(3))
+    truth = oracle.image(with_theta(shot, U, THETA_TRUE))
+    y = np.random.default_rng(7).poisson(truth + BKG).astype(np.float64)
+    L0, g0, gF0, _ = oracle.loss_grad(with_theta(shot, U, THETA), U,
+                                      THETA["cell"], THETA["rot"], y, BKG)
+    L, g, gF, _ = gpu_grad(shot, U, y, THETA)
+    assert abs(L - L0) <= 1e-6 * abs(L0)
+    gmax = np.abs(g0).max()
+    for r in range(10):
+        assert abs(g[r] - g0[r]) <= 1e-4 * abs(g0[r]) + 1e-6 * gmax, (
+            r, g[r], g0[r])
+    assert np.abs(gF - gF0).max() <= 1e-4 * np.abs(gF0).max()
+    big = np.abs(gF0) > 1e-2 * np.abs(gF0).max()
+    assert big.sum() >= 10
+    np.testing.assert_allclose(gF[big], gF0[big], rtol=1e-4)
+
+
 def test_adjoint_matches_fd_of_f64_forward(case):
     shot, U, y, (L0, g0, _, _) = case
     _, g, _, _ = gpu_grad(shot, U, y, THETA)

@@ -99,6 +99,34 @@ def test_server_matches_oracle(base):
     assert checked >= 3
 
 
+def test_full_size_request_in_a_mix_matches_oracle_on_sampled_rows(base):
+    """A request at the workload's largest sizes (a 2591x1351 ROI, 99
+    sources, 49 domains: 1.7e10 pixel-steps, one warp per pixel) served
+    between small ones with the benchmark's step budget of 2e9
+    pixel-steps; the oracle computes six of its rows."""
+    reqs = W.serving_requests(48, seed=40, min_pix=3.5e6, max_pix=4e6)
+    big = max(reqs, key=lambda r: r.pixel_steps)
+    assert big.pixel_steps > 1.5e10
+    assert len(big.lambdas) >= 95 and big.umats.shape[0] >= 45
+    others = small_requests(6, 41)
+    srv = nbgb.Server(base, step_budget=2_000_000_000)
+    ids = [submit(srv, r) for r in others[:3]]
+    bid = submit(srv, big)
+    ids += [submit(srv, r) for r in others[3:]]
+    done = srv.run_all()
+    assert sorted(done) == sorted(ids + [bid])
+    got = srv.result(bid)
+    srv.close()
+    f0, s0, nf, ns = big.roi
+    rows = [0, ns // 7, ns // 3, ns // 2, 2 * ns // 3, ns - 1]
+    pix = np.concatenate([np.arange(r * nf, (r + 1) * nf) for r in rows])
+    ref = oracle.image(W.request_shot(base, big), pix)
+    assert (ref > 1e-3 * ref.max()).sum() >= 40
+    rel, n = masked_rel_err(got[pix], ref, 1e-3)
+    assert rel <= 1e-5, (rel, n)
+    assert abs_err_frac(got[pix], ref) <= 1e-5
+
+
 def test_admission_under_memory_pressure(base):
     reqs = small_requests(8, 14)
     alone = run_alone(base, reqs)
