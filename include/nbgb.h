@@ -96,8 +96,8 @@ int nb_sim_create(nb_sim **out, int device, int precision, void *cuda_stream);
  *   interp    NB_INTERP_NEAREST (F at the nearest node, default_F outside
  *             the table) or NB_INTERP_TRICUBIC (4-point Lagrange per axis;
  *             nearest where the 4x4x4 stencil leaves the table).
- * Errors: NB_EINVAL for n_mosaic < 1, n_phi < 1, non-positive or (sinc)
- * non-integral N, a zero spindle with n_phi > 1, empty table, NULL axes or
+ * Errors: NB_EINVAL for n_mosaic < 1, n_phi < 1, n_mosaic x n_phi >
+ * 2048, non-positive or (sinc) non-integral N, a zero spindle with n_phi > 1, empty table, NULL axes or
  * umats, or F NULL before any table was set. */
 int nb_set_crystal(nb_sim *sim, const double axes[9], const double *umats,
                    int n_mosaic, int n_phi, double phi0_deg,
@@ -120,7 +120,8 @@ int nb_set_scale(nb_sim *sim, double scale);
  *             K != 0).
  * The library keeps the sources ordered by ascending 1/lambda (the sum does
  * not depend on their order; results agree to rounding). 
- * Errors: NB_EINVAL for n_src < 1, NULL arrays, non-unit directions,
+ * Errors: NB_EINVAL for n_src outside [1, 1024], NULL arrays, non-unit
+ * directions,
  * lambda <= 0, K outside [0, 1], or e_vec parallel to a direction. */
 int nb_set_beam(nb_sim *sim, const double *dirs, const double *lambda_A,
                 const double *weights, int n_src, double fluence,
@@ -141,8 +142,13 @@ long long nb_num_pixels(const nb_sim *sim);
 
 /* Queue the Bragg-spot sum of every pixel and add it to the image (the
  * fused addArray: image[p] += (double) I_p).  Asynchronous on the handle's
- * stream.  Errors: NB_ESTATE before crystal, beam and detector are set;
- * NB_ECUDA if the launch fails. */
+ * stream.  The kernels stage the phi x mosaic and source tables in 200 KB
+ * of shared memory: (18 n_phi n_mosaic + 12 n_src) x 4 bytes for NB_MIXED
+ * and NB_F32, which always fits within the limits of nb_set_crystal and
+ * nb_set_beam, and (9 n_phi n_mosaic + 11 n_src) x 8 bytes for NB_F64
+ * (with 1024 sources, at most 1592 orientations).  Errors: NB_ESTATE
+ * before crystal, beam and detector are set; NB_EINVAL if the tables
+ * exceed that limit; NB_ECUDA if the launch fails. */
 int nb_add_spots(nb_sim *sim);
 
 /* As nb_add_spots for the listed global pixel indices only (a host array

@@ -258,6 +258,39 @@ def test_bad_arguments_are_rejected():
     sim.close()
 
 
+@pytest.mark.parametrize("precision,n_pm", [("mixed", 2048), ("f64", 1592)])
+def test_largest_tables_that_fit_and_one_more(precision, n_pm):
+    """Maximum sizes: 1024 sources (the nb_set_beam limit) with n_pm mosaic
+    orientations, the most whose tables fit the kernels' 200 KB of shared
+    memory: (18 PM + 12 S) x 4 bytes for the FP32 forms (so the
+    nb_set_crystal limit of 2048), (9 PM + 11 S) x 8 bytes for FP64.  That
+    shot matches the oracle on one 16x8 tile; one orientation or one
+    source more is rejected with NB_EINVAL."""
+    s = W.shrink(W.single_shot_small(), 16, 8, 150, 140)
+    s.dirs, s.lambdas, s.weights = W.gaussian_spectrum(1024, 9.5, 0.005)
+    rng = np.random.default_rng(5)
+    s.umats = W.mosaic_umats(rng, n_pm, 0.05)
+    assert s.n_mosaic * s.n_phi == n_pm and s.n_src == 1024
+    ref = oracle.image(s)
+    got = run(s, precision)
+    (check_f64 if precision == "f64" else check_mixed)(got, ref)
+    t = s.copy()
+    t.umats = W.mosaic_umats(rng, n_pm + 1, 0.05)
+    sim = nbgb.Sim(precision)
+    with pytest.raises(nbgb.NbError) as e:
+        sim.set_shot(t)  # n_pm + 1 > 2048 fails here, in nb_set_crystal
+        sim.add_spots()  # FP64 tables over 200 KB fail here
+    assert e.value.code == nbgb.NB_EINVAL
+    sim.close()
+    t = s.copy()
+    t.dirs, t.lambdas, t.weights = W.gaussian_spectrum(1025, 9.5, 0.005)
+    sim = nbgb.Sim(precision)
+    with pytest.raises(nbgb.NbError) as e:
+        sim.set_shot(t)
+    assert e.value.code == nbgb.NB_EINVAL
+    sim.close()
+
+
 # ------------------------------------- full-size large shot, sampled rows
 
 
