@@ -47,7 +47,7 @@ __device__ __forceinline__ void lagrange4_deriv(float x, float w[4]) {
 }
 
 template <int HASF, int INTERP>
-__global__ void __launch_bounds__(kTileThreads, INTERP ? 2 : 4)
+__global__ void __launch_bounds__(kTileThreads, INTERP ? 3 : 4)
     spots_adjoint_kernel(AdjointArgs g) {
   const SpotArgs &a = g.a;
   extern __shared__ float smf[];
