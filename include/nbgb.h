@@ -235,11 +235,13 @@ int nb_poisson_loss(nb_sim *sim, const double *y, double bkg, double *dLdI,
  *
  * nb_add_background queues one launch that adds the background of every
  * pixel into the handle's image (after, before or without the spots; the
- * crystal is not needed).  NB_F64 handles evaluate it in FP64, NB_MIXED
- * and NB_F32 handles in FP32 per source with a compensated sum (geometry in
- * FP64).  Errors: NB_ESTATE before nb_set_beam, nb_set_detector and
- * nb_set_background; NB_EINVAL if the knot and source tables exceed the
- * kernel's 200 KB of shared memory. */
+ * crystal is not needed).  NB_F64 handles evaluate it in FP64.  NB_MIXED
+ * and NB_F32 handles take the pixel's corner in FP64 and the rest in FP32:
+ * each block of up to 32 sources is summed in four plain FP32 chains and
+ * the blocks are added with compensation (within about 12 ulp of the
+ * exact sum for any number of sources).  Errors: NB_ESTATE before
+ * nb_set_beam, nb_set_detector and nb_set_background; NB_EINVAL if the
+ * knot and source tables exceed the kernel's 200 KB of shared memory. */
 int nb_set_background(nb_sim *sim, const double *stol, const double *F,
                       int n_knots, double n_molecules);
 int nb_add_background(nb_sim *sim);
@@ -268,8 +270,11 @@ enum { NB_REQ_UNKNOWN = -1, NB_REQ_QUEUED = 0, NB_REQ_RUNNING = 1,
  *   Na, Nb, Nc   Gaussian lattice shape (the only shape served).
  *   dir, fluence, kahn_K, e_vec   beam direction shared by all sources,
  *                fluence, polarization.
- * Every step is one replay of a CUDA graph: work-list upload, counter
- * reset and a persistent kernel whose blocks pull 128-pixel work items.
+ * Every step is one replay of one of two CUDA graphs, used in turn: the
+ * work-list upload from that graph's pinned buffer, a counter reset and
+ * two persistent kernels whose blocks pull work items, 128 pixels for the
+ * thread-per-pixel kernel and 64 pixels for the warp-per-pixel kernel
+ * (which takes requests with tricubic lookup and >= 8 mosaic domains).
  * Errors: NB_EINVAL (bad sizes), NB_ENOMEM, NB_ECUDA. */
 int nb_server_create(nb_server **out, int device, void *cuda_stream,
                      int max_slots, long long pool_bytes,
