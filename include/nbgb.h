@@ -97,8 +97,9 @@ int nb_sim_create(nb_sim **out, int device, int precision, void *cuda_stream);
  *             the table) or NB_INTERP_TRICUBIC (4-point Lagrange per axis;
  *             nearest where the 4x4x4 stencil leaves the table).
  * Errors: NB_EINVAL for n_mosaic < 1, n_phi < 1, n_mosaic x n_phi >
- * 2048, non-positive or (sinc) non-integral N, a zero spindle with n_phi > 1, empty table, NULL axes or
- * umats, or F NULL before any table was set. */
+ * 2048, non-positive or (sinc) non-integral N, a zero spindle with
+ * n_phi > 1, empty table, NULL axes or umats, or F NULL before any table
+ * was set. */
 int nb_set_crystal(nb_sim *sim, const double axes[9], const double *umats,
                    int n_mosaic, int n_phi, double phi0_deg,
                    double phistep_deg, const double spindle[3], double Na,
@@ -119,10 +120,10 @@ int nb_set_scale(nb_sim *sim, double scale);
  *             polarized part (not parallel to any source direction when
  *             K != 0).
  * The library keeps the sources ordered by ascending 1/lambda (the sum does
- * not depend on their order; results agree to rounding). 
+ * not depend on their order; results agree to rounding).
  * Errors: NB_EINVAL for n_src outside [1, 1024], NULL arrays, non-unit
- * directions,
- * lambda <= 0, K outside [0, 1], or e_vec parallel to a direction. */
+ * directions, lambda <= 0, K outside [0, 1], or e_vec parallel to a
+ * direction. */
 int nb_set_beam(nb_sim *sim, const double *dirs, const double *lambda_A,
                 const double *weights, int n_src, double fluence,
                 double kahn_K, const double e_vec[3]);
