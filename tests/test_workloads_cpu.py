@@ -48,3 +48,12 @@ def test_flop_counts_scale_with_the_loop_nest():
     units = s.npix * s.oversample ** 2 * s.n_layers
     assert bg2 - bg1 == units * flops.BG_STEP * s.n_src
     assert abs(flops.fp32_peak_tflops(152, 2070.0) - 80.54784) < 1e-9
+    # the FP64 form evaluates every step as a term: per step hkl (9) +
+    # Gaussian (8) + term (exp 3, tricubic 198, accumulate 4) = 222, plus
+    # the per-item and per-unit work
+    per_px = flops.f64_flops(s, 1)
+    items = s.oversample ** 2 * s.n_layers * s.n_mosaic * s.n_phi
+    units = s.oversample ** 2 * s.n_layers
+    assert per_px == 222 * s.steps_per_pixel + flops.ITEM * items + \
+        flops.UNIT * units
+    assert flops.f64_flops(s, 10) == 10 * per_px
