@@ -11,22 +11,24 @@ namespace nbgb {
 
 constexpr int kSplitWarps = 4;
 constexpr int kSplitThreads = kSplitWarps * 32;
-constexpr int kRing = 64;
 constexpr int kMaxUnits = 32;
 constexpr int kUnitFloats = 10;  // vh[3], vl[3], scal, df[3]
-// per-lane item state, 9 float2: (G_hi, r_q) and (G_lo, r_lo) per axis,
-// (n0_h, n0_k), (n0_l, scal), one unused.  Pairs halve the shared loads;
-// the odd pair stride keeps distinct owners on distinct bank pairs unless
-// they are 16 lanes apart.
-constexpr int kStateStride = 18;
-constexpr int kCandRing = 64;     // per-warp ring of (lane, source block)
-constexpr int kSrcBlock = 8;      // sources per pruning block
+constexpr int kSrcBlock = 8;     // sources per pruning block
+// Per-warp ring of source intervals.  An entry is one (item, source range)
+// pair that can hold surviving terms, with a copy of its item's state, so
+// that entries outlive the item batch that pushed them.  Pending entries
+// never exceed 31 (each holds an unconsumed source) plus the 32 a push adds.
+constexpr int kEntries = 64;
 
-struct SplitRing {
-  float4 fw[kRing];  // f_h, f_k, f_l, weight: one 16-byte store / load
-  int4 n[kRing];     // table-relative nearest index (h, k, l), unused
+struct SplitEntry {
+  float4 a;  // G_hi h, r_q h, G_hi k, r_q k
+  float4 b;  // G_hi l, r_q l, G_lo h, r_lo h
+  float4 c;  // G_lo k, r_lo k, G_lo l, r_lo l
+  float4 d;  // n0 h, n0 k, n0 l, omega cap pol of the unit
+  int4 m;    // first source, count, position of the first source in the
+             // pixel's sequence of (entry, source) pairs, pm | unit << 16
 };
-static_assert(sizeof(SplitRing) % 16 == 0, "rings stay 16-byte aligned");
+static_assert(sizeof(SplitEntry) % 16 == 0, "entries stay 16-byte aligned");
 static_assert(SRC32_DL % 2 == 0 && SRC32_W == SRC32_DL + 1 &&
                   SRC32_STRIDE % 2 == 0 && kUnitFloats % 2 == 0,
               "float2 reads of (delta_lo, w) and of the unit rows");
@@ -55,50 +57,109 @@ __device__ __forceinline__ void ff_dot3_pairs(const float2 *A,
   fast_two_sum(s2, lo, gh, gl);
 }
 
+// Per-warp cache of cell polynomials in shared memory.  The terms of one
+// evaluation pass almost always lie around a single lattice point n, in the
+// cells n - {0,1}^3, and those 8 cells have distinct parities (the low bit
+// of each corner index).  So the cache has one slot per parity, and chunk k
+// (float4) of slot p sits at float4 k * kCellSlots + p: the same chunk of
+// every slot lies in one 128-byte row of shared-memory banks, and one
+// 16-byte load of chunk k by all lanes is a single shared-memory wavefront
+// whatever mix of slots the lanes read (lanes on one slot get a
+// broadcast).  A global 16-byte load delivers 128 bytes per wavefront
+// whether the lanes' addresses coincide or not, so reading the 256
+// coefficient bytes of each term from global memory costs 2 wavefronts per
+// term; from the cache it costs 1/2.
+constexpr int kCellSlots = 8;
+constexpr int kCellChunks = 16;  // float4 per cell polynomial
+
+// A cell's tricubic polynomial at x (cell coordinates in [0, 1)), nested
+// Horner in l, k, h (63 FMAs); chunk k of the coefficients at cp[k * stride],
+// read from shared memory (SHARED) or through the read-only path.
+template <bool SHARED>
+__device__ __forceinline__ float cell_horner(const float4 *cp, int stride,
+                                             const float x[3]) {
+  float qa[4];
+#pragma unroll
+  for (int ia = 0; ia < 4; ++ia) {
+    float pb[4];
+#pragma unroll
+    for (int ib = 0; ib < 4; ++ib) {
+      const float4 c4 = SHARED ? cp[(ia * 4 + ib) * stride]
+                               : __ldg(cp + (ia * 4 + ib) * stride);
+      pb[ib] = fmaf(fmaf(fmaf(c4.w, x[2], c4.z), x[2], c4.y), x[2], c4.x);
+    }
+    qa[ia] = fmaf(fmaf(fmaf(pb[3], x[1], pb[2]), x[1], pb[1]), x[1], pb[0]);
+  }
+  return fmaf(fmaf(fmaf(qa[3], x[0], qa[2]), x[0], qa[1]), x[0], qa[0]);
+}
+
+// The term F_cell^2 F_latt^2 w of a lane whose step survived the cut (`hit`),
+// given its fractional offset fr and table-relative nearest index n.  Called
+// by all 32 lanes of the warp: missing cells are loaded into the cache by
+// the whole warp (one coalesced 256-byte read per cell).  A lane whose
+// parity slot ends up holding another cell (two lattice points in one pass)
+// reads its cell from global memory instead.
 template <int INTERP>
-__device__ __forceinline__ void eval_term(const SpotArgs &a,
-                                          const SplitRing &q, int e,
-                                          Kahan &acc) {
-  const float4 fw = q.fw[e];
-  const int4 ni = q.n[e];
-  float fr[3] = {fw.x, fw.y, fw.z};
-  int n[3] = {ni.x, ni.y, ni.z};
+__device__ __forceinline__ float term_value(const SpotArgs &a, bool hit,
+                                            const float fr[3], const int n[3],
+                                            float w, float4 *cache,
+                                            int *tags) {
   float rad2 = a.N[0] * a.N[0] * fr[0] * fr[0];
   rad2 = fmaf(a.N[1] * a.N[1], fr[1] * fr[1], rad2);
   rad2 = fmaf(a.N[2] * a.N[2], fr[2] * fr[2], rad2);
   // fast exp: a few ulp for the significant terms (|argument| < ~20)
-  float fl2 = a.N6 * __expf(-2.f * rad2 * (1.f / 0.63f));
-  float fc;
+  const float fl2 = a.N6 * __expf(-2.f * rad2 * (1.f / 0.63f));
   int fl[3];
   float x[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    int neg = fr[c] < 0.f;
+    const int neg = fr[c] < 0.f;
     fl[c] = n[c] - neg;
     x[c] = neg ? 1.f + fr[c] : fr[c];
   }
-  if (INTERP == 1 && a.C4 && fl[0] >= 1 && fl[0] + 2 < a.hn[0] &&
-      fl[1] >= 1 && fl[1] + 2 < a.hn[1] && fl[2] >= 1 && fl[2] + 2 < a.hn[2]) {
-    // the cell's tricubic polynomial, nested Horner in l, k, h (63 FMAs)
-    const float4 *cp =
-        a.C4 + (((long long)(fl[0] - 1) * (a.hn[1] - 3) + (fl[1] - 1)) *
-                    (a.hn[2] - 3) + (fl[2] - 1)) * 16;
-    float qa[4];
-#pragma unroll
-    for (int ia = 0; ia < 4; ++ia) {
-      float pb[4];
-#pragma unroll
-      for (int ib = 0; ib < 4; ++ib) {
-        float4 c4 = __ldg(cp + ia * 4 + ib);
-        pb[ib] = fmaf(fmaf(fmaf(c4.w, x[2], c4.z), x[2], c4.y), x[2], c4.x);
-      }
-      qa[ia] = fmaf(fmaf(fmaf(pb[3], x[1], pb[2]), x[1], pb[1]), x[1], pb[0]);
+  const bool tri = INTERP == 1 && hit && a.C4 && fl[0] >= 1 &&
+                   fl[0] + 2 < a.hn[0] && fl[1] >= 1 && fl[1] + 2 < a.hn[1] &&
+                   fl[2] >= 1 && fl[2] + 2 < a.hn[2];
+  int ci = 0, par = 0;
+  if (tri) {
+    ci = ((fl[0] - 1) * (a.hn[1] - 3) + (fl[1] - 1)) * (a.hn[2] - 3) +
+         (fl[2] - 1);
+    par = (fl[0] & 1) | ((fl[1] & 1) << 1) | ((fl[2] & 1) << 2);
+  }
+  bool cached = false;
+  if (INTERP == 1) {
+    const int lane = threadIdx.x & 31;
+    unsigned handled = 0u;
+    unsigned miss = __ballot_sync(0xffffffffu, tri && tags[par] != ci);
+    while (miss) {
+      // load the cell of the first missing lane into its parity slot; each
+      // slot is loaded at most once per pass
+      const int src = __ffs(miss) - 1;
+      const int sp = __shfl_sync(0xffffffffu, par, src);
+      const int sci = __shfl_sync(0xffffffffu, ci, src);
+      const float2 v = __ldg(
+          reinterpret_cast<const float2 *>(a.C4 + (size_t)sci * kCellChunks) +
+          lane);
+      reinterpret_cast<float2 *>(
+          cache)[((lane >> 1) * kCellSlots + sp) * 2 + (lane & 1)] = v;
+      __syncwarp();
+      if (lane == 0) tags[sp] = sci;
+      __syncwarp();
+      handled |= 1u << sp;
+      miss = __ballot_sync(0xffffffffu,
+                           tri && !((handled >> par) & 1u) && tags[par] != ci);
     }
-    fc = fmaf(fmaf(fmaf(qa[3], x[0], qa[2]), x[0], qa[1]), x[0], qa[0]);
-  } else {
+    cached = tri && tags[par] == ci;
+  }
+  float fc = 0.f;
+  if (cached) {
+    fc = cell_horner<true>(cache + par, kCellSlots, x);
+  } else if (tri) {
+    fc = cell_horner<false>(a.C4 + (size_t)ci * kCellChunks, 1, x);
+  } else if (hit) {
     fc = fcell_f32<INTERP>(a, n, fr);
   }
-  acc.add(fc * fc * fl2 * fw.w);
+  return fc * fc * fl2 * w;
 }
 
 // Per-block view of one shot's staged tables in shared memory and the
@@ -106,14 +167,30 @@ __device__ __forceinline__ void eval_term(const SpotArgs &a,
 struct SplitBlock {
   const float2 *ax2;  // [PM][9] (hi, lo) pairs
   const float *src, *blk, *dh;
-  float *unit_base, *state_base;
-  int *cring_base;
-  SplitRing *rings;
+  float *unit_base;
+  SplitEntry *ent_base;  // [warp][kEntries]
+  float4 *cell_cache;    // [warp][kCellChunks][kCellSlots]
+  int *cell_tags;        // [warp][kCellSlots], -1 = empty
   int PM, S, nblk, sstep;
   float u0h, u0l, cwide, dmin, dmax, dmarg, inv_step;
   float cmarg[3];
   bool iv_ok, even;
 };
+
+// Bytes of dynamic shared memory split_stage lays out for PM orientations
+// and S sources.
+__host__ __device__ inline size_t split_smem_layout(int PM, int S) {
+  const int nblk = (S + kSrcBlock - 1) / kSrcBlock;
+  size_t off = (size_t)(2 * PM * 9 + S * SRC32_STRIDE +
+                        kSplitWarps * kMaxUnits * kUnitFloats) *
+               sizeof(float);
+  off = (off + 15) & ~(size_t)15;
+  off += (size_t)kSplitWarps * kEntries * sizeof(SplitEntry);
+  off += (size_t)kSplitWarps * kCellChunks * kCellSlots * sizeof(float4);
+  off += (size_t)(2 * nblk + S) * sizeof(float);
+  off += (size_t)kSplitWarps * kCellSlots * sizeof(int);
+  return off;
+}
 
 // Stages a shot's tables (double-float axes [PM][9], interleaved into
 // (hi, lo) pairs, and source rows [S][12]) into the dynamic shared memory
@@ -127,18 +204,20 @@ __device__ __forceinline__ void split_stage(SplitBlock &b, float *sms,
   float2 *s_ax2 = reinterpret_cast<float2 *>(sms);
   float *s_src = sms + 2 * PM * 9;
   float *s_unit = s_src + S * SRC32_STRIDE;  // [warp][unit][kUnitFloats]
-  // the rings hold float4s: 16-byte aligned base
-  size_t ring_off =
+  // entries and cache hold float4s: 16-byte aligned base
+  const size_t ent_off =
       ((size_t)(s_unit + kSplitWarps * kMaxUnits * kUnitFloats - sms) *
            sizeof(float) + 15) & ~(size_t)15;
-  SplitRing *rings = reinterpret_cast<SplitRing *>(
-      reinterpret_cast<char *>(sms) + ring_off);
-  float *s_state = reinterpret_cast<float *>(rings + kSplitWarps);
-  int *s_cring =
-      reinterpret_cast<int *>(s_state + kSplitWarps * 32 * kStateStride);
-  float *s_blk = reinterpret_cast<float *>(s_cring + kSplitWarps * kCandRing);
+  SplitEntry *s_ent = reinterpret_cast<SplitEntry *>(
+      reinterpret_cast<char *>(sms) + ent_off);
+  float4 *s_cache = reinterpret_cast<float4 *>(s_ent + kSplitWarps * kEntries);
+  float *s_blk =
+      reinterpret_cast<float *>(s_cache + kSplitWarps * kCellChunks * kCellSlots);
   const int nblk = (S + kSrcBlock - 1) / kSrcBlock;
   float *s_dh = s_blk + 2 * nblk;  // delta_hi of every source, contiguous
+  int *s_tags = reinterpret_cast<int *>(s_dh + S);
+  for (int i = threadIdx.x; i < kSplitWarps * kCellSlots; i += blockDim.x)
+    s_tags[i] = -1;
   for (int i = threadIdx.x; i < PM * 9; i += blockDim.x)
     s_ax2[i] = make_float2(axh[i], axl[i]);
   for (int i = threadIdx.x; i < S * SRC32_STRIDE; i += blockDim.x)
@@ -169,9 +248,9 @@ __device__ __forceinline__ void split_stage(SplitBlock &b, float *sms,
   b.blk = s_blk;
   b.dh = s_dh;
   b.unit_base = s_unit;
-  b.state_base = s_state;
-  b.cring_base = s_cring;
-  b.rings = rings;
+  b.ent_base = s_ent;
+  b.cell_cache = s_cache;
+  b.cell_tags = s_tags;
   b.PM = PM;
   b.S = S;
   b.nblk = nblk;
@@ -285,6 +364,129 @@ __device__ __forceinline__ void split_unit(const SpotArgs &a,
   ud[6] = scal;
 }
 
+// Per-warp queue of (entry, source) pairs: entries [e0, en) of the ring
+// are pending, pairs [ch, ct) of the pixel's sequence are not yet summed.
+struct PairQueue {
+  int e0 = 0, en = 0, ch = 0, ct = 0;
+};
+
+// Appends one entry per lane with len > 0 (sources k1 .. k1 + len - 1 of the
+// item whose state the lane holds), in lane order.  Called by all lanes.
+__device__ __forceinline__ void push_entries(
+    SplitEntry *ring, PairQueue &pq, int len, int k1, int aux,
+    const float Gh[3], const float rq[3], const float Gl[3], const float rl[3],
+    const float n0[3], float scal) {
+  const int lane = threadIdx.x & 31;
+  int inc = len;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  const int tot = __shfl_sync(0xffffffffu, inc, 31);
+  if (tot == 0) return;
+  const unsigned hm = __ballot_sync(0xffffffffu, len > 0);
+  if (len > 0) {
+    SplitEntry &E =
+        ring[(pq.en + __popc(hm & ((1u << lane) - 1u))) & (kEntries - 1)];
+    E.a = make_float4(Gh[0], rq[0], Gh[1], rq[1]);
+    E.b = make_float4(Gh[2], rq[2], Gl[0], rl[0]);
+    E.c = make_float4(Gl[1], rl[1], Gl[2], rl[2]);
+    E.d = make_float4(n0[0], n0[1], n0[2], scal);
+    E.m = make_int4(k1, len, pq.ct + inc - len, aux);
+  }
+  pq.en += __popc(hm);
+  pq.ct += tot;
+  __syncwarp();
+}
+
+// Sums the next min(32, ct - ch) pairs of the queue, one per lane: the exact
+// fractional offset of the step, the cut test, and for a surviving step its
+// term (F_cell from the cell cache, F_latt, weight) into the lane's Kahan
+// sum.  Called by all lanes; returns the number of surviving terms.
+template <int INTERP, int HASDIV>
+__device__ __forceinline__ unsigned sum_pairs(
+    const SpotArgs &a, const SplitBlock &b, const SplitEntry *ring,
+    PairQueue &pq, const float *unit, float4 *cache, int *tags, Kahan &acc) {
+  const int lane = threadIdx.x & 31;
+  const int np = min(32, pq.ct - pq.ch);
+  // entries e0 .. e0 + 31 can overlap the window [ch, ch + 32)
+  int4 mm = make_int4(0, 0, 0x7fffffff, 0);
+  if (pq.e0 + lane < pq.en) mm = ring[(pq.e0 + lane) & (kEntries - 1)].m;
+  const bool ov = pq.e0 + lane < pq.en && mm.z < pq.ch + np &&
+                  mm.z + mm.y > pq.ch;
+  // bit j of M: some entry starts at pair ch + j (entry e0 at bit 0)
+  const unsigned M = __reduce_or_sync(
+      0xffffffffu, ov ? 1u << max(mm.z - pq.ch, 0) : 0u);
+  const int j = __popc(M & (0xffffffffu >> (31 - lane))) - 1;
+  const int k1 = __shfl_sync(0xffffffffu, mm.x, j);
+  const int pos = __shfl_sync(0xffffffffu, mm.z, j);
+  const int aux = __shfl_sync(0xffffffffu, mm.w, j);
+  const unsigned done =
+      __ballot_sync(0xffffffffu, ov && mm.z + mm.y <= pq.ch + np);
+  const bool valid = lane < np;
+  const int k = valid ? k1 + (pq.ch + lane - pos) : 0;
+  const SplitEntry &E = ring[(pq.e0 + j) & (kEntries - 1)];
+  const float4 A = E.a, B = E.b, C = E.c, D = E.d;
+  const float Gh[3] = {A.x, A.z, B.x}, rq[3] = {A.y, A.w, B.y};
+  const float Gl[3] = {B.z, C.x, C.z}, rl[3] = {B.w, C.y, C.w};
+  const float n0[3] = {D.x, D.y, D.z};
+  const float *src = b.src + k * SRC32_STRIDE;
+  const float dh = b.dh[k];
+  // (delta_lo, w) of source k in one load
+  const float2 dlw = *reinterpret_cast<const float2 *>(src + SRC32_DL);
+  float fr[3];
+  int n[3];
+#pragma unroll
+  for (int x = 0; x < 3; ++x) {
+    float tq = fmaf(Gh[x], dh, rq[x]);
+    float e0 = 0.f, e1 = 0.f;
+    if (HASDIV) {
+      const size_t e = ((size_t)(aux & 0xffff) * b.S + k) * 3 + x;
+      e0 = __ldg(a.divh + e);
+      e1 = __ldg(a.divl + e);
+      tq -= e0;
+    }
+    float nf = rintf(tq);
+    // G_hi d_hi + (r_q - n) in one rounding (r_q on a 2^-21 grid makes
+    // r_q - n exact) plus the small terms
+    const float sx = fmaf(Gh[x], dh, __fsub_rn(rq[x], nf));
+    const float c = fmaf(Gh[x], dlw.x, fmaf(Gl[x], dh, rl[x]));
+    fr[x] = sx + c;
+    if (HASDIV) {
+      // the divergence term moves h after the rint: re-centre
+      fr[x] -= e0 + e1;
+      const float n2 = rintf(fr[x]);
+      fr[x] -= n2;
+      nf += n2;
+    }
+    n[x] = __float2int_rn(n0[x] + nf) - a.hmin[x];
+  }
+  float rad2 = a.N[0] * a.N[0] * fr[0] * fr[0];
+  rad2 = fmaf(a.N[1] * a.N[1], fr[1] * fr[1], rad2);
+  rad2 = fmaf(a.N[2] * a.N[2], fr[2] * fr[2], rad2);
+  const bool hit = valid && rad2 <= kGaussCut * 0.63f;
+  float w = dlw.y * D.w;
+  if (HASDIV && hit) {
+    const float *df = unit + (aux >> 16) * kUnitFloats + 7;
+    const float *dir = src + SRC32_DIR, *ev = src + SRC32_E,
+                *bv = src + SRC32_B;
+    const float c2 = df[0] * dir[0] + df[1] * dir[1] + df[2] * dir[2];
+    const float xx = df[0] * ev[0] + df[1] * ev[1] + df[2] * ev[2];
+    const float yy = df[0] * bv[0] + df[1] * bv[1] + df[2] * bv[2];
+    w *= 0.5f * (1.f + c2 * c2 - a.kahn * (xx * xx - yy * yy));
+  }
+  const unsigned hm = __ballot_sync(0xffffffffu, hit);
+  if (hm != 0u) {
+    const float t = term_value<INTERP>(a, hit, fr, n, w, cache, tags);
+    if (hit) acc.add(t);
+  }
+  pq.e0 += __popc(done);
+  pq.ch += np;
+  __syncwarp();  // the ring slots read above may be refilled next
+  return __popc(hm);
+}
+
 // The sum, without the prefactor, of the pixel whose U sub-pixel units are
 // already in `unit` (split_unit), computed by the calling warp (all 32
 // lanes); every lane returns the same value.  Adds the number of evaluated
@@ -297,15 +499,11 @@ __device__ __forceinline__ double split_sum(const SpotArgs &a,
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int PM = b.PM, S = b.S, nblk = b.nblk, sstep = b.sstep;
   const float2 *s_ax2 = b.ax2;
-  const float *s_src = b.src, *s_blk = b.blk,
-              *s_dh = b.dh;
-  SplitRing &q = b.rings[warp];
-  float *st = b.state_base + warp * 32 * kStateStride;
-  int *cring = b.cring_base + warp * kCandRing;
-  const unsigned lt_mask = (1u << lane) - 1u;
+  const float *s_blk = b.blk, *s_dh = b.dh;
+  SplitEntry *ring = b.ent_base + warp * kEntries;
+  float4 *cache = b.cell_cache + warp * kCellChunks * kCellSlots;
+  int *tags = b.cell_tags + warp * kCellSlots;
   const int U = a.os * a.os * a.T, items = U * PM;
-  const float cutg = kGaussCut * 0.63f;
-  const float kahn = a.kahn;
   const float N2[3] = {a.N[0] * a.N[0], a.N[1] * a.N[1], a.N[2] * a.N[2]};
   const float cwide = b.cwide;
   const float cmarg[3] = {b.cmarg[0], b.cmarg[1], b.cmarg[2]};
@@ -315,26 +513,34 @@ __device__ __forceinline__ double split_sum(const SpotArgs &a,
   const float inv_step = b.inv_step;
   const float u0h = b.u0h, u0l = b.u0l;
 
-  // ---- 2./3. scan the steps, evaluate surviving terms 32 at a time
   Kahan acc;
-  int head = 0, tail = 0;
+  PairQueue pq;
+  unsigned nterms = 0;
+  auto drain = [&]() {
+    while (pq.ct - pq.ch >= 32)
+      nterms += sum_pairs<INTERP, HASDIV>(a, b, ring, pq, unit, cache, tags,
+                                          acc);
+  };
+  // ---- items: lanes take (unit, phi x mosaic) items 32 at a time, form
+  // G and r, and push their source intervals; the pair queue is summed
+  // 32 pairs at a time as it fills
   for (int base = 0; base < items; base += 32) {
-    int it = base + lane;
-    bool valid = it < items;
-    int u = valid ? it / PM : 0, pm = valid ? it - u * PM : 0;
+    const int it = base + lane;
+    const bool valid = it < items;
+    const int u = valid ? it / PM : 0, pm = valid ? it - u * PM : 0;
     const float *ud = unit + u * kUnitFloats;
     // vh[3], vl[3], scal as four float2 loads (unit rows are 8-byte aligned)
     const float2 *u2 = reinterpret_cast<const float2 *>(ud);
     const float2 p0 = u2[0], p1 = u2[1], p2 = u2[2], p3 = u2[3];
-    float vh[3] = {p0.x, p0.y, p1.x}, vl[3] = {p1.y, p2.x, p2.y};
-    float scal = p3.x;
+    const float vh[3] = {p0.x, p0.y, p1.x}, vl[3] = {p1.y, p2.x, p2.y};
+    const float scal = p3.x;
     float Gh[3], Gl[3], rq[3], rl[3], n0[3];
 #pragma unroll
     for (int x = 0; x < 3; ++x) {
       ff_dot3_pairs(s_ax2 + pm * 9 + 3 * x, vh, vl, Gh[x], Gl[x]);
       float qh, qe;
       two_prod(Gh[x], u0h, qh, qe);
-      float ql = fmaf(Gh[x], u0l, fmaf(Gl[x], u0h, qe));
+      const float ql = fmaf(Gh[x], u0l, fmaf(Gl[x], u0h, qe));
       n0[x] = rintf(qh);
       float rh, rl0;
       two_sum(__fsub_rn(qh, n0[x]), ql, rh, rl0);
@@ -343,264 +549,110 @@ __device__ __forceinline__ double split_sum(const SpotArgs &a,
       rl[x] = rl0 + __fsub_rn(rh, rq[x]);
     }
     if (HASDIV) {
-      for (int k = 0; k < S; ++k) {
-        const float *src = s_src + k * SRC32_STRIDE;
-        const float dh = src[SRC32_DH];
-        // cut test on the cheap offset t - rint(t) (error ~1 ulp of t, which
-        // only moves terms ~1e-38 below the peak across the cut)
-        float tq[3], nf[3], fr[3];
-#pragma unroll
-        for (int x = 0; x < 3; ++x) {
-          tq[x] = fmaf(Gh[x], dh, rq[x]);
-          if (HASDIV && valid) tq[x] -= __ldg(a.divh + ((size_t)pm * S + k) * 3 + x);
-          nf[x] = rintf(tq[x]);
-          fr[x] = tq[x] - nf[x];
-        }
-        float rad2 = N2[0] * fr[0] * fr[0];
-        rad2 = fmaf(N2[1] * fr[1], fr[1], rad2);
-        rad2 = fmaf(N2[2] * fr[2], fr[2], rad2);
-        bool hit = valid && rad2 <= cutg;
-        unsigned m = __ballot_sync(0xffffffffu, hit);
-        if (m == 0u) continue;
-        if (hit) {
-          // the precise offset: G_hi d_hi + (r_q - n) in one rounding (r_q
-          // on a 2^-21 grid makes r_q - n exact) plus the small terms
-          const float dl = src[SRC32_DL];
-#pragma unroll
-          for (int x = 0; x < 3; ++x) {
-            float sx = fmaf(Gh[x], dh, __fsub_rn(rq[x], nf[x]));
-            float c = fmaf(Gh[x], dl, fmaf(Gl[x], dh, rl[x]));
-            fr[x] = sx + c;
-            if (HASDIV) {
-              // the divergence term moves h after the rint: re-centre
-              size_t e = ((size_t)pm * S + k) * 3 + x;
-              fr[x] -= __ldg(a.divh + e) + __ldg(a.divl + e);
-              float n2 = rintf(fr[x]);
-              fr[x] -= n2;
-              nf[x] += n2;
-            }
-          }
-          int e = (tail + __popc(m & lt_mask)) & (kRing - 1);
-          float w = src[SRC32_W] * scal;
-          if (HASDIV) {
-            const float *df = ud + 7, *dir = src + SRC32_DIR,
-                        *ev = src + SRC32_E, *bv = src + SRC32_B;
-            float c2 = df[0] * dir[0] + df[1] * dir[1] + df[2] * dir[2];
-            float x = df[0] * ev[0] + df[1] * ev[1] + df[2] * ev[2];
-            float y = df[0] * bv[0] + df[1] * bv[1] + df[2] * bv[2];
-            w *= 0.5f * (1.f + c2 * c2 - kahn * (x * x - y * y));
-          }
-          q.fw[e] = make_float4(fr[0], fr[1], fr[2], w);
-          q.n[e] = make_int4(__float2int_rn(n0[0] + nf[0]) - a.hmin[0],
-                             __float2int_rn(n0[1] + nf[1]) - a.hmin[1],
-                             __float2int_rn(n0[2] + nf[2]) - a.hmin[2], 0);
-        }
-        tail += __popc(m);
-        if (tail - head >= 32) {
-          __syncwarp();
-          eval_term<INTERP>(a, q, (head + lane) & (kRing - 1), acc);
-          head += 32;
-          __syncwarp();
-        }
-      }
-    } else {
-      // ---- pruned scan: h_x = G_x delta + r_x is linear in delta, so a
-      // block of sources whose delta range [dmin, dmax] keeps some axis
-      // farther than sqrt(cut)/N_x from every integer holds no surviving
-      // term.  Surviving (lane, block) pairs go into a ring; the warp
-      // then runs 4 blocks x 8 sources = 32 steps at a time.
-      float2 *my = reinterpret_cast<float2 *>(st + lane * kStateStride);
+      // sources of different directions: every source of every item
+      push_entries(ring, pq, valid ? S : 0, 0, pm | (u << 16), Gh, rq, Gl, rl,
+                   n0, scal);
+      drain();
+      continue;
+    }
+    // lattice points the item's sweep can come near: per axis the
+    // integers within sqrt(cwide)/N_x of [h(dmin), h(dmax)]
+    int ml[3] = {0, 0, 0}, nm[3] = {0, 0, 0}, ncomb = 0;
+    if (iv_ok && valid) {
+      ncomb = 1;
 #pragma unroll
       for (int x = 0; x < 3; ++x) {
-        my[x] = make_float2(Gh[x], rq[x]);
-        my[3 + x] = make_float2(Gl[x], rl[x]);
+        const float lo = fmaf(Gh[x], dmin, rq[x]), hi = fmaf(Gh[x], dmax, rq[x]);
+        ml[x] = (int)ceilf(fminf(lo, hi) - cmarg[x]);
+        nm[x] = (int)floorf(fmaxf(lo, hi) + cmarg[x]) - ml[x] + 1;
+        if (nm[x] < 0) nm[x] = 0;
+        ncomb *= nm[x];
       }
-      my[6] = make_float2(n0[0], n0[1]);
-      my[7] = make_float2(n0[2], scal);
-      __syncwarp();
-      int ch = 0, ct = 0;
-      auto run_cands = [&](int nc) {
-        // ring entry: owner lane | first source << 5 | count << 16
-        const int ci = lane >> 3, kk = lane & 7;
-        bool ok = ci < nc;
-        int ent = ok ? cring[(ch + ci) & (kCandRing - 1)] : 0;
-        int own = ent & 31, k0 = (ent >> 5) & 2047, cnt = (ent >> 16) & 15;
-        int k = k0 + kk;
-        ok = ok && kk < cnt && k < S;
-        const float2 *o =
-            reinterpret_cast<const float2 *>(st + own * kStateStride);
-        const float dh = s_dh[ok ? k : 0];
-        float fr[3], nf[3];
-        float2 gr[3];
-#pragma unroll
-        for (int x = 0; x < 3; ++x) {
-          gr[x] = o[x];  // (G_hi, r_q)
-          float tq = fmaf(gr[x].x, dh, gr[x].y);
-          nf[x] = rintf(tq);
-          fr[x] = tq - nf[x];
-        }
-        float rad2 = N2[0] * fr[0] * fr[0];
-        rad2 = fmaf(N2[1] * fr[1], fr[1], rad2);
-        rad2 = fmaf(N2[2] * fr[2], fr[2], rad2);
-        bool hit = ok && rad2 <= cutg;
-        unsigned m = __ballot_sync(0xffffffffu, hit);
-        if (m == 0u) return;
-        if (hit) {
-          // (delta_lo, w) of source k in one load
-          const float2 dlw = *reinterpret_cast<const float2 *>(
-              s_src + k * SRC32_STRIDE + SRC32_DL);
-          const float dl = dlw.x;
-          int e = (tail + __popc(m & lt_mask)) & (kRing - 1);
-          const float2 n01 = o[6], n2s = o[7];
-          const float n0o[3] = {n01.x, n01.y, n2s.x};
-          float f[3];
-          int nn[3];
+    }
+    if (iv_ok && __all_sync(0xffffffffu, ncomb <= 8)) {
+      // exact intervals: for lattice point m the exponent sum along the
+      // sweep is A d^2 + 2 B d + C, below cwide on one interval of the
+      // sorted delta table
+      const int maxc = (int)__reduce_max_sync(0xffffffffu, (unsigned)ncomb);
+      for (int c = 0; c < maxc; ++c) {
+        int k1 = 0, k2 = 0;
+        if (c < ncomb) {
+          float dx[3];
+          int cc = c;
 #pragma unroll
           for (int x = 0; x < 3; ++x) {
-            const float2 gl = o[3 + x];  // (G_lo, r_lo)
-            float sx = fmaf(gr[x].x, dh, __fsub_rn(gr[x].y, nf[x]));
-            float c = fmaf(gr[x].x, dl, fmaf(gl.x, dh, gl.y));
-            f[x] = sx + c;
-            nn[x] = __float2int_rn(n0o[x] + nf[x]) - a.hmin[x];
+            const int mx = ml[x] + cc % nm[x];
+            cc /= nm[x];
+            dx[x] = rq[x] - (float)mx;  // exact: r_q on a 2^-21 grid
           }
-          q.fw[e] = make_float4(f[0], f[1], f[2], dlw.y * n2s.y);
-          q.n[e] = make_int4(nn[0], nn[1], nn[2], 0);
-        }
-        tail += __popc(m);
-        if (tail - head >= 32) {
-          __syncwarp();
-          eval_term<INTERP>(a, q, (head + lane) & (kRing - 1), acc);
-          head += 32;
-          __syncwarp();
-        }
-      };
-      // lattice points the item's sweep can come near: per axis the
-      // integers within sqrt(cwide)/N_x of [h(dmin), h(dmax)]
-      int ml[3] = {0, 0, 0}, nm[3] = {0, 0, 0}, ncomb = 0;
-      if (iv_ok && valid) {
-        ncomb = 1;
-#pragma unroll
-        for (int x = 0; x < 3; ++x) {
-          float u = fmaf(Gh[x], dmin, rq[x]), v = fmaf(Gh[x], dmax, rq[x]);
-          ml[x] = (int)ceilf(fminf(u, v) - cmarg[x]);
-          nm[x] = (int)floorf(fmaxf(u, v) + cmarg[x]) - ml[x] + 1;
-          if (nm[x] < 0) nm[x] = 0;
-          ncomb *= nm[x];
-        }
-      }
-      if (iv_ok && __all_sync(0xffffffffu, ncomb <= 8)) {
-        // exact intervals: for lattice point m the exponent sum along
-        // the sweep is A d^2 + 2 B d + C, below cwide on one interval
-        const int maxc = (int)__reduce_max_sync(0xffffffffu, (unsigned)ncomb);
-        for (int c = 0; c < maxc; ++c) {
-          int k1 = 0, k2 = 0;
-          if (c < ncomb) {
-            float dx[3];
-            int cc = c;
-#pragma unroll
-            for (int x = 0; x < 3; ++x) {
-              int mx = ml[x] + cc % nm[x];
-              cc /= nm[x];
-              dx[x] = rq[x] - (float)mx;  // exact: r_q on a 2^-21 grid
-            }
-            float A = N2[0] * Gh[0] * Gh[0];
-            A = fmaf(N2[1] * Gh[1], Gh[1], A);
-            A = fmaf(N2[2] * Gh[2], Gh[2], A);
-            float B = N2[0] * Gh[0] * dx[0];
-            B = fmaf(N2[1] * Gh[1], dx[1], B);
-            B = fmaf(N2[2] * Gh[2], dx[2], B);
-            float C0 = N2[0] * dx[0] * dx[0];
-            C0 = fmaf(N2[1] * dx[1], dx[1], C0);
-            C0 = fmaf(N2[2] * dx[2], dx[2], C0);
-            if (A > 0.f) {
-              float disc = fmaf(B, B, -A * (C0 - cwide));
-              if (disc >= 0.f) {
-                float sq = sqrtf(disc);
-                float lo = (-B - sq) / A, hi = (-B + sq) / A;
-                float mg = 1e-4f * (fabsf(lo) + fabsf(hi)) + dmarg;
-                lo -= mg;
-                hi += mg;
-                // k1 = #{delta < lo}, k2 = #{delta <= hi} (sorted table)
-                if (even) {
-                  k1 = count_below(s_dh, S, guess_index(lo, dmin, inv_step, S),
-                                   lo);
-                  k2 = count_at_most(s_dh, S,
-                                     guess_index(hi, dmin, inv_step, S), hi);
-                } else {
-                  for (int st = sstep; st > 0; st >>= 1) {
-                    if (k1 + st <= S && s_dh[k1 + st - 1] < lo) k1 += st;
-                    if (k2 + st <= S && s_dh[k2 + st - 1] <= hi) k2 += st;
-                  }
+          float A = N2[0] * Gh[0] * Gh[0];
+          A = fmaf(N2[1] * Gh[1], Gh[1], A);
+          A = fmaf(N2[2] * Gh[2], Gh[2], A);
+          float B = N2[0] * Gh[0] * dx[0];
+          B = fmaf(N2[1] * Gh[1], dx[1], B);
+          B = fmaf(N2[2] * Gh[2], dx[2], B);
+          float C0 = N2[0] * dx[0] * dx[0];
+          C0 = fmaf(N2[1] * dx[1], dx[1], C0);
+          C0 = fmaf(N2[2] * dx[2], dx[2], C0);
+          if (A > 0.f) {
+            const float disc = fmaf(B, B, -A * (C0 - cwide));
+            if (disc >= 0.f) {
+              const float sq = sqrtf(disc);
+              float lo = (-B - sq) / A, hi = (-B + sq) / A;
+              const float mg = 1e-4f * (fabsf(lo) + fabsf(hi)) + dmarg;
+              lo -= mg;
+              hi += mg;
+              // k1 = #{delta < lo}, k2 = #{delta <= hi} (sorted table)
+              if (even) {
+                k1 = count_below(s_dh, S, guess_index(lo, dmin, inv_step, S),
+                                 lo);
+                k2 = count_at_most(s_dh, S, guess_index(hi, dmin, inv_step, S),
+                                   hi);
+              } else {
+                for (int st = sstep; st > 0; st >>= 1) {
+                  if (k1 + st <= S && s_dh[k1 + st - 1] < lo) k1 += st;
+                  if (k2 + st <= S && s_dh[k2 + st - 1] <= hi) k2 += st;
                 }
               }
-            } else if (C0 <= cwide) {
-              k2 = S;  // the sweep does not move: all or nothing
             }
-          }
-          const int nch = k2 > k1 ? (k2 - k1 + kSrcBlock - 1) / kSrcBlock : 0;
-          const int maxch =
-              (int)__reduce_max_sync(0xffffffffu, (unsigned)nch);
-          for (int j = 0; j < maxch; ++j) {
-            bool has = j < nch;
-            unsigned mm = __ballot_sync(0xffffffffu, has);
-            if (has) {
-              int st0 = k1 + j * kSrcBlock;
-              int cnt = min(kSrcBlock, k2 - st0);
-              cring[(ct + __popc(mm & lt_mask)) & (kCandRing - 1)] =
-                  lane | (st0 << 5) | (cnt << 16);
-            }
-            ct += __popc(mm);
-            __syncwarp();
-            while (ct - ch >= 4) {
-              run_cands(4);
-              ch += 4;
-            }
+          } else if (C0 <= cwide) {
+            k2 = S;  // the sweep does not move: all or nothing
           }
         }
-      } else {
-        for (int b = 0; b < nblk; ++b) {
-          bool pass = false;
-          if (valid) {
-            const float dmn = s_blk[2 * b], dmx = s_blk[2 * b + 1];
-            pass = true;
+        push_entries(ring, pq, k2 > k1 ? k2 - k1 : 0, k1, pm | (u << 16), Gh,
+                     rq, Gl, rl, n0, scal);
+        drain();
+      }
+    } else {
+      // pruned scan: h_x = G_x delta + r_x is linear in delta, so a block
+      // of sources whose delta range [dmn, dmx] keeps some axis farther
+      // than sqrt(cut)/N_x from every integer holds no surviving term
+      for (int bb = 0; bb < nblk; ++bb) {
+        bool pass = false;
+        if (valid) {
+          const float dmn = s_blk[2 * bb], dmx = s_blk[2 * bb + 1];
+          pass = true;
 #pragma unroll
-            for (int x = 0; x < 3; ++x) {
-              float u = fmaf(Gh[x], dmn, rq[x]), v = fmaf(Gh[x], dmx, rq[x]);
-              float lo = fminf(u, v) - cmarg[x],
-                    hi = fmaxf(u, v) + cmarg[x];
-              pass = pass && floorf(hi) >= ceilf(lo);
-            }
-          }
-          unsigned m = __ballot_sync(0xffffffffu, pass);
-          if (m == 0u) continue;
-          if (pass) {
-            int st0 = b * kSrcBlock;
-            int cnt = min(kSrcBlock, S - st0);
-            cring[(ct + __popc(m & lt_mask)) & (kCandRing - 1)] =
-                lane | (st0 << 5) | (cnt << 16);
-          }
-          ct += __popc(m);
-          __syncwarp();
-          while (ct - ch >= 4) {
-            run_cands(4);
-            ch += 4;
+          for (int x = 0; x < 3; ++x) {
+            const float lo0 = fmaf(Gh[x], dmn, rq[x]),
+                        hi0 = fmaf(Gh[x], dmx, rq[x]);
+            const float lo = fminf(lo0, hi0) - cmarg[x],
+                        hi = fmaxf(lo0, hi0) + cmarg[x];
+            pass = pass && floorf(hi) >= ceilf(lo);
           }
         }
+        const int st0 = bb * kSrcBlock;
+        push_entries(ring, pq, pass ? min(kSrcBlock, S - st0) : 0, st0,
+                     pm | (u << 16), Gh, rq, Gl, rl, n0, scal);
+        drain();
       }
-      if (ct > ch) {
-        run_cands(ct - ch);
-        ch = ct;
-      }
-      __syncwarp();  // the state area is rewritten by the next round
     }
   }
-  __syncwarp();
-  if (lane < tail - head)
-    eval_term<INTERP>(a, q, (head + lane) & (kRing - 1), acc);
-  evals += tail;
-  __syncwarp();
+  if (pq.ct > pq.ch)
+    nterms += sum_pairs<INTERP, HASDIV>(a, b, ring, pq, unit, cache, tags, acc);
+  evals += nterms;
 
-  // ---- 4. warp reduction in float-float: each lane's compensated sum is
+  // ---- warp reduction in float-float: each lane's compensated sum is
   // the pair (s, -c); pairs are added with error-free transformations (so
   // the butterfly gives every lane the same pair) and turned into FP64
   // once.  FP64 instructions run at 1/64 of the FP32 rate on this part and

@@ -12,20 +12,21 @@
 //      U = os^2 x layers sub-pixel units of all B pixels in FP64 (position,
 //      direction, solid angle, capture, polarization) into shared memory,
 //      then the warp sums the pixels one after another;
-//   2. lanes take (unit, phi x mosaic) items round-robin and form G and r
+//   2. lanes take (unit, phi x mosaic) items 32 at a time and form G and r
 //      in double-float.  h_x = G_x delta + r_x is linear in a source's
 //      delta = 1/lambda - u0, so for each lattice point near the item's
 //      sweep the sources whose exponent sum N^2 f^2 / 0.63 can stay below
 //      the underflow cut form one interval of the sorted delta table (a
-//      quadratic in delta, then a binary search); where that does not
-//      apply, blocks of 8 sources are pruned by their delta range.  The
-//      surviving (lane, source range) pairs go into a candidate ring, the
-//      warp tests 32 sources at a time, and steps below the cut are pushed
-//      into a per-warp term ring in shared memory;
-//   3. whenever the term ring holds 32 terms, every lane evaluates one of
-//      them (exp, F_cell from the cell's tricubic polynomial or the table,
-//      product) into its own Kahan sum;
-//   4. the 32 lane sums are reduced with warp shuffles in FP64.
+//      quadratic in delta, then a short search); where that does not
+//      apply, blocks of 8 sources are pruned by their delta range.  Each
+//      non-empty interval becomes one entry of a per-warp ring in shared
+//      memory, holding a copy of its item's state;
+//   3. whenever the ring holds 32 (entry, source) pairs, each lane takes
+//      one pair, forms the step's exact fractional offset and, if the step
+//      survives the cut, its term (exp, F_cell from the cell's tricubic
+//      polynomial in a per-warp shared-memory cache, or from the table)
+//      into its own Kahan sum;
+//   4. the 32 lane sums are reduced with warp shuffles in float-float.
 // The order of every operation depends only on the pixel's own inputs, so
 // a pixel's value does not depend on what else is in the launch.
 // Pixels are handed to warps through an atomic counter in a scratch word.
@@ -81,13 +82,7 @@ __global__ void __launch_bounds__(kSplitThreads, 5)
 }
 
 size_t split_smem_bytes(const SpotArgs &a) {
-  int nblk = (a.S + kSrcBlock - 1) / kSrcBlock;
-  return (size_t)(2 * a.PM * 9 + a.S * SRC32_STRIDE +
-                  kSplitWarps * kMaxUnits * kUnitFloats) * sizeof(float) +
-         16 /* alignment of the rings */ + kSplitWarps * sizeof(SplitRing) +
-         (size_t)kSplitWarps * 32 * kStateStride * sizeof(float) +
-         (size_t)kSplitWarps * kCandRing * sizeof(int) +
-         (size_t)(2 * nblk + a.S) * sizeof(float);
+  return split_smem_layout(a.PM, a.S);
 }
 
 bool split_supported(const SpotArgs &a) {
