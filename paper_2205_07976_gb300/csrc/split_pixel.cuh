@@ -20,14 +20,23 @@ constexpr int kSrcBlock = 8;     // sources per pruning block
 // never exceed 31 (each holds an unconsumed source) plus the 32 a push adds.
 constexpr int kEntries = 64;
 
+// Two kinds of entry.  An interval entry belongs to one lattice point m of
+// the item's sweep: every surviving step of it has m as its nearest
+// integer, so the entry holds r_q - (m - n0) in place of r_q and m's table
+// index, and a step's offset needs no rounding.  A block entry (pruning by
+// source blocks, or sources of different directions) holds r_q and n0, and
+// each step rounds to its nearest integer.
 struct SplitEntry {
-  float4 a;  // G_hi h, r_q h, G_hi k, r_q k
-  float4 b;  // G_hi l, r_q l, G_lo h, r_lo h
+  float4 a;  // G_hi h, r h, G_hi k, r k      (r = r_q, or r_q - (m - n0))
+  float4 b;  // G_hi l, r l, G_lo h, r_lo h
   float4 c;  // G_lo k, r_lo k, G_lo l, r_lo l
-  float4 d;  // n0 h, n0 k, n0 l, omega cap pol of the unit
+  float4 d;  // n0 h, n0 k, n0 l (floats) or m's table index (int bits), and
+             // omega cap pol of the unit
   int4 m;    // first source, count, position of the first source in the
-             // pixel's sequence of (entry, source) pairs, pm | unit << 16
+             // pixel's sequence of (entry, source) pairs,
+             // pm | unit << 16 | interval entry << 31
 };
+constexpr int kIntervalEntry = 1 << 31;
 static_assert(sizeof(SplitEntry) % 16 == 0, "entries stay 16-byte aligned");
 static_assert(SRC32_DL % 2 == 0 && SRC32_W == SRC32_DL + 1 &&
                   SRC32_STRIDE % 2 == 0 && kUnitFloats % 2 == 0,
@@ -94,7 +103,8 @@ __device__ __forceinline__ float cell_horner(const float4 *cp, int stride,
 }
 
 // The term F_cell^2 F_latt^2 w of a lane whose step survived the cut (`hit`),
-// given its fractional offset fr and table-relative nearest index n.  Called
+// given its fractional offset fr, table-relative nearest index n and
+// exponent sum rad2 = sum N^2 fr^2.  Called
 // by all 32 lanes of the warp: missing cells are loaded into the cache by
 // the whole warp (one coalesced 256-byte read per cell).  A lane whose
 // parity slot ends up holding another cell (two lattice points in one pass)
@@ -102,11 +112,8 @@ __device__ __forceinline__ float cell_horner(const float4 *cp, int stride,
 template <int INTERP>
 __device__ __forceinline__ float term_value(const SpotArgs &a, bool hit,
                                             const float fr[3], const int n[3],
-                                            float w, float4 *cache,
-                                            int *tags) {
-  float rad2 = a.N[0] * a.N[0] * fr[0] * fr[0];
-  rad2 = fmaf(a.N[1] * a.N[1], fr[1] * fr[1], rad2);
-  rad2 = fmaf(a.N[2] * a.N[2], fr[2] * fr[2], rad2);
+                                            float rad2, float w,
+                                            float4 *cache, int *tags) {
   // fast exp: a few ulp for the significant terms (|argument| < ~20)
   const float fl2 = a.N6 * __expf(-2.f * rad2 * (1.f / 0.63f));
   int fl[3];
@@ -117,9 +124,11 @@ __device__ __forceinline__ float term_value(const SpotArgs &a, bool hit,
     fl[c] = n[c] - neg;
     x[c] = neg ? 1.f + fr[c] : fr[c];
   }
-  const bool tri = INTERP == 1 && hit && a.C4 && fl[0] >= 1 &&
-                   fl[0] + 2 < a.hn[0] && fl[1] >= 1 && fl[1] + 2 < a.hn[1] &&
-                   fl[2] >= 1 && fl[2] + 2 < a.hn[2];
+  // the 4x4x4 stencil fl - 1 .. fl + 2 inside the table
+  const bool tri = INTERP == 1 && hit && a.C4 &&
+                   (unsigned)(fl[0] - 1) < (unsigned)(a.hn[0] - 3) &&
+                   (unsigned)(fl[1] - 1) < (unsigned)(a.hn[1] - 3) &&
+                   (unsigned)(fl[2] - 1) < (unsigned)(a.hn[2] - 3);
   int ci = 0, par = 0;
   if (tri) {
     ci = ((fl[0] - 1) * (a.hn[1] - 3) + (fl[1] - 1)) * (a.hn[2] - 3) +
@@ -371,11 +380,12 @@ struct PairQueue {
 };
 
 // Appends one entry per lane with len > 0 (sources k1 .. k1 + len - 1 of the
-// item whose state the lane holds), in lane order.  Called by all lanes.
+// item whose state the lane holds; r and d4 as SplitEntry describes), in
+// lane order.  Called by all lanes.
 __device__ __forceinline__ void push_entries(
     SplitEntry *ring, PairQueue &pq, int len, int k1, int aux,
-    const float Gh[3], const float rq[3], const float Gl[3], const float rl[3],
-    const float n0[3], float scal) {
+    const float Gh[3], const float r[3], const float Gl[3], const float rl[3],
+    float4 d4) {
   const int lane = threadIdx.x & 31;
   int inc = len;
 #pragma unroll
@@ -389,10 +399,10 @@ __device__ __forceinline__ void push_entries(
   if (len > 0) {
     SplitEntry &E =
         ring[(pq.en + __popc(hm & ((1u << lane) - 1u))) & (kEntries - 1)];
-    E.a = make_float4(Gh[0], rq[0], Gh[1], rq[1]);
-    E.b = make_float4(Gh[2], rq[2], Gl[0], rl[0]);
+    E.a = make_float4(Gh[0], r[0], Gh[1], r[1]);
+    E.b = make_float4(Gh[2], r[2], Gl[0], rl[0]);
     E.c = make_float4(Gl[1], rl[1], Gl[2], rl[2]);
-    E.d = make_float4(n0[0], n0[1], n0[2], scal);
+    E.d = d4;
     E.m = make_int4(k1, len, pq.ct + inc - len, aux);
   }
   pq.en += __popc(hm);
@@ -428,39 +438,49 @@ __device__ __forceinline__ unsigned sum_pairs(
   const int k = valid ? k1 + (pq.ch + lane - pos) : 0;
   const SplitEntry &E = ring[(pq.e0 + j) & (kEntries - 1)];
   const float4 A = E.a, B = E.b, C = E.c, D = E.d;
-  const float Gh[3] = {A.x, A.z, B.x}, rq[3] = {A.y, A.w, B.y};
+  const float Gh[3] = {A.x, A.z, B.x}, r[3] = {A.y, A.w, B.y};
   const float Gl[3] = {B.z, C.x, C.z}, rl[3] = {B.w, C.y, C.w};
-  const float n0[3] = {D.x, D.y, D.z};
   const float *src = b.src + k * SRC32_STRIDE;
   const float dh = b.dh[k];
   // (delta_lo, w) of source k in one load
   const float2 dlw = *reinterpret_cast<const float2 *>(src + SRC32_DL);
   float fr[3];
   int n[3];
+  if (!HASDIV && (aux & kIntervalEntry)) {
+    // G_hi d_hi + (r_q - (m - n0)) in one rounding plus the small terms;
+    // the nearest integer is m
 #pragma unroll
-  for (int x = 0; x < 3; ++x) {
-    float tq = fmaf(Gh[x], dh, rq[x]);
-    float e0 = 0.f, e1 = 0.f;
-    if (HASDIV) {
-      const size_t e = ((size_t)(aux & 0xffff) * b.S + k) * 3 + x;
-      e0 = __ldg(a.divh + e);
-      e1 = __ldg(a.divl + e);
-      tq -= e0;
+    for (int x = 0; x < 3; ++x) {
+      fr[x] = fmaf(Gh[x], dh, r[x]) + fmaf(Gh[x], dlw.x, fmaf(Gl[x], dh, rl[x]));
+      n[x] = __float_as_int(x == 0 ? D.x : x == 1 ? D.y : D.z);
     }
-    float nf = rintf(tq);
-    // G_hi d_hi + (r_q - n) in one rounding (r_q on a 2^-21 grid makes
-    // r_q - n exact) plus the small terms
-    const float sx = fmaf(Gh[x], dh, __fsub_rn(rq[x], nf));
-    const float c = fmaf(Gh[x], dlw.x, fmaf(Gl[x], dh, rl[x]));
-    fr[x] = sx + c;
-    if (HASDIV) {
-      // the divergence term moves h after the rint: re-centre
-      fr[x] -= e0 + e1;
-      const float n2 = rintf(fr[x]);
-      fr[x] -= n2;
-      nf += n2;
+  } else {
+    const float n0[3] = {D.x, D.y, D.z};
+#pragma unroll
+    for (int x = 0; x < 3; ++x) {
+      float tq = fmaf(Gh[x], dh, r[x]);
+      float e0 = 0.f, e1 = 0.f;
+      if (HASDIV) {
+        const size_t e = ((size_t)(aux & 0xffff) * b.S + k) * 3 + x;
+        e0 = __ldg(a.divh + e);
+        e1 = __ldg(a.divl + e);
+        tq -= e0;
+      }
+      float nf = rintf(tq);
+      // G_hi d_hi + (r_q - n) in one rounding (r_q on a 2^-21 grid makes
+      // r_q - n exact) plus the small terms
+      const float sx = fmaf(Gh[x], dh, __fsub_rn(r[x], nf));
+      const float c = fmaf(Gh[x], dlw.x, fmaf(Gl[x], dh, rl[x]));
+      fr[x] = sx + c;
+      if (HASDIV) {
+        // the divergence term moves h after the rint: re-centre
+        fr[x] -= e0 + e1;
+        const float n2 = rintf(fr[x]);
+        fr[x] -= n2;
+        nf += n2;
+      }
+      n[x] = __float2int_rn(n0[x] + nf) - a.hmin[x];
     }
-    n[x] = __float2int_rn(n0[x] + nf) - a.hmin[x];
   }
   float rad2 = a.N[0] * a.N[0] * fr[0] * fr[0];
   rad2 = fmaf(a.N[1] * a.N[1], fr[1] * fr[1], rad2);
@@ -468,7 +488,7 @@ __device__ __forceinline__ unsigned sum_pairs(
   const bool hit = valid && rad2 <= kGaussCut * 0.63f;
   float w = dlw.y * D.w;
   if (HASDIV && hit) {
-    const float *df = unit + (aux >> 16) * kUnitFloats + 7;
+    const float *df = unit + ((aux >> 16) & 31) * kUnitFloats + 7;
     const float *dir = src + SRC32_DIR, *ev = src + SRC32_E,
                 *bv = src + SRC32_B;
     const float c2 = df[0] * dir[0] + df[1] * dir[1] + df[2] * dir[2];
@@ -478,7 +498,7 @@ __device__ __forceinline__ unsigned sum_pairs(
   }
   const unsigned hm = __ballot_sync(0xffffffffu, hit);
   if (hm != 0u) {
-    const float t = term_value<INTERP>(a, hit, fr, n, w, cache, tags);
+    const float t = term_value<INTERP>(a, hit, fr, n, rad2, w, cache, tags);
     if (hit) acc.add(t);
   }
   pq.e0 += __popc(done);
@@ -551,7 +571,7 @@ __device__ __forceinline__ double split_sum(const SpotArgs &a,
     if (HASDIV) {
       // sources of different directions: every source of every item
       push_entries(ring, pq, valid ? S : 0, 0, pm | (u << 16), Gh, rq, Gl, rl,
-                   n0, scal);
+                   make_float4(n0[0], n0[1], n0[2], scal));
       drain();
       continue;
     }
@@ -576,14 +596,17 @@ __device__ __forceinline__ double split_sum(const SpotArgs &a,
       const int maxc = (int)__reduce_max_sync(0xffffffffu, (unsigned)ncomb);
       for (int c = 0; c < maxc; ++c) {
         int k1 = 0, k2 = 0;
+        float dx[3] = {0.f, 0.f, 0.f};
+        int nt[3] = {0, 0, 0};
         if (c < ncomb) {
-          float dx[3];
           int cc = c;
 #pragma unroll
           for (int x = 0; x < 3; ++x) {
+            // lattice point n0 + mx; its table index nt
             const int mx = ml[x] + cc % nm[x];
             cc /= nm[x];
             dx[x] = rq[x] - (float)mx;  // exact: r_q on a 2^-21 grid
+            nt[x] = (int)n0[x] + mx - a.hmin[x];
           }
           float A = N2[0] * Gh[0] * Gh[0];
           A = fmaf(N2[1] * Gh[1], Gh[1], A);
@@ -619,8 +642,10 @@ __device__ __forceinline__ double split_sum(const SpotArgs &a,
             k2 = S;  // the sweep does not move: all or nothing
           }
         }
-        push_entries(ring, pq, k2 > k1 ? k2 - k1 : 0, k1, pm | (u << 16), Gh,
-                     rq, Gl, rl, n0, scal);
+        push_entries(ring, pq, k2 > k1 ? k2 - k1 : 0, k1,
+                     pm | (u << 16) | kIntervalEntry, Gh, dx, Gl, rl,
+                     make_float4(__int_as_float(nt[0]), __int_as_float(nt[1]),
+                                 __int_as_float(nt[2]), scal));
         drain();
       }
     } else {
@@ -643,7 +668,8 @@ __device__ __forceinline__ double split_sum(const SpotArgs &a,
         }
         const int st0 = bb * kSrcBlock;
         push_entries(ring, pq, pass ? min(kSrcBlock, S - st0) : 0, st0,
-                     pm | (u << 16), Gh, rq, Gl, rl, n0, scal);
+                     pm | (u << 16), Gh, rq, Gl, rl,
+                     make_float4(n0[0], n0[1], n0[2], scal));
         drain();
       }
     }
