@@ -76,8 +76,10 @@ struct SpotArgs {
   // F[i][j][l..l+3] (zero past the end), one 16-byte load per stencil row
   const float4 *F4;
   // optional tricubic cell polynomials: for the cell whose 4x4x4 stencil
-  // starts at table node (i, j, k), 16 float4 = 64 monomial coefficients
-  // C[a][b][c] of x^a y^b z^c (c fastest), x in [0, 1) from node + 1
+  // starts at table node (i, j, k), 16 float4 = the 64 monomial
+  // coefficients C[a][b][c] of x^a y^b z^c, x in [0, 1) from node + 1;
+  // float4 2 (4 P + b) holds C[2P][b][3], C[2P+1][b][3], C[2P][b][2],
+  // C[2P+1][b][2] and the next one the same for c = 1 and c = 0
   const float4 *C4;
   int hmin[3], hn[3];
   float defF;

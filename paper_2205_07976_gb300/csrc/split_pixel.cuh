@@ -27,9 +27,9 @@ constexpr int kEntries = 64;
 // source blocks, or sources of different directions) holds r_q and n0, and
 // each step rounds to its nearest integer.
 struct SplitEntry {
-  float4 a;  // G_hi h, r h, G_hi k, r k      (r = r_q, or r_q - (m - n0))
-  float4 b;  // G_hi l, r l, G_lo h, r_lo h
-  float4 c;  // G_lo k, r_lo k, G_lo l, r_lo l
+  float4 a;  // G_hi h, G_hi k, r h, r k      (r = r_q, or r_q - (m - n0))
+  float4 b;  // G_lo h, G_lo k, r_lo h, r_lo k
+  float4 c;  // G_hi l, r l, G_lo l, r_lo l
   float4 d;  // n0 h, n0 k, n0 l (floats) or m's table index (int bits), and
              // omega cap pol of the unit
   int4 m;    // first source, count, position of the first source in the
@@ -66,6 +66,29 @@ __device__ __forceinline__ void ff_dot3_pairs(const float2 *A,
   fast_two_sum(s2, lo, gh, gl);
 }
 
+// Packed two-lane FP32 arithmetic (Blackwell's f32x2 instructions): one
+// instruction rounds each lane exactly as the scalar fmaf / add does.
+__device__ __forceinline__ unsigned long long pk2(float2 v) {
+  return (unsigned long long)__float_as_uint(v.x) |
+         ((unsigned long long)__float_as_uint(v.y) << 32);
+}
+__device__ __forceinline__ float2 upk2(unsigned long long v) {
+  return make_float2(__uint_as_float((unsigned)v),
+                     __uint_as_float((unsigned)(v >> 32)));
+}
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;"
+      : "=l"(d)
+      : "l"(pk2(a)), "l"(pk2(b)), "l"(pk2(c)));
+  return upk2(d);
+}
+__device__ __forceinline__ float2 fadd2(float2 a, float2 b) {
+  unsigned long long d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk2(a)), "l"(pk2(b)));
+  return upk2(d);
+}
+
 // Per-warp cache of cell polynomials in shared memory.  The terms of one
 // evaluation pass almost always lie around a single lattice point n, in the
 // cells n - {0,1}^3, and those 8 cells have distinct parities (the low bit
@@ -81,25 +104,34 @@ __device__ __forceinline__ void ff_dot3_pairs(const float2 *A,
 constexpr int kCellSlots = 8;
 constexpr int kCellChunks = 16;  // float4 per cell polynomial
 
-// A cell's tricubic polynomial at x (cell coordinates in [0, 1)), nested
-// Horner in l, k, h (63 FMAs); chunk k of the coefficients at cp[k * stride],
-// read from shared memory (SHARED) or through the read-only path.
+// A cell's tricubic polynomial at x (cell coordinates in [0, 1)): nested
+// Horner in l, k, h, the z and y chains of the powers x^(2P) and x^(2P+1)
+// side by side in packed FMAs (30 packed + 3 scalar FMAs for the 63 of
+// the scalar form, with the same roundings); chunk q of the coefficients
+// (the layout of SpotArgs::C4) at cp[q * stride], read from shared memory
+// (SHARED) or through the read-only path.
 template <bool SHARED>
 __device__ __forceinline__ float cell_horner(const float4 *cp, int stride,
                                              const float x[3]) {
-  float qa[4];
+  const float2 z2 = make_float2(x[2], x[2]), y2 = make_float2(x[1], x[1]);
+  float2 q[2];
 #pragma unroll
-  for (int ia = 0; ia < 4; ++ia) {
-    float pb[4];
+  for (int P = 0; P < 2; ++P) {
+    float2 pb[4];
 #pragma unroll
     for (int ib = 0; ib < 4; ++ib) {
-      const float4 c4 = SHARED ? cp[(ia * 4 + ib) * stride]
-                               : __ldg(cp + (ia * 4 + ib) * stride);
-      pb[ib] = fmaf(fmaf(fmaf(c4.w, x[2], c4.z), x[2], c4.y), x[2], c4.x);
+      const int q0 = (P * 4 + ib) * 2;
+      const float4 A = SHARED ? cp[q0 * stride] : __ldg(cp + q0 * stride);
+      const float4 B =
+          SHARED ? cp[(q0 + 1) * stride] : __ldg(cp + (q0 + 1) * stride);
+      float2 v = ffma2(make_float2(A.x, A.y), z2, make_float2(A.z, A.w));
+      v = ffma2(v, z2, make_float2(B.x, B.y));
+      pb[ib] = ffma2(v, z2, make_float2(B.z, B.w));
     }
-    qa[ia] = fmaf(fmaf(fmaf(pb[3], x[1], pb[2]), x[1], pb[1]), x[1], pb[0]);
+    q[P] = ffma2(ffma2(ffma2(pb[3], y2, pb[2]), y2, pb[1]), y2, pb[0]);
   }
-  return fmaf(fmaf(fmaf(qa[3], x[0], qa[2]), x[0], qa[1]), x[0], qa[0]);
+  // q[P] = (C(x^(2P)) part, C(x^(2P+1)) part); Horner in x
+  return fmaf(fmaf(fmaf(q[1].y, x[0], q[1].x), x[0], q[0].y), x[0], q[0].x);
 }
 
 // The term F_cell^2 F_latt^2 w of a lane whose step survived the cut (`hit`),
@@ -399,9 +431,9 @@ __device__ __forceinline__ void push_entries(
   if (len > 0) {
     SplitEntry &E =
         ring[(pq.en + __popc(hm & ((1u << lane) - 1u))) & (kEntries - 1)];
-    E.a = make_float4(Gh[0], r[0], Gh[1], r[1]);
-    E.b = make_float4(Gh[2], r[2], Gl[0], rl[0]);
-    E.c = make_float4(Gl[1], rl[1], Gl[2], rl[2]);
+    E.a = make_float4(Gh[0], Gh[1], r[0], r[1]);
+    E.b = make_float4(Gl[0], Gl[1], rl[0], rl[1]);
+    E.c = make_float4(Gh[2], r[2], Gl[2], rl[2]);
     E.d = d4;
     E.m = make_int4(k1, len, pq.ct + inc - len, aux);
   }
@@ -438,8 +470,8 @@ __device__ __forceinline__ unsigned sum_pairs(
   const int k = valid ? k1 + (pq.ch + lane - pos) : 0;
   const SplitEntry &E = ring[(pq.e0 + j) & (kEntries - 1)];
   const float4 A = E.a, B = E.b, C = E.c, D = E.d;
-  const float Gh[3] = {A.x, A.z, B.x}, r[3] = {A.y, A.w, B.y};
-  const float Gl[3] = {B.z, C.x, C.z}, rl[3] = {B.w, C.y, C.w};
+  const float Gh[3] = {A.x, A.y, C.x}, r[3] = {A.z, A.w, C.y};
+  const float Gl[3] = {B.x, B.y, C.z}, rl[3] = {B.z, B.w, C.w};
   const float *src = b.src + k * SRC32_STRIDE;
   const float dh = b.dh[k];
   // (delta_lo, w) of source k in one load
@@ -449,11 +481,18 @@ __device__ __forceinline__ unsigned sum_pairs(
   if (!HASDIV && (aux & kIntervalEntry)) {
     // G_hi d_hi + (r_q - (m - n0)) in one rounding plus the small terms;
     // the nearest integer is m
-#pragma unroll
-    for (int x = 0; x < 3; ++x) {
-      fr[x] = fmaf(Gh[x], dh, r[x]) + fmaf(Gh[x], dlw.x, fmaf(Gl[x], dh, rl[x]));
-      n[x] = __float_as_int(x == 0 ? D.x : x == 1 ? D.y : D.z);
-    }
+    // axes h and k in packed FMAs, l in scalar ones (the same roundings)
+    const float2 dh2 = make_float2(dh, dh), dl2 = make_float2(dlw.x, dlw.x);
+    const float2 f01 =
+        fadd2(ffma2(make_float2(A.x, A.y), dh2, make_float2(A.z, A.w)),
+              ffma2(make_float2(A.x, A.y), dl2,
+                    ffma2(make_float2(B.x, B.y), dh2, make_float2(B.z, B.w))));
+    fr[0] = f01.x;
+    fr[1] = f01.y;
+    fr[2] = fmaf(Gh[2], dh, r[2]) + fmaf(Gh[2], dlw.x, fmaf(Gl[2], dh, rl[2]));
+    n[0] = __float_as_int(D.x);
+    n[1] = __float_as_int(D.y);
+    n[2] = __float_as_int(D.z);
   } else {
     const float n0[3] = {D.x, D.y, D.z};
 #pragma unroll
@@ -594,19 +633,26 @@ __device__ __forceinline__ double split_sum(const SpotArgs &a,
       // sweep is A d^2 + 2 B d + C, below cwide on one interval of the
       // sorted delta table
       const int maxc = (int)__reduce_max_sync(0xffffffffu, (unsigned)ncomb);
+      // the lattice points ml + (d0, d1, d2), d_x < nm_x, in odometer order
+      int dg[3] = {0, 0, 0};
       for (int c = 0; c < maxc; ++c) {
         int k1 = 0, k2 = 0;
         float dx[3] = {0.f, 0.f, 0.f};
         int nt[3] = {0, 0, 0};
         if (c < ncomb) {
-          int cc = c;
 #pragma unroll
           for (int x = 0; x < 3; ++x) {
             // lattice point n0 + mx; its table index nt
-            const int mx = ml[x] + cc % nm[x];
-            cc /= nm[x];
+            const int mx = ml[x] + dg[x];
             dx[x] = rq[x] - (float)mx;  // exact: r_q on a 2^-21 grid
             nt[x] = (int)n0[x] + mx - a.hmin[x];
+          }
+          if (++dg[0] == nm[0]) {
+            dg[0] = 0;
+            if (++dg[1] == nm[1]) {
+              dg[1] = 0;
+              ++dg[2];
+            }
           }
           float A = N2[0] * Gh[0] * Gh[0];
           A = fmaf(N2[1] * Gh[1], Gh[1], A);
@@ -620,8 +666,10 @@ __device__ __forceinline__ double split_sum(const SpotArgs &a,
           if (A > 0.f) {
             const float disc = fmaf(B, B, -A * (C0 - cwide));
             if (disc >= 0.f) {
-              const float sq = sqrtf(disc);
-              float lo = (-B - sq) / A, hi = (-B + sq) / A;
+              // the bounds carry a relative margin far above the error of
+              // the reciprocal
+              const float sq = sqrtf(disc), ia = __frcp_rn(A);
+              float lo = (-B - sq) * ia, hi = (-B + sq) * ia;
               const float mg = 1e-4f * (fabsf(lo) + fabsf(hi)) + dmarg;
               lo -= mg;
               hi += mg;

@@ -126,16 +126,24 @@ __global__ void cell_polynomials_kernel(const float *F, int nh, int nk,
           for (int q = 0; q < 4; ++q) v = fmaf(kLagrangeMono[q][b], U[a][q][r], v);
           T[a][b][r] = v;
         }
-    float4 *out = C4 + c * 16;
+    float Cm[4][4][4];  // coefficient of x^a y^b z^c
     for (int a = 0; a < 4; ++a)  // along l
-      for (int b = 0; b < 4; ++b) {
-        float v[4];
+      for (int b = 0; b < 4; ++b)
         for (int cc = 0; cc < 4; ++cc) {
           float t = 0.f;
           for (int r = 0; r < 4; ++r) t = fmaf(kLagrangeMono[r][cc], T[a][b][r], t);
-          v[cc] = t;
+          Cm[a][b][cc] = t;
         }
-        out[a * 4 + b] = make_float4(v[0], v[1], v[2], v[3]);
+    // chunks 2 (2 P + b) and 2 (2 P + b) + 1 pair the powers x^(2P) and
+    // x^(2P+1) so that packed two-lane FMAs run two Horner chains in z
+    float4 *out = C4 + c * 16;
+    for (int P = 0; P < 2; ++P)
+      for (int b = 0; b < 4; ++b) {
+        const int a0 = 2 * P, a1 = 2 * P + 1;
+        out[(P * 4 + b) * 2] = make_float4(Cm[a0][b][3], Cm[a1][b][3],
+                                           Cm[a0][b][2], Cm[a1][b][2]);
+        out[(P * 4 + b) * 2 + 1] = make_float4(Cm[a0][b][1], Cm[a1][b][1],
+                                               Cm[a0][b][0], Cm[a1][b][0]);
       }
   }
 }
