@@ -17,6 +17,11 @@ steps (outside the events) to flush the 129 MB L2.  Multi-GPU (torchrun):
 independent replicas, one shot per rank, no data-path collective; the
 slowest rank's time sets the rate.
 
+The oracle leg (`cpu`, rank 0 at N=1) times the FP64 CPU oracle on a row
+sample of the large shot (cpu_baseline) and reports every form's error
+against it per configuration: the single shot and the precision sweep
+(N = 10, 50, 200), with each form's full-image time (precision).
+
 --impl reference times the FP64 CPU oracle (the only reference this method
 has: the paper ships no code) on the host cores, on a strided row sample of
 the same shot per step.
@@ -42,8 +47,8 @@ WORKLOAD = ("large shot 3072x3072, oversample 2, 2 layers (0.5 mm, atten "
             "0.3 mm), 100 sources (0.5% Gaussian at 9.5 keV), 50 mosaic "
             "domains, cell 79x79x38 A, N=25 Gaussian, tricubic F on "
             "[-60,60]^3, Kahn 0.99")
-SM_COUNT_GB300 = 152
 FP32_LANES_PER_SM = 128
+MAX_SM_MHZ = 2070.0  # GB300's maximum SM clock
 # DRAM bytes (read + write) of one full-size launch of the warp-per-pixel
 # kernel, from one ncu capture (profiles/spots_split_large_shot_dram.txt);
 # valid only while the kernel sources hash to the value they had then
@@ -66,6 +71,27 @@ def captured_traffic():
     return TRAFFIC_CAPTURE["bytes"]
 
 
+# FP32-pipe utilisation of the warp-per-pixel kernel from one ncu --set full
+# capture on a 512x512 window of the large shot
+# (profiles/spots_split_window512_full.txt), keyed like the traffic figure
+PIPES_CAPTURE = None
+
+
+def captured_pipes():
+    """ncu's pipe utilisation of the current kernel, or None once its
+    sources changed since the capture."""
+    if PIPES_CAPTURE is None:
+        return None
+    import hashlib
+    h = hashlib.sha256()
+    for f in TRAFFIC_CAPTURE["sources"]:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    if h.hexdigest()[:16] != PIPES_CAPTURE["sha256_16"]:
+        return None
+    return {k: v for k, v in PIPES_CAPTURE.items() if k != "sha256_16"}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -78,8 +104,9 @@ def parse():
                     help="time an N x N window of the large shot instead "
                          "of the whole image (for profiling)")
     ap.add_argument("--legs", default="main,e2e,f64,cpu,serve,bkg,grad",
-                    help="comma list of main, e2e, f64, cpu, serve, bkg, "
-                         "grad")
+                    help="comma list of main, e2e, f64, cpu (the oracle "
+                         "leg: cpu_baseline and the per-config errors), "
+                         "serve, bkg, grad")
     ap.add_argument("--serve-requests", type=int, default=4096)
     ap.add_argument("--serve-seq-subset", type=int, default=16)
     ap.add_argument("--serve-budget", type=int, default=2_000_000_000,
@@ -290,11 +317,20 @@ def run_ours(args):
         return
     from paper_2205_07976_gb300 import flops
     evaluated, _ = sim.stats()  # terms evaluated by the last timed launch
+    # one more launch, untimed, with the counting instantiation: what a
+    # launch performs (the counts depend only on the inputs)
+    sim.count_work(True)
+    sim.zero()
+    step()
+    work = sim.work()
+    sim.count_work(False)
     t_kernel = sum(a.elapsed_time(b) for a, b in kernel_times) / 1e3 / len(
         kernel_times)
     alg = flops.algorithmic_flops(shot, evaluated)
+    performed = flops.performed_flops(shot, work)
     achieved = alg / t_kernel / 1e12
-    peak_fp32 = flops.fp32_peak_tflops(152, 2070.0)
+    sm_count = torch.cuda.get_device_properties(local).multi_processor_count
+    peak_fp32 = flops.fp32_peak_tflops(sm_count, MAX_SM_MHZ)
     sm_mhz = clocks["sm_mhz"] if clocks else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -321,18 +357,28 @@ def run_ours(args):
                      "kernel_ms": t_kernel * 1e3,
                      "algorithmic_tflop_per_launch": alg / 1e12,
                      "evaluated_terms": evaluated,
-                     "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x "
-                                    "2070 MHz (derived from unit counts; "
-                                    "FP32 is not in MEASURED_PEAKS)",
+                     "sm_count": sm_count,
+                     "peak_source": f"{sm_count} SMs (queried) x 128 FP32 "
+                                    "lanes x 2 flops x 2070 MHz (derived "
+                                    "from unit counts; FP32 is not in "
+                                    "MEASURED_PEAKS)",
                      "frac_at_measured_clock": (
-                         achieved / flops.fp32_peak_tflops(152, sm_mhz)
-                         if sm_mhz else None)},
+                         achieved / flops.fp32_peak_tflops(sm_count, sm_mhz)
+                         if sm_mhz else None),
+                     "performed_tflop_per_launch": performed / 1e12,
+                     "frac_performed": performed / t_kernel / 1e12
+                     / peak_fp32,
+                     "work": work,
+                     "ncu_pipes": captured_pipes()},
         "clocks": clocks,
     }
     if args.window:
         line["config"]["window"] = f"{args.window}x{args.window} pixels"
     if world == 1 and not args.no_cpu_baseline and "cpu" in legs:
         line["cpu_baseline"] = cpu_baseline(shot, 192)
+        # the oracle leg also gives each form's error per configuration
+        line["precision"] = run_precision(args, local, stream, torch, np,
+                                          nbgb, W)
     print(json.dumps(line), flush=True)
 
 
@@ -401,6 +447,78 @@ def run_f64(args, shot, local, stream, torch, nbgb, W):
                          "peak_source": "measured: independent FP64 FMA "
                                         "chains on every SM "
                                         "(nb_fp64_peak_tflops)"}}
+
+
+def run_precision(args, local, stream, torch, np, nbgb, W):
+    """Error of every form against the FP64 oracle, per configuration: the
+    single shot (256^2, N=10 sinc, every pixel) and the precision sweep
+    (1024^2, 100 sources, 20 domains, N in {10, 50, 200} sinc; the GPU
+    computes the whole image, the oracle every 16th row of it).  Relative
+    error per pixel on the sampled pixels above 1e-3 of their maximum (the
+    NB_MIXED gate) and, for NB_F64, above 1e-6 of it (the NB_F64 gate);
+    times are CUDA events around one full-image launch (median of 3, after
+    one untimed launch).  At N=200 the oracle's literal sin(pi N h)/sin(pi h)
+    is compared with its reduced form on the same pixels: that difference
+    is the rounding the FP64 gate has to allow at large N."""
+    import oracle
+    every = 16
+    out = {"sample": f"oracle on every {every}th row of the 1024^2 sweep "
+                     "(64 rows, 65536 pixels); every pixel of the 256^2 "
+                     "shot",
+           "configs": {}}
+
+    def rel(got, ref, floor):
+        m = ref > floor * ref.max()
+        r = np.abs(got[m] - ref[m]) / ref[m]
+        return float(r.max()), float(np.median(r)), int(m.sum())
+
+    def time_form(shot, prec):
+        sim = nbgb.Sim(prec, device=local, stream=stream).set_shot(shot)
+        sim.add_spots()
+        stream.synchronize()
+        ts = []
+        for _ in range(3):
+            sim.zero()
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            sim.add_spots()
+            ev1.record(stream)
+            stream.synchronize()
+            ts.append(ev0.elapsed_time(ev1) / 1e3)
+        img = sim.image()
+        sim.close()
+        return float(np.median(ts)), img
+
+    cases = [("single shot 256x256, N=10 sinc", W.single_shot_small(), None)]
+    for N in (10, 50, 200):
+        s = W.precision_shot(N)
+        cases.append((f"precision 1024x1024, N={N} sinc", s,
+                      W.strided_rows(s, every)))
+    for name, shot, pix in cases:
+        t0 = time.perf_counter()
+        ref = oracle.image(shot, pixels=pix)
+        t_orc = time.perf_counter() - t0
+        npx = shot.npix if pix is None else len(pix)
+        row = {"oracle_pixel_steps_per_s":
+               npx * shot.steps_per_pixel / t_orc}
+        for prec in ("f64", "mixed", "f32"):
+            t, img = time_form(shot, prec)
+            got = img if pix is None else img[pix]
+            e3 = rel(got, ref, 1e-3)
+            row[prec] = {"ms": t * 1e3,
+                         "pixel_steps_per_s": shot.pixel_steps / t,
+                         "max_rel": e3[0], "median_rel": e3[1],
+                         "pixels": e3[2]}
+            if prec == "f64":
+                e6 = rel(got, ref, 1e-6)
+                row[prec]["max_rel_above_1e-6"] = e6[0]
+        if shot.ncells[0] == 200:
+            lit = oracle.image(shot, pixels=pix, sinc_mode="literal")
+            row["oracle_literal_vs_reduced_max_rel_above_1e-6"] = rel(
+                lit, ref, 1e-6)[0]
+        out["configs"][name] = row
+    return out
 
 
 def run_grad(args, local, stream, torch, nbgb, W):
@@ -500,7 +618,9 @@ def run_background(args, shot, local, stream, flush, torch, nbgb, W):
             from paper_2205_07976_gb300 import flops
             ndir = len({tuple(d) for d in np.asarray(shot.dirs)})
             alg = flops.background_flops(shot, ndir)
-            peak = flops.fp32_peak_tflops(152, 2070.0)
+            peak = flops.fp32_peak_tflops(
+                torch.cuda.get_device_properties(local).multi_processor_count,
+                MAX_SM_MHZ)
             out["roofline"] = {"bound": "alu", "achieved": alg / t / 1e12,
                                "peak": peak, "unit": "TFLOP/s",
                                "frac": alg / t / 1e12 / peak,

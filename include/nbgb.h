@@ -182,6 +182,47 @@ const double *nb_image_device_ptr(const nb_sim *sim);
 int nb_get_stats(nb_sim *sim, long long *evaluated_terms,
                  long long *pixel_steps);
 
+/* Replace the values of the resident structure-factor table (Sec. II: one
+ * structure factor per Bragg spot) from device memory: F holds n_elems
+ * floats on the handle's device in the layout of nb_set_crystal, and
+ * n_elems must equal hkl_n[0] hkl_n[1] hkl_n[2] of the table set there
+ * (shape, origin, lookup and default_F are kept).  The copy is queued on
+ * the handle's stream (nothing goes through the host), so the caller must
+ * not change F until that stream has passed it; the tricubic tables
+ * derived from F are rebuilt at the next launch.  This is the refinement
+ * loop's upload: a structure-factor table that already lives on the GPU
+ * (a torch tensor being refined) stays there.  Errors: NB_ESTATE before
+ * nb_set_crystal has set a table; NB_EINVAL for NULL F or a wrong
+ * n_elems; NB_ECUDA if the copy cannot be queued. */
+int nb_set_fcell_device(nb_sim *sim, const float *F, size_t n_elems);
+
+/* Work counts of the last nb_add_spots* call, for the roofline of the work
+ * the kernels perform (the Bragg-spot sum of Sec. III-B: its steps, and
+ * what the warp-per-pixel kernel does to avoid visiting most of them).
+ * counts[i] for i < n_counts receives (entries past NB_WORK_N are 0):
+ *   NB_WORK_PIXEL_STEPS  pixels x subpixels x layers x sources x phi x mosaic
+ *   NB_WORK_UNITS        pixels x subpixels x layers
+ *   NB_WORK_ITEMS        units x phi steps x mosaic domains
+ *   NB_WORK_INTERVALS    lattice points for which the warp kernel solved the
+ *                        source interval of an item (0 for other kernels)
+ *   NB_WORK_BLOCKS       (item, 8-source block) range tests of the warp
+ *                        kernel's pruned scan (0 for other kernels)
+ *   NB_WORK_PAIRS        steps whose fractional offset was formed and tested
+ *                        against the Gaussian cut (every step for the
+ *                        thread-per-pixel and FP64 kernels)
+ *   NB_WORK_TERMS        steps whose term was evaluated (as nb_get_stats;
+ *                        every step for NB_F64)
+ * The warp kernel counts pairs, intervals and blocks only in launches made
+ * with the option NB_OPT_COUNT_WORK set (a separate instantiation, so that
+ * the counting costs the other launches nothing); otherwise those three
+ * are -1 after a warp-kernel launch.  The counts depend only on the inputs.
+ * Blocks until the launch is done.  Errors: NB_EINVAL for NULL counts or
+ * n_counts < 1. */
+enum { NB_WORK_PIXEL_STEPS = 0, NB_WORK_UNITS = 1, NB_WORK_ITEMS = 2,
+       NB_WORK_INTERVALS = 3, NB_WORK_BLOCKS = 4, NB_WORK_PAIRS = 5,
+       NB_WORK_TERMS = 6, NB_WORK_N = 7 };
+int nb_get_work(nb_sim *sim, long long *counts, int n_counts);
+
 /* Differentiable crystal (the refinement loop of x-ray tracing, Sec. II:
  * crystal parameters are refined until the simulated image matches the
  * measured one).  Sets the lab axes to the rows of Rx(tx) Ry(ty) Rz(tz) U
@@ -351,7 +392,11 @@ enum {
      * units and >= 8 (unit, phi x mosaic) items per pixel, else one thread
      * per pixel), NB_VARIANT_THREAD, NB_VARIANT_WARP (Gaussian shapes with
      * <= 32 units only; falls back to NB_VARIANT_THREAD otherwise) */
-    NB_OPT_VARIANT = 1
+    NB_OPT_VARIANT = 1,
+    /* 1: launches of the warp-per-pixel kernel also count the work
+     * nb_get_work reports (pairs, intervals, block tests); 0 (default):
+     * they do not, and run the instantiation without the counters */
+    NB_OPT_COUNT_WORK = 2
 };
 enum { NB_VARIANT_AUTO = 0, NB_VARIANT_THREAD = 1, NB_VARIANT_WARP = 2 };
 
@@ -381,7 +426,14 @@ int nb_set_option(nb_sim *sim, int key, long long value);
  * Scratch: a file-scope device array of about 200 KB on every GPU that
  * loads the library (held until the process exits) holds the staged tables
  * and two counters; n_pm <= 2048 and n_src <= 1024 are the limits it fits,
- * and larger values return NB_EINVAL.  Every call shares the array and
+ * and larger values return NB_EINVAL.  The kernel also stages those
+ * tables, with its per-warp rings, in at most 200 KB (204800 bytes) of
+ * shared memory: (72 n_pm + 48 n_src + 5120, rounded up to a multiple of
+ * 16) + 8 ceil(n_src / 8) + 4 n_src + 28800 bytes must fit, so the two limits
+ * cannot both be reached: with n_pm = 2048 at most 441 sources are
+ * accepted, with n_src = 1024 at most 1619 orientations.  A pair beyond
+ * that returns NB_EINVAL before anything is queued.  Every call shares the
+ * array and
  * rewrites it (the counters are cleared before the kernel runs), so calls
  * whose work overlaps on the GPU race: serialise them.  The first call on a
  * device looks up the array's device address once (cudaGetSymbolAddress

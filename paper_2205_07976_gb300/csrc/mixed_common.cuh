@@ -7,6 +7,40 @@
 
 namespace nbgb {
 
+// Packed two-lane FP32 arithmetic (Blackwell's f32x2 instructions): one
+// instruction rounds each lane exactly as the scalar fmaf / add / sub / mul
+// does.
+__device__ __forceinline__ unsigned long long pk2(float2 v) {
+  return (unsigned long long)__float_as_uint(v.x) |
+         ((unsigned long long)__float_as_uint(v.y) << 32);
+}
+__device__ __forceinline__ float2 upk2(unsigned long long v) {
+  return make_float2(__uint_as_float((unsigned)v),
+                     __uint_as_float((unsigned)(v >> 32)));
+}
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;"
+      : "=l"(d)
+      : "l"(pk2(a)), "l"(pk2(b)), "l"(pk2(c)));
+  return upk2(d);
+}
+__device__ __forceinline__ float2 fadd2(float2 a, float2 b) {
+  unsigned long long d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk2(a)), "l"(pk2(b)));
+  return upk2(d);
+}
+__device__ __forceinline__ float2 fsub2(float2 a, float2 b) {
+  unsigned long long d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk2(a)), "l"(pk2(b)));
+  return upk2(d);
+}
+__device__ __forceinline__ float2 fmul2(float2 a, float2 b) {
+  unsigned long long d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk2(a)), "l"(pk2(b)));
+  return upk2(d);
+}
+
 __device__ __forceinline__ double dot3d_m(const double *a, const double *b) {
   return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
 }
@@ -136,6 +170,52 @@ __device__ __forceinline__ void frac_ff(float Gh, float Gl, float rh, float rl,
   float t2 = __fsub_rn(t, nf);  // exact
   fh = __fadd_rn(t2, lo);
   fl = __fsub_rn(lo, __fsub_rn(fh, t2));
+}
+
+// frac_ff<0> for two axes at once (the lanes of the float2s), with the
+// same roundings lane by lane; the negations are moved into the operands
+// (exact in IEEE arithmetic).
+__device__ __forceinline__ void frac_ff2(float2 Gh, float2 Gl, float2 rh,
+                                         float2 rl, float dh, float dl,
+                                         float2 &fh, float2 &fl,
+                                         float2 &nf) {
+  const float2 d2 = make_float2(dh, dh), l2 = make_float2(dl, dl);
+  const float2 pn = fmul2(Gh, make_float2(-dh, -dh));  // -p, p = Gh dh
+  const float2 pe = ffma2(Gh, d2, pn);                 // Gh dh - p
+  const float2 t = fsub2(rh, pn);                      // two_sum(p, rh)
+  const float2 bb = fadd2(t, pn);
+  const float2 te = fsub2(fsub2(rh, bb), fadd2(pn, fsub2(t, bb)));
+  float2 lo = fadd2(fadd2(pe, te), rl);
+  lo = ffma2(Gh, l2, lo);
+  lo = ffma2(Gl, d2, lo);
+  nf = make_float2(rintf(t.x), rintf(t.y));
+  const float2 t2 = fsub2(t, nf);  // exact
+  fh = fadd2(t2, lo);
+  fl = fsub2(lo, fsub2(fh, t2));
+}
+
+// sin(pi x) of two arguments at once: sinpi_reduced lane by lane
+__device__ __forceinline__ float2 sinpi_reduced2(float2 x) {
+  const float2 t = fmul2(x, x);
+  float2 p = ffma2(make_float2(-6.941131045e-03f, -6.941131045e-03f), t,
+                   make_float2(8.199509639e-02f, 8.199509639e-02f));
+  p = ffma2(p, t, make_float2(-5.992401060e-01f, -5.992401060e-01f));
+  p = ffma2(p, t, make_float2(2.550162271e+00f, 2.550162271e+00f));
+  p = ffma2(p, t, make_float2(-5.167712735e+00f, -5.167712735e+00f));
+  p = ffma2(p, t, make_float2(3.141592653e+00f, 3.141592653e+00f));
+  return fmul2(x, p);
+}
+
+// y = N f - rint(N f) for two axes, f = fh + fl (double-float), N f formed
+// exactly (two_prod) before the reduction; the negated products keep the
+// roundings of the scalar form
+__device__ __forceinline__ float2 sinc_arg2(float2 N2, float2 fh, float2 fl) {
+  const float2 nN2 = make_float2(-N2.x, -N2.y);
+  const float2 yh = fmul2(N2, fh);
+  const float2 ye_neg = ffma2(nN2, fh, yh);       // -(N fh - yh)
+  const float2 yl_neg = ffma2(nN2, fl, ye_neg);   // -(N fl + ye)
+  const float2 rr = make_float2(rintf(yh.x), rintf(yh.y));
+  return fsub2(fsub2(yh, rr), yl_neg);
 }
 
 template <int INTERP>

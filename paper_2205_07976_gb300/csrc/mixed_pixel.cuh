@@ -101,6 +101,50 @@ __device__ __forceinline__ double mixed_pixel(const SpotArgs &a,
               rh[x] = rl[x] = n0[x] = 0.f;
             }
           }
+          if (MODE == 0 && SHAPE == 0 && !HASDIV) {
+            // sinc in NB_MIXED: the h and k axes in packed two-lane FP32
+            // arithmetic, l in scalar; the numerator and denominator sines
+            // of an axis pair in one packed polynomial each
+            const float2 Gh2 = make_float2(Gh[0], Gh[1]),
+                         Gl2 = make_float2(Gl[0], Gl[1]),
+                         rh2 = make_float2(rh[0], rh[1]),
+                         rl2 = make_float2(rl[0], rl[1]),
+                         N2 = make_float2(a.N[0], a.N[1]);
+            for (int k = 0; k < v.S; ++k) {
+              const float *src = s_src + k * SRC32_STRIDE;
+              const float dh = src[SRC32_DH], dl = src[SRC32_DL];
+              float2 fh2, fl2v, nf2;
+              frac_ff2(Gh2, Gl2, rh2, rl2, dh, dl, fh2, fl2v, nf2);
+              float frz, frlz, nfz;
+              frac_ff<0>(Gh[2], Gl[2], rh[2], rl[2], dh, dl, 0.f, 0.f, frz,
+                         frlz, nfz);
+              const float fr[3] = {fh2.x, fh2.y, frz};
+              int n[3];
+              n[0] = __float2int_rn(n0[0] + nf2.x) - a.hmin[0];
+              n[1] = __float2int_rn(n0[1] + nf2.y) - a.hmin[1];
+              n[2] = __float2int_rn(n0[2] + nfz) - a.hmin[2];
+              const float2 yr2 = sinc_arg2(N2, fh2, fl2v);
+              const float2 nh = sinpi_reduced2(yr2);  // numerators h, k
+              const float2 dk = sinpi_reduced2(fh2);  // denominators h, k
+              float yzh, yze;
+              two_prod(a.N[2], frz, yzh, yze);
+              const float yzl = fmaf(a.N[2], frlz, yze);
+              const float yzr = __fsub_rn(yzh, rintf(yzh)) + yzl;
+              const float2 sl = sinpi_reduced2(make_float2(yzr, frz));
+              // at a lattice point (|f| < 1e-9) the ratio is N
+              const bool z0 = fabsf(fh2.x) < 1e-9f, z1 = fabsf(fh2.y) < 1e-9f,
+                         z2 = fabsf(frz) < 1e-9f;
+              const float num = (z0 ? a.N[0] : nh.x) * (z1 ? a.N[1] : nh.y) *
+                                (z2 ? a.N[2] : sl.x);
+              const float den = (z0 ? 1.f : dk.x) * (z1 ? 1.f : dk.y) *
+                                (z2 ? 1.f : sl.y);
+              const float ratio = __fdividef(num, den);
+              ++evals;
+              const float fc = fcell_f32<INTERP>(a, n, fr);
+              acc.add(fc * fc * (ratio * ratio) * src[SRC32_W]);
+            }
+            continue;
+          }
           for (int k = 0; k < v.S; ++k) {
             const float *src = s_src + k * SRC32_STRIDE;
             float fr[3], frl[3];

@@ -88,7 +88,10 @@ struct nb_sim {
       d_F, d_image, d_list, d_tmp, d_stats, d_work;
   int variant = NB_VARIANT_AUTO;
   int sm_count = 0;
-  long long last_pixel_steps = 0;
+  long long last_pixel_steps = 0, last_pixels = 0;
+  bool last_warp = false;  // the last launch ran the warp-per-pixel kernel
+  bool count_work = false;  // NB_OPT_COUNT_WORK
+  bool last_counted = false;  // the last launch counted its work
   // parametrised crystal (for gradients): U, cell, rotation angles
   bool have_params = false;
   double pU[9] = {0}, pcell[3] = {0}, prot[3] = {0};
@@ -541,6 +544,7 @@ int nb_set_crystal(nb_sim *s, const double axes[9], const double *umats,
                    double Nb, double Nc, int shape, const float *F,
                    const int hkl_min[3], const int hkl_n[3], int interp,
                    double default_F) {
+  nbgb::NvtxRange nvtx_("nb_set_crystal");
   if (!s) return NB_EINVAL;
   if (!axes || !umats) return fail(s, NB_EINVAL, "axes/umats NULL");
   if (n_mosaic < 1 || n_phi < 1 || (long long)n_mosaic * n_phi > nbgb::kMaxPM)
@@ -608,9 +612,28 @@ int nb_set_crystal(nb_sim *s, const double axes[9], const double *umats,
   return NB_OK;
 }
 
+int nb_set_fcell_device(nb_sim *s, const float *F, size_t n_elems) {
+  nbgb::NvtxRange nvtx_("nb_set_fcell_device");
+  if (!s) return NB_EINVAL;
+  if (!F) return fail(s, NB_EINVAL, "F NULL");
+  if (!s->have_F) return fail(s, NB_ESTATE, "no structure-factor table yet");
+  const size_t nF = (size_t)s->hn[0] * s->hn[1] * s->hn[2];
+  if (n_elems != nF)
+    return fail(s, NB_EINVAL, "n_elems differs from the table's size");
+  DeviceGuard g(s->device);
+  cudaError_t e = cudaMemcpyAsync(s->d_F.p, F, nF * sizeof(float),
+                                  cudaMemcpyDeviceToDevice, s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e, "F copy");
+  // the derived tables are rebuilt from the new values at the next launch
+  s->F4_valid = false;
+  s->C4_valid = false;
+  return NB_OK;
+}
+
 int nb_set_crystal_params(nb_sim *s, const double U[9], const double cell[3],
                           const double rot[3], const double ncells[3],
                           double scale) {
+  nbgb::NvtxRange nvtx_("nb_set_crystal_params");
   if (!s) return NB_EINVAL;
   if (!U || !cell || !rot || !ncells)
     return fail(s, NB_EINVAL, "NULL parameter array");
@@ -645,6 +668,7 @@ int nb_set_scale(nb_sim *s, double scale) {
 int nb_set_beam(nb_sim *s, const double *dirs, const double *lambda_A,
                 const double *weights, int n_src, double fluence,
                 double kahn_K, const double e_vec[3]) {
+  nbgb::NvtxRange nvtx_("nb_set_beam");
   if (!s) return NB_EINVAL;
   if (n_src < 1 || n_src > nbgb::kMaxSrc)
     return fail(s, NB_EINVAL, "need 1 <= n_src <= 1024");
@@ -685,6 +709,7 @@ long long nb_num_pixels(const nb_sim *s) { return s ? s->npix : 0; }
 int nb_set_detector(nb_sim *s, int n_panels, const nb_panel *panels,
                     int oversample, int n_layers, double thickness_m,
                     double atten_m) {
+  nbgb::NvtxRange nvtx_("nb_set_detector");
   if (!s) return NB_EINVAL;
   if (n_panels < 1 || !panels) return fail(s, NB_EINVAL, "no panels");
   if (oversample < 1 || oversample > 64 || n_layers < 1 || n_layers > 64)
@@ -771,12 +796,15 @@ static void ensure_sliding_table(nb_sim *s) {
 }
 
 // the tricubic polynomial of every table cell (64 floats per cell) for the
-// warp-per-pixel kernel; skipped above 2 GB or if the allocation fails
+// warp-per-pixel kernel; skipped above 2 GB, for an axis longer than 1000
+// nodes, or if the allocation fails
 static void ensure_cell_polynomials(nb_sim *s) {
   if (s->C4_valid || s->interp != NB_INTERP_TRICUBIC ||
       s->precision != NB_MIXED)
     return;
   if (s->hn[0] < 4 || s->hn[1] < 4 || s->hn[2] < 4) return;
+  // the warp kernel packs a table index into 10 bits per axis
+  if (s->hn[0] > 1000 || s->hn[1] > 1000 || s->hn[2] > 1000) return;
   size_t cells = (size_t)(s->hn[0] - 3) * (s->hn[1] - 3) * (s->hn[2] - 3);
   size_t bytes = cells * 16 * sizeof(float4);
   if (bytes > (size_t)2 << 30) return;
@@ -808,14 +836,19 @@ static int launch(nb_sim *s, const long long *dev_list, long long n_list) {
     return fail(s, NB_EINVAL,
                 "phi x mosaic and source tables exceed 200 KB of shared "
                 "memory");
-  cudaError_t e = s->d_stats.ensure(sizeof(unsigned long long));
-  if (e != cudaSuccess) return fail(s, NB_ENOMEM, "statistics counter");
-  e = cudaMemsetAsync(s->d_stats.p, 0, sizeof(unsigned long long), s->stream);
+  // counters: [0] evaluated terms, [1..3] the warp kernel's pairs,
+  // intervals and source blocks
+  cudaError_t e = s->d_stats.ensure(4 * sizeof(unsigned long long));
+  if (e != cudaSuccess) return fail(s, NB_ENOMEM, "statistics counters");
+  e = cudaMemsetAsync(s->d_stats.p, 0, 4 * sizeof(unsigned long long),
+                      s->stream);
   if (e != cudaSuccess) return cuda_fail(s, e, "statistics reset");
   a.stats = (unsigned long long *)s->d_stats.p;
+  a.wstats = s->count_work ? a.stats + 1 : nullptr;
   long long pix = dev_list ? n_list : s->npix;
   s->last_pixel_steps = pix * (long long)s->os * s->os * s->T * s->n_src *
                         s->n_mosaic * s->n_phi;
+  s->last_pixels = pix;
   // one warp per pixel pays off where the scattered terms are expensive
   // (tricubic lookups) and a pixel has enough items to fill the lanes
   bool auto_warp = a.interp == NB_INTERP_TRICUBIC &&
@@ -824,6 +857,8 @@ static int launch(nb_sim *s, const long long *dev_list, long long n_list) {
       s->precision == NB_MIXED && nbgb::split_supported(a) &&
       (s->variant == NB_VARIANT_WARP ||
        (s->variant == NB_VARIANT_AUTO && auto_warp));
+  s->last_warp = warp_variant && s->precision != NB_F64;
+  s->last_counted = s->count_work;
   if (s->precision == NB_F64) {
     e = nbgb::launch_spots_f64(a, s->stream);
   } else if (warp_variant) {
@@ -844,6 +879,7 @@ static int launch(nb_sim *s, const long long *dev_list, long long n_list) {
 }
 
 int nb_add_spots(nb_sim *s) {
+  nbgb::NvtxRange nvtx_("nb_add_spots");
   if (!s) return NB_EINVAL;
   DeviceGuard g(s->device);
   return launch(s, nullptr, 0);
@@ -851,6 +887,7 @@ int nb_add_spots(nb_sim *s) {
 
 int nb_add_spots_pixels(nb_sim *s, const long long *pixels,
                         long long n_pix) {
+  nbgb::NvtxRange nvtx_("nb_add_spots_pixels");
   if (!s) return NB_EINVAL;
   if (n_pix < 0 || (n_pix > 0 && !pixels))
     return fail(s, NB_EINVAL, "pixel list");
@@ -873,6 +910,7 @@ int nb_add_spots_pixels(nb_sim *s, const long long *pixels,
 }
 
 int nb_zero_image(nb_sim *s) {
+  nbgb::NvtxRange nvtx_("nb_zero_image");
   if (!s) return NB_EINVAL;
   if (!s->have_det) return fail(s, NB_ESTATE, "detector not set");
   DeviceGuard g(s->device);
@@ -890,6 +928,7 @@ __global__ void nb_to_f32_kernel(const double *src, float *dst, long long n) {
 
 int nb_get_image(nb_sim *s, void *dst, size_t n_elems, int dtype,
                  int on_device) {
+  nbgb::NvtxRange nvtx_("nb_get_image");
   if (!s) return NB_EINVAL;
   if (!dst) return fail(s, NB_EINVAL, "dst NULL");
   if (!s->have_det) return fail(s, NB_ESTATE, "detector not set");
@@ -931,6 +970,7 @@ const double *nb_image_device_ptr(const nb_sim *s) {
 
 int nb_adjoint(nb_sim *s, const double *dLdI, double grad[10],
                double *gradF) {
+  nbgb::NvtxRange nvtx_("nb_adjoint");
   if (!s) return NB_EINVAL;
   if (!dLdI || !grad) return fail(s, NB_EINVAL, "NULL dLdI / grad");
   if (!s->have_crystal || !s->have_beam || !s->have_det || !s->have_F)
@@ -969,6 +1009,7 @@ int nb_adjoint(nb_sim *s, const double *dLdI, double grad[10],
 
 int nb_poisson_loss(nb_sim *s, const double *y, double bkg, double *dLdI,
                     double *loss) {
+  nbgb::NvtxRange nvtx_("nb_poisson_loss");
   if (!s) return NB_EINVAL;
   if (!y || !dLdI || !loss) return fail(s, NB_EINVAL, "NULL argument");
   if (!s->have_det) return fail(s, NB_ESTATE, "detector not set");
@@ -998,11 +1039,17 @@ int nb_set_option(nb_sim *s, int key, long long value) {
     s->variant = (int)value;
     return NB_OK;
   }
+  if (key == NB_OPT_COUNT_WORK) {
+    if (value != 0 && value != 1) return fail(s, NB_EINVAL, "bad value");
+    s->count_work = value != 0;
+    return NB_OK;
+  }
   return fail(s, NB_EINVAL, "unknown option");
 }
 
 int nb_get_stats(nb_sim *s, long long *evaluated_terms,
                  long long *pixel_steps) {
+  nbgb::NvtxRange nvtx_("nb_get_stats");
   if (!s) return NB_EINVAL;
   if (!evaluated_terms || !pixel_steps)
     return fail(s, NB_EINVAL, "NULL output");
@@ -1019,8 +1066,46 @@ int nb_get_stats(nb_sim *s, long long *evaluated_terms,
   return NB_OK;
 }
 
+int nb_get_work(nb_sim *s, long long *counts, int n_counts) {
+  nbgb::NvtxRange nvtx_("nb_get_work");
+  if (!s) return NB_EINVAL;
+  if (!counts || n_counts < 1) return fail(s, NB_EINVAL, "NULL output");
+  long long v[NB_WORK_N] = {0};
+  v[NB_WORK_PIXEL_STEPS] = s->last_pixel_steps;
+  const long long units = s->last_pixels * (long long)s->os * s->os * s->T;
+  v[NB_WORK_UNITS] = units;
+  v[NB_WORK_ITEMS] = units * s->n_mosaic * s->n_phi;
+  if (s->d_stats.p) {
+    DeviceGuard g(s->device);
+    unsigned long long c[4] = {0, 0, 0, 0};
+    cudaError_t e = cudaMemcpyAsync(c, s->d_stats.p, sizeof c,
+                                    cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "statistics read");
+    if (s->precision == NB_F64) {
+      // every step is tested and evaluated
+      v[NB_WORK_PAIRS] = v[NB_WORK_TERMS] = s->last_pixel_steps;
+    } else {
+      v[NB_WORK_TERMS] = (long long)c[0];
+      if (!s->last_warp) {
+        // the thread-per-pixel kernels test every step
+        v[NB_WORK_PAIRS] = s->last_pixel_steps;
+      } else if (s->last_counted) {
+        v[NB_WORK_PAIRS] = (long long)c[1];
+        v[NB_WORK_INTERVALS] = (long long)c[2];
+        v[NB_WORK_BLOCKS] = (long long)c[3];
+      } else {
+        v[NB_WORK_PAIRS] = v[NB_WORK_INTERVALS] = v[NB_WORK_BLOCKS] = -1;
+      }
+    }
+  }
+  for (int i = 0; i < n_counts; ++i) counts[i] = i < NB_WORK_N ? v[i] : 0;
+  return NB_OK;
+}
+
 int nb_set_background(nb_sim *s, const double *stol, const double *F,
                       int n_knots, double n_molecules) {
+  nbgb::NvtxRange nvtx_("nb_set_background");
   if (!s) return NB_EINVAL;
   if (!stol || !F) return fail(s, NB_EINVAL, "NULL background table");
   if (n_knots < 2 || n_knots > nbgb::kMaxKnots)
@@ -1041,6 +1126,7 @@ int nb_set_background(nb_sim *s, const double *stol, const double *F,
 }
 
 int nb_add_background(nb_sim *s) {
+  nbgb::NvtxRange nvtx_("nb_add_background");
   if (!s) return NB_EINVAL;
   if (!s->have_beam || !s->have_det || !s->have_bg)
     return fail(s, NB_ESTATE,
@@ -1148,6 +1234,7 @@ int nb_add_background(nb_sim *s) {
 }
 
 int nb_synchronize(nb_sim *s) {
+  nbgb::NvtxRange nvtx_("nb_synchronize");
   if (!s) return NB_EINVAL;
   DeviceGuard g(s->device);
   cudaError_t e = cudaStreamSynchronize(s->stream);

@@ -13,11 +13,22 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <vector>
 
 namespace nbgb {
+
+// An NVTX range named after a C-ABI call, pushed for the call's duration:
+// profilers that attach an NVTX tool show the library's calls on the host
+// timeline (without a tool the push and pop cost a branch).
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 constexpr double kElectronRadius = 2.8179403262e-15;  // m, CODATA 2018
 constexpr int kTileF = 16;                            // pixels per tile, fast
@@ -104,6 +115,11 @@ struct SpotArgs {
   // statistics of the launch: [0] terms evaluated (the FP32 forms skip
   // Gaussian terms that underflow); null to skip counting
   unsigned long long *stats;
+  // work the warp-per-pixel kernel performs besides the terms: [0]
+  // (interval, source) pairs tested against the cut, [1] lattice-point
+  // intervals solved, [2] source blocks tested; null to skip counting (the
+  // kernel is then instantiated without the counters)
+  unsigned long long *wstats;
 };
 
 // host: v as a double-float pair, hi = v rounded to FP32, lo the rest

@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(kSplitThreads, 5)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int staged = -1;
   SplitBlock b;
-  unsigned long long evals = 0;
+  SplitCounts cnt;
   const int U = base.os * base.os * base.T;
   const int B = kMaxUnits / U;
   while (true) {
@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(kSplitThreads, 5)
       for (int bi = 0; bi < nb; ++bi) {
         const long long p = w.first + warp + (long long)(i0 + bi) * kSplitWarps;
         const double v = split_sum<INTERP, 0>(
-            base, b, unit + bi * U * kUnitFloats, evals);
+            base, b, unit + bi * U * kUnitFloats, cnt);
         if (lane == 0) pool[sp.img_off + p] = sp.prefactor * v;
       }
       __syncwarp();  // the next batch rewrites the units
@@ -339,6 +339,7 @@ int nb_server_create(nb_server **out, int device, void *cuda_stream,
                      double default_F, double Na, double Nb, double Nc,
                      const double dir[3], double fluence, double kahn_K,
                      const double e_vec[3]) {
+  nbgb::NvtxRange nvtx_("nb_server_create");
   if (!out) return NB_EINVAL;
   *out = nullptr;
   if (!panel || !F || !hkl_min || !hkl_n || !dir || !e_vec) return NB_EINVAL;
@@ -498,8 +499,11 @@ int nb_server_create(nb_server **out, int device, void *cuda_stream,
     cudaGetLastError();
     // the tricubic polynomial of every cell, as the stand-alone warp
     // kernel uses it (same results bit for bit)
+    // (not for an axis longer than 1000 nodes: the warp kernel packs a
+    // table index into 10 bits per axis)
     if (interp == NB_INTERP_TRICUBIC && hkl_n[0] >= 4 && hkl_n[1] >= 4 &&
-        hkl_n[2] >= 4) {
+        hkl_n[2] >= 4 && hkl_n[0] <= 1000 && hkl_n[1] <= 1000 &&
+        hkl_n[2] <= 1000) {
       size_t cells =
           (size_t)(hkl_n[0] - 3) * (hkl_n[1] - 3) * (hkl_n[2] - 3);
       if (cells * 16 * sizeof(float4) <= ((size_t)2 << 30) &&
@@ -596,6 +600,7 @@ int nb_server_submit(nb_server *s, const double axes[9], const double *umats,
                      const double *weights, int n_src, double scale,
                      int roi_f0, int roi_s0, int roi_nf, int roi_ns,
                      long long *request_id) {
+  nbgb::NvtxRange nvtx_("nb_server_submit");
   if (!s) return NB_EINVAL;
   if (!axes || !umats || !lambda_A || !weights || !request_id)
     return sfail(s, NB_EINVAL, "NULL argument");
@@ -719,6 +724,7 @@ static bool any_schedulable(const nb_server *s) {
 }
 
 int nb_server_step(nb_server *s, double timeout_s, int *n_active) {
+  nbgb::NvtxRange nvtx_("nb_server_step");
   if (!s) return NB_EINVAL;
   int prev = 0;
   cudaGetDevice(&prev);
@@ -839,6 +845,7 @@ int nb_server_state(nb_server *s, long long id, int *state) {
 
 int nb_server_result(nb_server *s, long long id, void *dst, size_t n_elems,
                      int dtype, int on_device) {
+  nbgb::NvtxRange nvtx_("nb_server_result");
   if (!s || !dst) return NB_EINVAL;
   auto it = s->reqs.find(id);
   if (it == s->reqs.end()) return sfail(s, NB_EINVAL, "unknown request");

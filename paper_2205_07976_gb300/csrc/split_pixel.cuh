@@ -30,8 +30,10 @@ struct SplitEntry {
   float4 a;  // G_hi h, G_hi k, r h, r k      (r = r_q, or r_q - (m - n0))
   float4 b;  // G_lo h, G_lo k, r_lo h, r_lo k
   float4 c;  // G_hi l, r l, G_lo l, r_lo l
-  float4 d;  // n0 h, n0 k, n0 l (floats) or m's table index (int bits), and
-             // omega cap pol of the unit
+  float4 d;  // n0 h, n0 k, n0 l (floats), or for m (int bits) its table
+             // index, or with tricubic cell polynomials ci0, the index
+             // packed (10 bits per axis, plus 1) and pk (entry_cell_data);
+             // and omega cap pol of the unit
   int4 m;    // first source, count, position of the first source in the
              // pixel's sequence of (entry, source) pairs,
              // pm | unit << 16 | interval entry << 31
@@ -64,29 +66,6 @@ __device__ __forceinline__ void ff_dot3_pairs(const float2 *A,
   lo = fmaf(a1.y, vh[1], lo);
   lo = fmaf(a2.y, vh[2], lo);
   fast_two_sum(s2, lo, gh, gl);
-}
-
-// Packed two-lane FP32 arithmetic (Blackwell's f32x2 instructions): one
-// instruction rounds each lane exactly as the scalar fmaf / add does.
-__device__ __forceinline__ unsigned long long pk2(float2 v) {
-  return (unsigned long long)__float_as_uint(v.x) |
-         ((unsigned long long)__float_as_uint(v.y) << 32);
-}
-__device__ __forceinline__ float2 upk2(unsigned long long v) {
-  return make_float2(__uint_as_float((unsigned)v),
-                     __uint_as_float((unsigned)(v >> 32)));
-}
-__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
-  unsigned long long d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;"
-      : "=l"(d)
-      : "l"(pk2(a)), "l"(pk2(b)), "l"(pk2(c)));
-  return upk2(d);
-}
-__device__ __forceinline__ float2 fadd2(float2 a, float2 b) {
-  unsigned long long d;
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk2(a)), "l"(pk2(b)));
-  return upk2(d);
 }
 
 // Per-warp cache of cell polynomials in shared memory.  The terms of one
@@ -134,69 +113,129 @@ __device__ __forceinline__ float cell_horner(const float4 *cp, int stride,
   return fmaf(fmaf(fmaf(q[1].y, x[0], q[1].x), x[0], q[0].y), x[0], q[0].x);
 }
 
+// The cell of a tricubic term: whether its 4x4x4 stencil lies inside the
+// table (tri), the cell's index in the polynomial table (ci), its parity
+// slot in the cache (par) and the coordinates x in [0, 1) within the cell.
+struct CellRef {
+  bool tri;
+  int ci, par;
+  float x[3];
+};
+
+// The cell of a step with fractional offset fr and table-relative nearest
+// index n: its stencil starts at fl - 1, fl = n - (fr < 0) per axis.
+template <int INTERP>
+__device__ __forceinline__ void cell_of(const SpotArgs &a, bool hit,
+                                        const float fr[3], const int n[3],
+                                        CellRef &c) {
+  int fl[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const int neg = fr[k] < 0.f;
+    fl[k] = n[k] - neg;
+    c.x[k] = neg ? 1.f + fr[k] : fr[k];
+  }
+  // the 4x4x4 stencil fl - 1 .. fl + 2 inside the table
+  c.tri = INTERP == 1 && hit && a.C4 &&
+          (unsigned)(fl[0] - 1) < (unsigned)(a.hn[0] - 3) &&
+          (unsigned)(fl[1] - 1) < (unsigned)(a.hn[1] - 3) &&
+          (unsigned)(fl[2] - 1) < (unsigned)(a.hn[2] - 3);
+  c.ci = 0;
+  c.par = 0;
+  if (c.tri) {
+    c.ci = ((fl[0] - 1) * (a.hn[1] - 3) + (fl[1] - 1)) * (a.hn[2] - 3) +
+           (fl[2] - 1);
+    c.par = (fl[0] & 1) | ((fl[1] & 1) << 1) | ((fl[2] & 1) << 2);
+  }
+}
+
+// Cell data of an interval entry's lattice point m (table-relative index
+// nt), computed once per entry: ci0 = the index of the cell whose stencil
+// starts at nt - 1; pk = the parity of nt (bits 0-2) and, in bits 3-10,
+// for each sign pattern s of a step's offset (bit k: f_k < 0, which moves
+// the stencil one node down along axis k) whether that stencil lies inside
+// the table.  A step's cell is then ci0 minus the strides its pattern
+// selects, with parity pk ^ s.
+__device__ __forceinline__ void entry_cell_data(const SpotArgs &a,
+                                                const int nt[3], int &ci0,
+                                                int &pk) {
+  const int H1 = a.hn[1] - 3, H2 = a.hn[2] - 3;
+  ci0 = ((nt[0] - 1) * H1 + (nt[1] - 1)) * H2 + (nt[2] - 1);
+  // sign pattern s has bit k set when axis k moves down
+  const unsigned pos_bits[3] = {0x55u, 0x33u, 0x0Fu};
+  unsigned ok = 0xFFu;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const unsigned span = (unsigned)(a.hn[k] - 3);
+    const bool up = (unsigned)(nt[k] - 1) < span;    // f_k >= 0
+    const bool down = (unsigned)(nt[k] - 2) < span;  // f_k < 0
+    ok &= (up ? pos_bits[k] : 0u) | (down ? (~pos_bits[k] & 0xFFu) : 0u);
+  }
+  pk = (nt[0] & 1) | ((nt[1] & 1) << 1) | ((nt[2] & 1) << 2) | (int)(ok << 3);
+}
+
+__device__ __forceinline__ void cell_of_entry(const SpotArgs &a, bool hit,
+                                              const float fr[3], int ci0,
+                                              int pk, CellRef &c) {
+  const int s = (fr[0] < 0.f) | ((fr[1] < 0.f) << 1) | ((fr[2] < 0.f) << 2);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) c.x[k] = fr[k] < 0.f ? 1.f + fr[k] : fr[k];
+  const int H2 = a.hn[2] - 3;
+  c.tri = hit && ((pk >> (3 + s)) & 1);
+  c.ci = ci0 - ((s & 1) ? (a.hn[1] - 3) * H2 : 0) - ((s & 2) ? H2 : 0) -
+         ((s >> 2) & 1);
+  c.par = (pk & 7) ^ s;
+}
+
 // The term F_cell^2 F_latt^2 w of a lane whose step survived the cut (`hit`),
-// given its fractional offset fr, table-relative nearest index n and
-// exponent sum rad2 = sum N^2 fr^2.  Called
+// given its fractional offset fr, table-relative nearest index n, cell c
+// and exponent sum rad2 = sum N^2 fr^2.  Called
 // by all 32 lanes of the warp: missing cells are loaded into the cache by
 // the whole warp (one coalesced 256-byte read per cell).  A lane whose
 // parity slot ends up holding another cell (two lattice points in one pass)
 // reads its cell from global memory instead.
 template <int INTERP>
 __device__ __forceinline__ float term_value(const SpotArgs &a, bool hit,
+                                            const CellRef &c,
                                             const float fr[3], const int n[3],
                                             float rad2, float w,
                                             float4 *cache, int *tags) {
   // fast exp: a few ulp for the significant terms (|argument| < ~20)
   const float fl2 = a.N6 * __expf(-2.f * rad2 * (1.f / 0.63f));
-  int fl[3];
-  float x[3];
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    const int neg = fr[c] < 0.f;
-    fl[c] = n[c] - neg;
-    x[c] = neg ? 1.f + fr[c] : fr[c];
-  }
-  // the 4x4x4 stencil fl - 1 .. fl + 2 inside the table
-  const bool tri = INTERP == 1 && hit && a.C4 &&
-                   (unsigned)(fl[0] - 1) < (unsigned)(a.hn[0] - 3) &&
-                   (unsigned)(fl[1] - 1) < (unsigned)(a.hn[1] - 3) &&
-                   (unsigned)(fl[2] - 1) < (unsigned)(a.hn[2] - 3);
-  int ci = 0, par = 0;
-  if (tri) {
-    ci = ((fl[0] - 1) * (a.hn[1] - 3) + (fl[1] - 1)) * (a.hn[2] - 3) +
-         (fl[2] - 1);
-    par = (fl[0] & 1) | ((fl[1] & 1) << 1) | ((fl[2] & 1) << 2);
-  }
   bool cached = false;
   if (INTERP == 1) {
     const int lane = threadIdx.x & 31;
-    unsigned handled = 0u;
-    unsigned miss = __ballot_sync(0xffffffffu, tri && tags[par] != ci);
-    while (miss) {
-      // load the cell of the first missing lane into its parity slot; each
-      // slot is loaded at most once per pass
-      const int src = __ffs(miss) - 1;
-      const int sp = __shfl_sync(0xffffffffu, par, src);
-      const int sci = __shfl_sync(0xffffffffu, ci, src);
-      const float2 v = __ldg(
-          reinterpret_cast<const float2 *>(a.C4 + (size_t)sci * kCellChunks) +
-          lane);
-      reinterpret_cast<float2 *>(
-          cache)[((lane >> 1) * kCellSlots + sp) * 2 + (lane & 1)] = v;
-      __syncwarp();
-      if (lane == 0) tags[sp] = sci;
-      __syncwarp();
-      handled |= 1u << sp;
-      miss = __ballot_sync(0xffffffffu,
-                           tri && !((handled >> par) & 1u) && tags[par] != ci);
+    unsigned miss = __ballot_sync(0xffffffffu, c.tri && tags[c.par] != c.ci);
+    if (miss == 0u) {
+      cached = c.tri;
+    } else {
+      unsigned handled = 0u;
+      while (miss) {
+        // load the cell of the first missing lane into its parity slot; each
+        // slot is loaded at most once per pass
+        const int src = __ffs(miss) - 1;
+        const int sp = __shfl_sync(0xffffffffu, c.par, src);
+        const int sci = __shfl_sync(0xffffffffu, c.ci, src);
+        const float2 v = __ldg(reinterpret_cast<const float2 *>(
+                                   a.C4 + (size_t)sci * kCellChunks) +
+                               lane);
+        reinterpret_cast<float2 *>(
+            cache)[((lane >> 1) * kCellSlots + sp) * 2 + (lane & 1)] = v;
+        __syncwarp();
+        if (lane == 0) tags[sp] = sci;
+        __syncwarp();
+        handled |= 1u << sp;
+        miss = __ballot_sync(0xffffffffu, c.tri && !((handled >> c.par) & 1u) &&
+                                              tags[c.par] != c.ci);
+      }
+      cached = c.tri && tags[c.par] == c.ci;
     }
-    cached = tri && tags[par] == ci;
   }
   float fc = 0.f;
   if (cached) {
-    fc = cell_horner<true>(cache + par, kCellSlots, x);
-  } else if (tri) {
-    fc = cell_horner<false>(a.C4 + (size_t)ci * kCellChunks, 1, x);
+    fc = cell_horner<true>(cache + c.par, kCellSlots, c.x);
+  } else if (c.tri) {
+    fc = cell_horner<false>(a.C4 + (size_t)c.ci * kCellChunks, 1, c.x);
   } else if (hit) {
     fc = fcell_f32<INTERP>(a, n, fr);
   }
@@ -405,6 +444,14 @@ __device__ __forceinline__ void split_unit(const SpotArgs &a,
   ud[6] = scal;
 }
 
+// Work one warp performed (warp-uniform counts), for the launch statistics
+struct SplitCounts {
+  unsigned long long terms = 0;   // terms evaluated
+  unsigned long long pairs = 0;   // (entry, source) pairs tested
+  unsigned long long ivals = 0;   // lattice-point intervals solved
+  unsigned long long blocks = 0;  // source blocks tested
+};
+
 // Per-warp queue of (entry, source) pairs: entries [e0, en) of the ring
 // are pending, pairs [ch, ct) of the pixel's sequence are not yet summed.
 struct PairQueue {
@@ -419,6 +466,8 @@ __device__ __forceinline__ void push_entries(
     const float Gh[3], const float r[3], const float Gl[3], const float rl[3],
     float4 d4) {
   const int lane = threadIdx.x & 31;
+  const unsigned hm = __ballot_sync(0xffffffffu, len > 0);
+  if (hm == 0u) return;
   int inc = len;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -426,8 +475,6 @@ __device__ __forceinline__ void push_entries(
     if (lane >= o) inc += t;
   }
   const int tot = __shfl_sync(0xffffffffu, inc, 31);
-  if (tot == 0) return;
-  const unsigned hm = __ballot_sync(0xffffffffu, len > 0);
   if (len > 0) {
     SplitEntry &E =
         ring[(pq.en + __popc(hm & ((1u << lane) - 1u))) & (kEntries - 1)];
@@ -490,9 +537,16 @@ __device__ __forceinline__ unsigned sum_pairs(
     fr[0] = f01.x;
     fr[1] = f01.y;
     fr[2] = fmaf(Gh[2], dh, r[2]) + fmaf(Gh[2], dlw.x, fmaf(Gl[2], dh, rl[2]));
-    n[0] = __float_as_int(D.x);
-    n[1] = __float_as_int(D.y);
-    n[2] = __float_as_int(D.z);
+    if (INTERP == 1 && a.C4) {
+      const int npk = __float_as_int(D.y);
+      n[0] = (npk & 1023) - 1;
+      n[1] = ((npk >> 10) & 1023) - 1;
+      n[2] = ((npk >> 20) & 1023) - 1;
+    } else {
+      n[0] = __float_as_int(D.x);
+      n[1] = __float_as_int(D.y);
+      n[2] = __float_as_int(D.z);
+    }
   } else {
     const float n0[3] = {D.x, D.y, D.z};
 #pragma unroll
@@ -537,7 +591,13 @@ __device__ __forceinline__ unsigned sum_pairs(
   }
   const unsigned hm = __ballot_sync(0xffffffffu, hit);
   if (hm != 0u) {
-    const float t = term_value<INTERP>(a, hit, fr, n, rad2, w, cache, tags);
+    CellRef cr;
+    if (INTERP == 1 && !HASDIV && a.C4 && (aux & kIntervalEntry))
+      cell_of_entry(a, hit, fr, __float_as_int(D.x), __float_as_int(D.z), cr);
+    else
+      cell_of<INTERP>(a, hit, fr, n, cr);
+    const float t =
+        term_value<INTERP>(a, hit, cr, fr, n, rad2, w, cache, tags);
     if (hit) acc.add(t);
   }
   pq.e0 += __popc(done);
@@ -548,13 +608,13 @@ __device__ __forceinline__ unsigned sum_pairs(
 
 // The sum, without the prefactor, of the pixel whose U sub-pixel units are
 // already in `unit` (split_unit), computed by the calling warp (all 32
-// lanes); every lane returns the same value.  Adds the number of evaluated
-// terms to `evals`.
-template <int INTERP, int HASDIV>
+// lanes); every lane returns the same value.  Adds the terms it evaluated
+// to `cnt` and, with COUNT, the rest of the work it performed.
+template <int INTERP, int HASDIV, int COUNT = 0>
 __device__ __forceinline__ double split_sum(const SpotArgs &a,
                                             const SplitBlock &b,
                                             const float *unit,
-                                            unsigned long long &evals) {
+                                            SplitCounts &cnt) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int PM = b.PM, S = b.S, nblk = b.nblk, sstep = b.sstep;
   const float2 *s_ax2 = b.ax2;
@@ -574,7 +634,7 @@ __device__ __forceinline__ double split_sum(const SpotArgs &a,
 
   Kahan acc;
   PairQueue pq;
-  unsigned nterms = 0;
+  unsigned nterms = 0, nivals = 0, nblocks = 0;
   auto drain = [&]() {
     while (pq.ct - pq.ch >= 32)
       nterms += sum_pairs<INTERP, HASDIV>(a, b, ring, pq, unit, cache, tags,
@@ -633,6 +693,7 @@ __device__ __forceinline__ double split_sum(const SpotArgs &a,
       // sweep is A d^2 + 2 B d + C, below cwide on one interval of the
       // sorted delta table
       const int maxc = (int)__reduce_max_sync(0xffffffffu, (unsigned)ncomb);
+      if (COUNT) nivals += __reduce_add_sync(0xffffffffu, (unsigned)ncomb);
       // the lattice points ml + (d0, d1, d2), d_x < nm_x, in odometer order
       int dg[3] = {0, 0, 0};
       for (int c = 0; c < maxc; ++c) {
@@ -690,16 +751,33 @@ __device__ __forceinline__ double split_sum(const SpotArgs &a,
             k2 = S;  // the sweep does not move: all or nothing
           }
         }
+        float4 d4;
+        if (INTERP == 1 && a.C4) {
+          // the lattice point's cell data once per entry; the index packed
+          // (clamped to [-1, hn]: any index outside the table looks up
+          // default_F, and cell tables exist only for hn < 1024)
+          int ci0 = 0, pk = 0, npk = 0;
+          if (c < ncomb) {
+            entry_cell_data(a, nt, ci0, pk);
+#pragma unroll
+            for (int x = 0; x < 3; ++x)
+              npk |= (min(max(nt[x], -1), a.hn[x]) + 1) << (10 * x);
+          }
+          d4 = make_float4(__int_as_float(ci0), __int_as_float(npk),
+                           __int_as_float(pk), scal);
+        } else {
+          d4 = make_float4(__int_as_float(nt[0]), __int_as_float(nt[1]),
+                           __int_as_float(nt[2]), scal);
+        }
         push_entries(ring, pq, k2 > k1 ? k2 - k1 : 0, k1,
-                     pm | (u << 16) | kIntervalEntry, Gh, dx, Gl, rl,
-                     make_float4(__int_as_float(nt[0]), __int_as_float(nt[1]),
-                                 __int_as_float(nt[2]), scal));
+                     pm | (u << 16) | kIntervalEntry, Gh, dx, Gl, rl, d4);
         drain();
       }
     } else {
       // pruned scan: h_x = G_x delta + r_x is linear in delta, so a block
       // of sources whose delta range [dmn, dmx] keeps some axis farther
       // than sqrt(cut)/N_x from every integer holds no surviving term
+      if (COUNT) nblocks += __popc(__ballot_sync(0xffffffffu, valid)) * nblk;
       for (int bb = 0; bb < nblk; ++bb) {
         bool pass = false;
         if (valid) {
@@ -724,7 +802,12 @@ __device__ __forceinline__ double split_sum(const SpotArgs &a,
   }
   if (pq.ct > pq.ch)
     nterms += sum_pairs<INTERP, HASDIV>(a, b, ring, pq, unit, cache, tags, acc);
-  evals += nterms;
+  cnt.terms += nterms;
+  if (COUNT) {
+    cnt.pairs += pq.ct;
+    cnt.ivals += nivals;
+    cnt.blocks += nblocks;
+  }
 
   // ---- warp reduction in float-float: each lane's compensated sum is
   // the pair (s, -c); pairs are added with error-free transformations (so

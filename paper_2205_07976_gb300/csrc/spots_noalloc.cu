@@ -133,6 +133,7 @@ extern "C" int nb_add_spots_noalloc(
     const int hkl_n[3], int interp, double default_F, const double *lambda_A,
     const double *weights, int n_src, const double dir[3], double fluence,
     double kahn_K, const double e_vec[3], double *image, void *cuda_stream) {
+  nbgb::NvtxRange nvtx_("nb_add_spots_noalloc");
   using namespace nbgb;
   // ---- argument checks (host values only)
   if (!panel || !axes_pm || !F || !hkl_min || !hkl_n || !lambda_A ||

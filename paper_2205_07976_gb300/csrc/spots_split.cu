@@ -34,7 +34,8 @@
 
 namespace nbgb {
 
-template <int INTERP, int HASDIV>
+// COUNT: also count the pairs, intervals and block tests (a.wstats)
+template <int INTERP, int HASDIV, int COUNT>
 __global__ void __launch_bounds__(kSplitThreads, 5)
     spots_split_kernel(SpotArgs a, unsigned long long *work) {
   extern __shared__ float sms[];
@@ -42,7 +43,7 @@ __global__ void __launch_bounds__(kSplitThreads, 5)
   split_stage(b, sms, a, a.axh, a.axl, a.src32, a.PM, a.S, a.u0h, a.u0l);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long n_work = a.pixlist ? a.n_list : a.npix;
-  unsigned long long evals = 0;  // terms evaluated by this warp
+  SplitCounts cnt;  // work of this warp
   // a warp takes B pixels at a time and sets up all their sub-pixel units
   // in one pass, so the FP64 geometry fills up to 32 lanes
   // (one pixel at a time when a warp gets few pixels: pixels differ in
@@ -67,18 +68,26 @@ __global__ void __launch_bounds__(kSplitThreads, 5)
       split_unit<HASDIV>(a, P, s, f, lane - bi * U, unit + lane * kUnitFloats);
     }
     __syncwarp();
+    double mine = 0.0;  // lane bi keeps the sum of pixel bi
     for (int bi = 0; bi < nb; ++bi) {
-      const double v = split_sum<INTERP, HASDIV>(
-          a, b, unit + bi * U * kUnitFloats, evals);
-      // fused accumulate into the image
-      if (lane == 0) {
-        const long long gp = a.pixlist ? a.pixlist[first + bi] : first + bi;
-        a.image[gp] += a.prefactor * v;
-      }
+      const double v = split_sum<INTERP, HASDIV, COUNT>(
+          a, b, unit + bi * U * kUnitFloats, cnt);
+      if (lane == bi) mine = v;
+    }
+    // fused accumulate into the image: lanes 0 .. nb-1 add the batch's
+    // pixels, consecutive in the image, in one coalesced access
+    if (lane < nb) {
+      const long long gp = a.pixlist ? a.pixlist[first + lane] : first + lane;
+      a.image[gp] += a.prefactor * mine;
     }
     __syncwarp();  // the next batch rewrites the units
   }
-  if (lane == 0 && a.stats && evals) atomicAdd(a.stats, evals);
+  if (lane == 0 && a.stats && cnt.terms) atomicAdd(a.stats, cnt.terms);
+  if (COUNT && lane == 0 && a.wstats) {
+    atomicAdd(a.wstats, cnt.pairs);
+    atomicAdd(a.wstats + 1, cnt.ivals);
+    atomicAdd(a.wstats + 2, cnt.blocks);
+  }
 }
 
 size_t split_smem_bytes(const SpotArgs &a) {
@@ -93,9 +102,17 @@ bool split_supported(const SpotArgs &a) {
 cudaError_t launch_spots_split(const SpotArgs &a, unsigned long long *work,
                                int sm_count, cudaStream_t st) {
   size_t smem = split_smem_bytes(a);
-  void (*kern)(SpotArgs, unsigned long long *) =
-      a.interp ? (a.has_div ? spots_split_kernel<1, 1> : spots_split_kernel<1, 0>)
-               : (a.has_div ? spots_split_kernel<0, 1> : spots_split_kernel<0, 0>);
+  void (*kern)(SpotArgs, unsigned long long *);
+  if (a.wstats)
+    kern = a.interp ? (a.has_div ? spots_split_kernel<1, 1, 1>
+                                 : spots_split_kernel<1, 0, 1>)
+                    : (a.has_div ? spots_split_kernel<0, 1, 1>
+                                 : spots_split_kernel<0, 0, 1>);
+  else
+    kern = a.interp ? (a.has_div ? spots_split_kernel<1, 1, 0>
+                                 : spots_split_kernel<1, 0, 0>)
+                    : (a.has_div ? spots_split_kernel<0, 1, 0>
+                                 : spots_split_kernel<0, 0, 0>);
   cudaError_t e = cudaFuncSetAttribute(
       kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

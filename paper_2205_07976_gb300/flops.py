@@ -48,6 +48,40 @@ def algorithmic_flops(shot, evaluated_terms: int, pixels: int = None) -> float:
                  + ITEM * items + UNIT * units)
 
 
+# Work the kernels perform (nb_get_work counts) rather than the method's
+# count.  The warp-per-pixel kernel does not visit every step: per item it
+# bounds the lattice points its source sweep can reach, solves one source
+# interval per lattice point (or tests 8-source blocks), and forms the
+# offset and the cut test only for the (interval, source) pairs inside:
+#   per pair tested: h and f (9) and the Gaussian exponent (8)          17
+#   per interval: A, B, C of the quadratic in delta (3 x 8), its
+#     discriminant, root and reciprocal (5), bounds and margins (8),
+#     the lattice point's offsets (3)                                    40
+#   per block test: per axis 2 FMAs, 2 margins, floor and ceil (3 x 6)   18
+#   per item: G, r (21) and the lattice range per axis (3 x 6)           39
+PAIR = STEP_HKL + STEP_GAUSS
+INTERVAL = 40
+BLOCK = 18
+ITEM_RANGE = 18
+
+
+def performed_flops(shot, work: dict) -> float:
+    """FP32 flops a launch performed, from the nb_get_work counts of that
+    launch (keys of nbgb.WORK_NAMES).  For the thread-per-pixel kernels
+    (every step tested, no intervals) this equals algorithmic_flops."""
+    per_term = TERM_ACCUM + (TERM_GAUSS if shot.shape == 1 else 0) + (
+        TERM_TRICUBIC if shot.interp == 1 else 0)
+    if work["intervals"] == 0 and work["blocks"] == 0:
+        per_pair = STEP_HKL + (STEP_GAUSS if shot.shape == 1 else STEP_SINC)
+        item = ITEM
+    else:
+        per_pair = PAIR
+        item = ITEM + ITEM_RANGE
+    return float(per_pair * work["pairs"] + INTERVAL * work["intervals"]
+                 + BLOCK * work["blocks"] + per_term * work["terms"]
+                 + item * work["items"] + UNIT * work["units"])
+
+
 def f64_flops(shot, pixels: int) -> float:
     """Flops of the plain FP64 form on `pixels` pixels of `shot`: the same
     count in FP64 arithmetic, with every step a term (NB_F64 skips none)."""

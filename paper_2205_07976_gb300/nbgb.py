@@ -23,6 +23,9 @@ NB_F64, NB_MIXED, NB_F32 = 0, 1, 2
 NB_DTYPE_F32, NB_DTYPE_F64 = 0, 1
 PRECISIONS = {"f64": NB_F64, "mixed": NB_MIXED, "f32": NB_F32}
 NB_OPT_VARIANT = 1
+NB_OPT_COUNT_WORK = 2
+WORK_NAMES = ("pixel_steps", "units", "items", "intervals", "blocks",
+              "pairs", "terms")
 VARIANTS = {"auto": 0, "thread": 1, "warp": 2}
 
 _LOCK = threading.Lock()
@@ -66,6 +69,8 @@ SIGNATURES = {
                                     ctypes.c_int]),
     "nb_image_device_ptr": (_vp, [_vp]),
     "nb_get_stats": (ctypes.c_int, [_vp, _llp, _llp]),
+    "nb_get_work": (ctypes.c_int, [_vp, _llp, ctypes.c_int]),
+    "nb_set_fcell_device": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t]),
     "nb_set_option": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_longlong]),
     "nb_set_crystal_params": (ctypes.c_int, [_vp, _dp, _dp, _dp, _dp,
                                              ctypes.c_double]),
@@ -234,6 +239,11 @@ class Sim:
         s.F = np.ascontiguousarray(F, dtype=np.float32)
         self.set_crystal(s)
 
+    def set_fcell_device(self, ptr: int, n: int):
+        """Replace the resident table's values from n float32 values at a
+        device pointer (stream-ordered device-to-device copy)."""
+        _check(self.lib.nb_set_fcell_device(self.h, _vp(ptr), int(n)), self.h)
+
     def set_shot(self, shot):
         self.shot = shot
         self.set_crystal(shot)
@@ -303,6 +313,19 @@ class Sim:
         _check(self.lib.nb_get_stats(self.h, ctypes.byref(ev),
                                      ctypes.byref(ps)), self.h)
         return int(ev.value), int(ps.value)
+
+    def count_work(self, on: bool = True):
+        """Make the following launches count the work work() reports."""
+        _check(self.lib.nb_set_option(self.h, NB_OPT_COUNT_WORK, int(on)),
+               self.h)
+        return self
+
+    def work(self):
+        """Work counts of the last add_spots call (nb_get_work), by name."""
+        v = (ctypes.c_longlong * len(WORK_NAMES))()
+        _check(self.lib.nb_get_work(self.h, ctypes.cast(v, _llp),
+                                    len(WORK_NAMES)), self.h)
+        return dict(zip(WORK_NAMES, [int(x) for x in v]))
 
     def synchronize(self):
         _check(self.lib.nb_synchronize(self.h), self.h)

@@ -180,6 +180,84 @@ def test_autograd_function_matches_adjoint(case):
     sim.close()
 
 
+def _params(th, device="cpu"):
+    return torch.tensor(np.concatenate([th["rot"], th["cell"], th["N"],
+                                        [th["scale"]]]),
+                        dtype=torch.float64, device=device,
+                        requires_grad=True)
+
+
+def test_autograd_keeps_F_on_the_device(case):
+    """A CUDA table is uploaded device to device, once: a second forward
+    with the same unchanged tensor uploads nothing, an in-place change
+    uploads again, and the gradients (on the devices of params and F) still
+    equal the adjoint's."""
+    from paper_2205_07976_gb300.autograd import bragg_image
+    shot, U, y, _ = case
+    dev = torch.device("cuda", 0)
+    sim = nbgb.Sim("mixed").set_shot(with_theta(shot, U, THETA))
+    params = _params(THETA, dev)
+    F = torch.from_numpy(shot.F.astype(np.float32)).to(dev).requires_grad_(
+        True)
+    yd = torch.from_numpy(y).to(dev)
+    bragg_image(params, F, sim, U)
+    assert sim.F_uploads == 1
+    img = bragg_image(params, F, sim, U)
+    assert sim.F_uploads == 1
+    loss = (img + BKG - yd * torch.log(img + BKG)).sum()
+    loss.backward()
+    assert sim.F_uploads == 1
+    assert params.grad.device == dev and F.grad.device == dev
+    L, g, gF, _ = gpu_grad(shot, U, y, THETA)
+    assert abs(loss.item() - L) <= 1e-9 * abs(L)
+    np.testing.assert_allclose(params.grad.cpu().numpy(), g, rtol=1e-8,
+                               atol=1e-12 * np.abs(g).max())
+    # F is float32, so autograd hands back its gradient in float32
+    assert F.grad.dtype == torch.float32
+    np.testing.assert_allclose(F.grad.cpu().numpy(), gF, rtol=1.2e-7,
+                               atol=1e-12 * np.abs(gF).max())
+    with torch.no_grad():
+        F.mul_(1.0)  # same values, new version
+    bragg_image(params, F, sim, U)
+    assert sim.F_uploads == 2
+    sim.close()
+
+
+def test_autograd_two_forwards_then_backward(case):
+    """Two forwards on one handle at different parameters and tables, then
+    the first one's backward: its gradient is the one at its own point."""
+    from paper_2205_07976_gb300.autograd import bragg_image
+    shot, U, y, _ = case
+    dev = torch.device("cuda", 0)
+    sim = nbgb.Sim("mixed").set_shot(with_theta(shot, U, THETA))
+    p1 = _params(THETA)
+    F1 = torch.from_numpy(shot.F.astype(np.float32)).to(dev).requires_grad_(
+        True)
+    th2 = dict(rot=THETA["rot"] * -1.5, cell=THETA["cell"] + 0.02,
+               N=THETA["N"] + 0.3, scale=0.9)
+    p2 = _params(th2)
+    F2 = (F1.detach() * 1.05).requires_grad_(True)
+    yd = torch.from_numpy(y).to(dev)
+    img1 = bragg_image(p1, F1, sim, U)
+    img2 = bragg_image(p2, F2, sim, U)
+    loss1 = (img1 + BKG - yd * torch.log(img1 + BKG)).sum()
+    loss1.backward()
+    L, g, gF, _ = gpu_grad(shot, U, y, THETA)
+    np.testing.assert_allclose(p1.grad.numpy(), g, rtol=1e-8,
+                               atol=1e-12 * np.abs(g).max())
+    np.testing.assert_allclose(F1.grad.cpu().numpy(), gF, rtol=1.2e-7,
+                               atol=1e-12 * np.abs(gF).max())
+    # and the second forward's image was its own
+    s2 = with_theta(shot, U, th2)
+    s2.F = (shot.F.astype(np.float32) * np.float32(1.05))
+    sim2 = nbgb.Sim("mixed").set_shot(s2)
+    sim2.set_params(U, th2["cell"], th2["rot"], th2["N"], th2["scale"])
+    sim2.add_spots()
+    np.testing.assert_array_equal(img2.detach().cpu().numpy(), sim2.image())
+    sim2.close()
+    sim.close()
+
+
 def test_adjoint_rejects_unsupported_setups():
     shot, U = grad_shot(1)
     sim = nbgb.Sim("mixed").set_shot(shot)

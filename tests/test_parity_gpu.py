@@ -218,6 +218,72 @@ def test_stats_count_evaluated_terms():
     assert abs(counts[0] - counts[1]) <= 1e-4 * counts[0]
 
 
+def test_work_counts_of_each_kernel():
+    """nb_get_work: the counts fixed by the shot, and the ordering of what
+    each kernel performed (terms <= pairs <= pixel-steps)."""
+    s = W.shrink(W.large_shot(), 24, 16, 2500, 700)
+    units = s.npix * s.oversample ** 2 * s.n_layers
+    for prec, variant in (("mixed", "thread"), ("mixed", "warp"),
+                          ("f64", "auto")):
+        sim = nbgb.Sim(prec).set_shot(s).set_variant(variant)
+        sim.add_spots()
+        if variant == "warp":
+            # counted only by the counting instantiation
+            w = sim.work()
+            assert w["pairs"] == w["intervals"] == w["blocks"] == -1
+            img = sim.image()
+            sim.count_work(True).zero()
+            sim.add_spots()
+            # which counts the same sum
+            assert np.array_equal(sim.image(), img)
+        w = sim.work()
+        ev, ps = sim.stats()
+        sim.close()
+        assert w["pixel_steps"] == ps == s.pixel_steps
+        assert w["units"] == units
+        assert w["items"] == units * s.n_mosaic * s.n_phi
+        if prec == "f64":
+            assert w["pairs"] == w["terms"] == ps
+            continue
+        assert w["terms"] == ev
+        if variant == "thread":
+            assert w["pairs"] == ps and w["intervals"] == w["blocks"] == 0
+        else:
+            # N = 25: the exact intervals apply (block tests only where an
+            # item's sweep reaches more than 8 lattice points); they skip
+            # most steps and keep every surviving term
+            assert w["intervals"] > 0
+            assert ev <= w["pairs"] < ps
+
+
+def test_fcell_device_upload_equals_host_upload():
+    """nb_set_fcell_device replaces the table's values from device memory:
+    the image equals the one with the same table given on the host, for the
+    nearest and the tricubic (cell polynomial) lookups; a wrong size is
+    rejected."""
+    torch = pytest.importorskip("torch")
+    for interp in (W.INTERP_NEAREST, W.INTERP_TRICUBIC):
+        s = W.shrink(W.large_shot(), 24, 16, 2500, 700)
+        s.interp = interp
+        F2 = (s.F * np.float32(1.25) + np.float32(3.0)).astype(np.float32)
+        t = s.copy()
+        t.F = F2
+        ref = nbgb.simulate(t, "mixed", variant="warp")
+        sim = nbgb.Sim("mixed").set_shot(s).set_variant("warp")
+        sim.add_spots()  # builds the derived tables of the first table
+        dF = torch.from_numpy(F2).cuda()
+        torch.cuda.synchronize()
+        sim.set_fcell_device(dF.data_ptr(), dF.numel())
+        sim.zero()
+        sim.add_spots()
+        got = sim.image()
+        with pytest.raises(nbgb.NbError) as e:
+            sim.set_fcell_device(dF.data_ptr(), dF.numel() - 1)
+        assert e.value.code == nbgb.NB_EINVAL
+        sim.close()
+        np.testing.assert_array_equal(got, ref)
+
+
 def test_single_pixel_and_empty_list():
     s = W.shrink(W.single_shot_small(), 1, 1, 200, 170)
     ref = oracle.image(s)
