@@ -467,8 +467,8 @@ def run_precision(args, local, stream, torch, np, nbgb, W):
                      "shot",
            "configs": {}}
 
-    def rel(got, ref, floor):
-        m = ref > floor * ref.max()
+    def rel(got, ref, floor, absolute=False):
+        m = ref > (floor if absolute else floor * ref.max())
         r = np.abs(got[m] - ref[m]) / ref[m]
         return float(r.max()), float(np.median(r)), int(m.sum())
 
@@ -511,12 +511,16 @@ def run_precision(args, local, stream, torch, np, nbgb, W):
                          "max_rel": e3[0], "median_rel": e3[1],
                          "pixels": e3[2]}
             if prec == "f64":
-                e6 = rel(got, ref, 1e-6)
-                row[prec]["max_rel_above_1e-6"] = e6[0]
+                row[prec]["max_rel_above_1e-6"] = rel(got, ref, 1e-6)[0]
+                # every pixel above 1e-250 photons (the FP64 gate)
+                row[prec]["max_rel_above_1e-250"] = rel(got, ref, 1e-250,
+                                                        True)[0]
         if shot.ncells[0] == 200:
             lit = oracle.image(shot, pixels=pix, sinc_mode="literal")
             row["oracle_literal_vs_reduced_max_rel_above_1e-6"] = rel(
                 lit, ref, 1e-6)[0]
+            row["oracle_literal_vs_reduced_max_rel_above_1e-250"] = rel(
+                lit, ref, 1e-250, True)[0]
         out["configs"][name] = row
     return out
 

@@ -3,6 +3,12 @@
 Every translation unit under csrc/ is compiled in parallel with nvcc and
 linked into paper_2205_07976_gb300/_build/libnbgb.so.  A stamp file keyed
 on the sources, flags and machine skips the rebuild when nothing changed.
+
+build(variant="check") makes the debug build libnbgb_check.so: the same
+sources with -DNB_CHECK=1, whose kernels check their table and image
+indexing and report a failed check through the call's status (see
+csrc/nbgb_internal.cuh).  nbgb.load() takes it when the environment
+variable NBGB_VARIANT is "check".
 """
 from __future__ import annotations
 
@@ -53,19 +59,33 @@ def _stamp(extra_flags) -> str:
     return h.hexdigest()
 
 
-def build(force: bool = False, extra_flags=(), verbose: bool = False) -> str:
-    """Build (if needed) and return the path of libnbgb.so."""
-    os.makedirs(BUILD, exist_ok=True)
-    stamp_file = os.path.join(BUILD, "libnbgb.stamp")
+VARIANTS = {"release": ("libnbgb.so", ()),
+            "check": ("libnbgb_check.so", ("-DNB_CHECK=1",))}
+
+
+def lib_path(variant: str = "release") -> str:
+    return os.path.join(BUILD, VARIANTS[variant][0])
+
+
+def build(force: bool = False, extra_flags=(), verbose: bool = False,
+          variant: str = "release") -> str:
+    """Build (if needed) and return the path of libnbgb.so (or of the
+    variant's library)."""
+    name, vflags = VARIANTS[variant]
+    lib = os.path.join(BUILD, name)
+    objdir = BUILD if variant == "release" else os.path.join(BUILD, variant)
+    os.makedirs(objdir, exist_ok=True)
+    extra_flags = tuple(vflags) + tuple(extra_flags)
+    stamp_file = os.path.join(BUILD, name[:-3] + ".stamp")
     stamp = _stamp(extra_flags)
-    if (not force and os.path.exists(LIB) and os.path.exists(stamp_file)
+    if (not force and os.path.exists(lib) and os.path.exists(stamp_file)
             and open(stamp_file).read() == stamp):
-        return LIB
+        return lib
     cc = nvcc()
     objs = []
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(objdir, os.path.basename(src)[:-3] + ".o")
         cmd = [cc, *ARCH, *FLAGS, *PER_FILE.get(os.path.basename(src), []),
                *extra_flags, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -77,15 +97,15 @@ def build(force: bool = False, extra_flags=(), verbose: bool = False) -> str:
 
     with concurrent.futures.ThreadPoolExecutor(max_workers=8) as ex:
         objs = list(ex.map(compile_one, _sources()))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [cc, *ARCH, "-shared", *objs, "-o", tmp, "-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib)
     with open(stamp_file, "w") as fh:
         fh.write(stamp)
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":

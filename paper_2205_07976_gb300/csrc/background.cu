@@ -119,6 +119,7 @@ __global__ void __launch_bounds__(kTileThreads)
         }
       }
   // addArray: the pixel's value is rounded first, then added (no FMA)
+  gp = nb_idx(a.check, NB_SITE_IMAGE, gp, a.npix);
   a.image[gp] = __dadd_rn(a.image[gp], __dmul_rn(b.prefactor, acc));
 }
 
@@ -275,6 +276,7 @@ __global__ void __launch_bounds__(kTileThreads)
         }
       }
   // addArray: the pixel's value is rounded first, then added (no FMA)
+  gp = nb_idx(a.check, NB_SITE_IMAGE, gp, a.npix);
   a.image[gp] = __dadd_rn(a.image[gp], __dmul_rn(b.prefactor, acc.value()));
 }
 

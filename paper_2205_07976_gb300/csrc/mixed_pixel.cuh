@@ -17,6 +17,8 @@ struct PixelView {
   float u0h, u0l;
 };
 
+// s_srcq: the sources' (delta on the grid qD, rest) pairs of the sinc fast
+// path in shared memory, or null.
 template <int SHAPE, int INTERP, int MODE, int HASDIV>
 __device__ __forceinline__ double mixed_pixel(const SpotArgs &a,
                                               const PixelView &v,
@@ -24,7 +26,8 @@ __device__ __forceinline__ double mixed_pixel(const SpotArgs &a,
                                               const float *s_axl,
                                               const float *s_src,
                                               const DevPanel &P, int s, int f,
-                                              unsigned &evals) {
+                                              unsigned &evals,
+                                              const float *s_srcq = nullptr) {
   const double px = P.px;
   const int os = a.os;
   const float kahn = a.kahn;
@@ -100,6 +103,84 @@ __device__ __forceinline__ double mixed_pixel(const SpotArgs &a,
               Gl[x] = 0.f;
               rh[x] = rl[x] = n0[x] = 0.f;
             }
+          }
+          // sinc in NB_MIXED, fast path: G rounded to the grid qG and
+          // delta to qD (qG qD = 2^-21, each with at most 11 and 12
+          // significant bits), r to the grid 2^-21.  Then G_q delta_q is
+          // exact in FP32, and so is G_q delta_q + (r_q - n): the offset
+          // of the step is that exact value plus the small terms
+          // G_rest delta_q + G_q delta_rest + G_rest delta_rest + r_rest
+          // (|.| < ~2e-3, good to ~1e-10), kept as a double-float pair.
+          // Taken per item when |G| < 2^11 qG on every axis, otherwise the
+          // general path below.
+          bool fastq = false;
+          float Gq[3], Gr[3], rq2[3], rr2[3];
+          if (MODE == 0 && SHAPE == 0 && !HASDIV && s_srcq) {
+            const float qG = a.sinc_qG, iqG = 1.f / qG;  // powers of 2
+            fastq = true;
+#pragma unroll
+            for (int x = 0; x < 3; ++x) {
+              fastq = fastq && fabsf(Gh[x]) < 2048.f * qG;
+              Gq[x] = __fmul_rn(rintf(__fmul_rn(Gh[x], iqG)), qG);
+              Gr[x] = __fsub_rn(Gh[x], Gq[x]) + Gl[x];
+              rq2[x] = __fmul_rn(rintf(__fmul_rn(rh[x], 2097152.f)),
+                                 1.f / 2097152.f);
+              rr2[x] = __fsub_rn(rh[x], rq2[x]) + rl[x];
+            }
+          }
+          if (fastq) {
+            float blk = 0.f;  // plain sum of up to 8 sources' terms
+            for (int k = 0; k < v.S; ++k) {
+              const float2 dq =
+                  reinterpret_cast<const float2 *>(s_srcq)[k];
+              float fh[3], fl[3];
+              int n[3];
+#pragma unroll
+              for (int x = 0; x < 3; ++x) {
+                const float nf = rintf(fmaf(Gq[x], dq.x, rq2[x]));
+                const float sx = fmaf(Gq[x], dq.x, __fsub_rn(rq2[x], nf));
+                const float lo =
+                    fmaf(Gr[x], dq.x, fmaf(Gq[x], dq.y, fmaf(Gr[x], dq.y,
+                                                             rr2[x])));
+                fh[x] = __fadd_rn(sx, lo);
+                fl[x] = __fsub_rn(lo, __fsub_rn(fh[x], sx));
+                // nf was rounded from the grid values, which differ from h
+                // by up to |lo|: for an offset beyond 1/2, n moves to h's
+                // nearest lattice point, as the table lookup needs (the
+                // sinc ratio is the same for f and f -+ 1 up to its sign;
+                // the tricubic cell coordinates move with n)
+                const int adj = (fh[x] > 0.5f) - (fh[x] < -0.5f);
+                if (INTERP == 1) fh[x] = __fsub_rn(fh[x], (float)adj);
+                n[x] = __float2int_rn(n0[x] + nf) - a.hmin[x] + adj;
+              }
+              const float2 yr2 =
+                  sinc_arg2(make_float2(a.N[0], a.N[1]),
+                            make_float2(fh[0], fh[1]),
+                            make_float2(fl[0], fl[1]));
+              float yzh, yze;
+              two_prod(a.N[2], fh[2], yzh, yze);
+              const float yzl = fmaf(a.N[2], fl[2], yze);
+              const float yzr = __fsub_rn(yzh, rintf(yzh)) + yzl;
+              const float2 nh = sinpi_reduced2_d4(yr2);
+              const float2 dk = sinpi_reduced2_d4(make_float2(fh[0], fh[1]));
+              const float2 sl = sinpi_reduced2_d4(make_float2(yzr, fh[2]));
+              const bool z0 = fabsf(fh[0]) < 1e-9f, z1 = fabsf(fh[1]) < 1e-9f,
+                         z2 = fabsf(fh[2]) < 1e-9f;
+              const float num = (z0 ? a.N[0] : nh.x) * (z1 ? a.N[1] : nh.y) *
+                                (z2 ? a.N[2] : sl.x);
+              const float den = (z0 ? 1.f : dk.x) * (z1 ? 1.f : dk.y) *
+                                (z2 ? 1.f : sl.y);
+              const float ratio = __fdividef(num, den);
+              ++evals;
+              const float fc = fcell_f32<INTERP>(a, n, fh);
+              blk += fc * fc * (ratio * ratio) * s_src[k * SRC32_STRIDE +
+                                                       SRC32_W];
+              if ((k & 7) == 7 || k == v.S - 1) {
+                acc.add(blk);
+                blk = 0.f;
+              }
+            }
+            continue;
           }
           if (MODE == 0 && SHAPE == 0 && !HASDIV) {
             // sinc in NB_MIXED: the h and k axes in packed two-lane FP32

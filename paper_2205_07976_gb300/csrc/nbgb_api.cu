@@ -85,7 +85,8 @@ struct nb_sim {
   double thick = 0, atten = 0;
   // device
   DevBuf d_panels, d_ax64, d_axh, d_axl, d_src64, d_src32, d_divh, d_divl,
-      d_F, d_image, d_list, d_tmp, d_stats, d_work;
+      d_F, d_image, d_list, d_tmp, d_stats, d_work, d_srcq, d_check;
+  float sinc_qG = 0.f;  // grid of G for the sinc fast path (0: off)
   int variant = NB_VARIANT_AUTO;
   int sm_count = 0;
   long long last_pixel_steps = 0, last_pixels = 0;
@@ -367,6 +368,28 @@ static int upload_tables(nb_sim *s) {
       r[nbgb::SRC64_B + c] = bp[c];
     }
   }
+  // sinc fast path (NB_MIXED, one direction): delta_k = u_k - u0 on the
+  // grid qD = 2^(e - 12), |delta| <= 2^e, so that delta / qD has at most
+  // 12 bits; the kernel rounds G to qG = 2^-21 / qD, so that the product
+  // of the two rounded values is exact in FP32 and lies on the 2^-21 grid
+  // of r (see mixed_pixel.cuh)
+  std::vector<float> srcq;
+  s->sinc_qG = 0.f;
+  if (s->precision == NB_MIXED && !s->has_div) {
+    double m = 0.0;
+    for (int k = 0; k < S; ++k)
+      m = std::max(m, std::fabs(1.0 / s->lam[k] - s->u0));
+    const int e = m > 0.0 ? (int)std::ceil(std::log2(m)) : -20;
+    const double qD = std::ldexp(1.0, e - 12);
+    srcq.resize((size_t)2 * S);
+    for (int k = 0; k < S; ++k) {
+      const double d = 1.0 / s->lam[k] - s->u0;
+      const double dq = std::nearbyint(d / qD) * qD;
+      srcq[2 * k] = (float)dq;  // exact: at most 13 bits on a power-of-2 grid
+      srcq[2 * k + 1] = (float)(d - dq);
+    }
+    s->sinc_qG = (float)std::ldexp(1.0, -21 - (e - 12));
+  }
   // divergence term E[pm][k][x] = A_pm,x . (i_k - i_0) u_k
   std::vector<float> divh, divl;
   if (s->has_div) {
@@ -402,6 +425,12 @@ static int upload_tables(nb_sim *s) {
                   cudaMemcpyHostToDevice, s->stream);
   cudaMemcpyAsync(s->d_src32.p, src32.data(), src32.size() * 4,
                   cudaMemcpyHostToDevice, s->stream);
+  if (!srcq.empty()) {
+    if ((e = s->d_srcq.ensure(srcq.size() * 4)) != cudaSuccess)
+      return fail(s, NB_ENOMEM, "source grid table");
+    cudaMemcpyAsync(s->d_srcq.p, srcq.data(), srcq.size() * 4,
+                    cudaMemcpyHostToDevice, s->stream);
+  }
   if (s->has_div) {
     if ((e = s->d_divh.ensure(divh.size() * 4)) != cudaSuccess ||
         (e = s->d_divl.ensure(divl.size() * 4)) != cudaSuccess)
@@ -476,17 +505,46 @@ static void fill_args(const nb_sim *s, SpotArgs &a) {
   a.has_div = s->has_div;
   a.divh = (const float *)s->d_divh.p;
   a.divl = (const float *)s->d_divl.p;
+  a.srcq = s->sinc_qG > 0.f ? (const float *)s->d_srcq.p : nullptr;
+  a.sinc_qG = a.srcq ? s->sinc_qG : 0.f;
   a.prefactor = nbgb::kElectronRadius * nbgb::kElectronRadius * s->fluence *
                 s->scale / ((double)s->os * s->os * s->n_mosaic * s->n_phi);
   a.image = (double *)s->d_image.p;
+  a.check = (unsigned long long *)s->d_check.p;  // NB_CHECK builds only
   nbgb::args_ff(a);
+}
+
+// NB_CHECK builds: waits for the handle's work and reports a failed bounds
+// check of its kernels (the site and index the first one recorded)
+static int read_check(nb_sim *s) {
+#if NB_CHECK
+  if (!s->d_check.p) return NB_OK;
+  unsigned long long w = 0;
+  cudaError_t e = cudaMemcpyAsync(&w, s->d_check.p, sizeof w,
+                                  cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e, "bounds-check read");
+  if (w) {
+    char msg[128];
+    std::snprintf(msg, sizeof msg, "bounds check failed: site %d index %lld",
+                  (int)((w >> 56) & 0x7f),
+                  (long long)(w & ((1ull << 56) - 1)));
+    cudaMemsetAsync(s->d_check.p, 0, sizeof w, s->stream);
+    return fail(s, NB_ECUDA, msg);
+  }
+#else
+  (void)s;
+#endif
+  return NB_OK;
 }
 
 // ------------------------------------------------------------------- ABI
 
 extern "C" {
 
-const char *nb_version(void) { return "nbgb 0.1 (sm_103a)"; }
+const char *nb_version(void) {
+  return NB_CHECK ? "nbgb 0.1 (sm_103a) +check" : "nbgb 0.1 (sm_103a)";
+}
 
 const char *nb_last_error(const nb_sim *sim) {
   if (!sim) return "null handle";
@@ -515,6 +573,20 @@ int nb_sim_create(nb_sim **out, int device, int precision,
     return NB_ECUDA;
   }
   s->stream = (cudaStream_t)cuda_stream;
+#if NB_CHECK
+  {
+    // the word a failed bounds check writes
+    DeviceGuard g(device);
+    if (s->d_check.ensure(sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMemset(s->d_check.p, 0, sizeof(unsigned long long)) !=
+            cudaSuccess) {
+      cudaGetLastError();
+      s->d_check.release();
+      delete s;
+      return NB_ENOMEM;
+    }
+  }
+#endif
   *out = s;
   return NB_OK;
 }
@@ -528,7 +600,7 @@ int nb_free(nb_sim *sim) {
                       &sim->d_axl,    &sim->d_src64, &sim->d_src32,
                       &sim->d_divh,   &sim->d_divl,  &sim->d_F,
                       &sim->d_image,  &sim->d_list,  &sim->d_tmp,
-                      &sim->d_stats,  &sim->d_work,  &sim->d_dax,
+                      &sim->d_stats,  &sim->d_work,  &sim->d_srcq,  &sim->d_check,  &sim->d_dax,
                       &sim->d_part,   &sim->d_grad,  &sim->d_F4,
                       &sim->d_C4,     &sim->d_bg64,  &sim->d_bg32,
                       &sim->d_bgrng};
@@ -831,7 +903,8 @@ static int launch(nb_sim *s, const long long *dev_list, long long n_list) {
   size_t smem_need =
       s->precision == NB_F64
           ? (size_t)(a.PM * 9 + a.S * nbgb::SRC64_STRIDE) * sizeof(double)
-          : (size_t)(2 * a.PM * 9 + a.S * nbgb::SRC32_STRIDE) * sizeof(float);
+          : (size_t)(2 * a.PM * 9 + a.S * (nbgb::SRC32_STRIDE + 2)) *
+                sizeof(float);
   if (smem_need > 200 * 1024)
     return fail(s, NB_EINVAL,
                 "phi x mosaic and source tables exceed 200 KB of shared "
@@ -875,7 +948,7 @@ static int launch(nb_sim *s, const long long *dev_list, long long n_list) {
     e = nbgb::launch_spots_mixed(a, s->precision, s->stream);
   }
   if (e != cudaSuccess) return cuda_fail(s, e, "spots launch");
-  return NB_OK;
+  return read_check(s);
 }
 
 int nb_add_spots(nb_sim *s) {
@@ -985,6 +1058,7 @@ int nb_adjoint(nb_sim *s, const double *dLdI, double grad[10],
   if (rc != NB_OK) return rc;
   if (s->has_div)
     return fail(s, NB_EINVAL, "the adjoint needs one source direction");
+  ensure_cell_polynomials(s);  // tricubic value and gradient per cell
   SpotArgs a;
   fill_args(s, a);
   if (nbgb::adjoint_smem_bytes(a, a.interp == NB_INTERP_TRICUBIC && gradF) >
@@ -998,13 +1072,13 @@ int nb_adjoint(nb_sim *s, const double *dLdI, double grad[10],
               ((double)s->os * s->os * s->n_mosaic * s->n_phi);
   e = nbgb::launch_adjoint(a, (const float *)s->d_dax.p, dLdI, gradF,
                            (double *)s->d_part.p, kc, s->scale,
-                           (double *)s->d_grad.p, s->stream);
+                           (double *)s->d_grad.p, s->sm_count, s->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(grad, s->d_grad.p, 10 * sizeof(double),
                         cudaMemcpyDeviceToHost, s->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
   if (e != cudaSuccess) return cuda_fail(s, e, "adjoint");
-  return NB_OK;
+  return read_check(s);
 }
 
 int nb_poisson_loss(nb_sim *s, const double *y, double bkg, double *dLdI,
@@ -1201,6 +1275,7 @@ int nb_add_background(nb_sim *s) {
   nbgb::BgArgs b;
   std::memset(&b, 0, sizeof b);
   SpotArgs &a = b.geo;
+  a.check = (unsigned long long *)s->d_check.p;  // NB_CHECK builds only
   a.panels = (const DevPanel *)s->d_panels.p;
   a.n_panels = (int)s->panels.size();
   a.n_tiles = s->n_tiles;
@@ -1230,7 +1305,7 @@ int nb_add_background(nb_sim *s) {
   e = nbgb::launch_background(b, f64, s->stream);
   if (e != cudaSuccess) return cuda_fail(s, e, "background launch");
   // the pageable copies above are staged before the launch returns
-  return NB_OK;
+  return read_check(s);
 }
 
 int nb_synchronize(nb_sim *s) {

@@ -18,7 +18,46 @@
 
 #include <vector>
 
+#ifndef NB_CHECK
+#define NB_CHECK 0
+#endif
+
 namespace nbgb {
+
+// Bounds checks of the kernels' table and image indexing, compiled in only
+// with -DNB_CHECK=1 (the debug build; `_build.build(variant="check")`).  A
+// failed check records its site and index in a device word (the first one
+// wins) and the access uses index 0 instead, so nothing faults; the host
+// reads the word after each launch and the call returns NB_ECUDA with the
+// site and index in nb_last_error.  Without NB_CHECK the index passes
+// through unchanged.
+enum {
+  NB_SITE_F = 1,        // structure-factor entry (nearest lookup)
+  NB_SITE_STENCIL = 2,  // last entry of a 4x4x4 tricubic stencil
+  NB_SITE_CELL = 3,     // cell polynomial
+  NB_SITE_IMAGE = 4,    // image pixel
+  NB_SITE_SOURCE = 5,   // source row
+  NB_SITE_GRADF = 6,    // structure-factor gradient entry
+  NB_SITE_KNOT = 7      // background knot
+};
+
+__device__ __forceinline__ long long nb_idx(unsigned long long *word, int site,
+                                           long long i, long long n) {
+#if NB_CHECK
+  if ((unsigned long long)i >= (unsigned long long)n) {
+    if (word)
+      atomicCAS(word, 0ull,
+                (1ull << 63) | ((unsigned long long)site << 56) |
+                    ((unsigned long long)i & ((1ull << 56) - 1)));
+    return 0;
+  }
+#else
+  (void)word;
+  (void)site;
+  (void)n;
+#endif
+  return i;
+}
 
 // An NVTX range named after a C-ABI call, pushed for the call's duration:
 // profilers that attach an NVTX tool show the library's calls on the host
@@ -110,6 +149,11 @@ struct SpotArgs {
   double kahn64;
   int has_div;
   const float *divh, *divl;
+  // sinc fast path of NB_MIXED: per source delta split on a fixed grid qD
+  // (srcq[S][2] = (delta on the grid, the rest)), and the grid qG of the
+  // items' G, with qG qD = 2^-21; sinc_qG = 0: no fast path
+  const float *srcq;
+  float sinc_qG;
   double prefactor;  // r_e^2 fluence scale / (os^2 M Phi)
   double *image;
   // statistics of the launch: [0] terms evaluated (the FP32 forms skip
@@ -120,7 +164,28 @@ struct SpotArgs {
   // intervals solved, [2] source blocks tested; null to skip counting (the
   // kernel is then instantiated without the counters)
   unsigned long long *wstats;
+  // NB_CHECK builds: the word a failed bounds check writes (null: none)
+  unsigned long long *check;
 };
+
+__device__ __forceinline__ long long table_size(const SpotArgs &a) {
+  return (long long)a.hn[0] * a.hn[1] * a.hn[2];
+}
+__device__ __forceinline__ long long cell_count(const SpotArgs &a) {
+  return (long long)(a.hn[0] - 3) * (a.hn[1] - 3) * (a.hn[2] - 3);
+}
+// offset in F of row (i, j) of the 4x4x4 stencil that starts at fl - 1
+// (its 4 entries checked in NB_CHECK builds)
+__device__ __forceinline__ long long stencil_row(const SpotArgs &a,
+                                                 const int fl[3], int i,
+                                                 int j) {
+  const long long off =
+      ((long long)(fl[0] - 1 + i) * a.hn[1] + (fl[1] - 1 + j)) * a.hn[2] +
+      (fl[2] - 1);
+  return nb_idx(a.check, NB_SITE_STENCIL, off + 3, table_size(a)) == off + 3
+             ? off
+             : 0;
+}
 
 // host: v as a double-float pair, hi = v rounded to FP32, lo the rest
 inline void split_ff_host(double v, float ff[2]) {
@@ -296,7 +361,7 @@ int loss_blocks(long long n);
 cudaError_t launch_adjoint(const SpotArgs &a, const float *dax,
                            const double *dLdI, double *gradF,
                            double *partials, double kc, double scale,
-                           double *grad_out, cudaStream_t st);
+                           double *grad_out, int sm_count, cudaStream_t st);
 cudaError_t launch_poisson_loss(const double *img, const double *y,
                                 long long n, double bkg, double *dLdI,
                                 double *partials, double *loss_out,

@@ -252,6 +252,12 @@ struct nb_server {
   int cur = 0;             // the buffer the next step is built in
   long long step_counter = 0;
   cudaStream_t copy_stream = nullptr;  // result copies
+  // steps built in buffer b run on stream_of(b): consecutive steps overlap,
+  // so the tail of one step's persistent kernels is filled by the next;
+  // up_ev[b] marks the slot uploads made for a step on its stream, which
+  // the next step (on the other stream) waits for
+  cudaStream_t stream2 = nullptr;
+  cudaEvent_t up_ev[2] = {nullptr, nullptr};
   // host bookkeeping
   long long next_id = 1;
   std::deque<long long> queue;
@@ -295,33 +301,39 @@ static void pool_free(nb_server *s, long long off, long long n) {
   }
 }
 
-// The graph of one step from host buffer b: work lists to the device (one
-// device copy serves both buffers: steps run in stream order), counters
-// reset, the two persistent kernels.
+static cudaStream_t stream_of(const nb_server *s, int b) {
+  return b == 0 ? s->stream : s->stream2;
+}
+
+// The graph of one step from host buffer b, on stream_of(b): its work
+// lists to its own device copies, its counters reset, the two persistent
+// kernels.
 static int build_graph(nb_server *s, int b) {
-  cudaError_t e = cudaStreamBeginCapture(s->stream,
-                                         cudaStreamCaptureModeThreadLocal);
+  cudaStream_t st = stream_of(s, b);
+  cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return sfail(s, NB_ECUDA, "graph capture begin");
-  cudaMemcpyAsync(s->d_work.p, s->h_work[b], sizeof(WorkList),
-                  cudaMemcpyHostToDevice, s->stream);
-  cudaMemcpyAsync(s->d_work_w.p, s->h_work_w[b], sizeof(WorkList),
-                  cudaMemcpyHostToDevice, s->stream);
-  cudaMemsetAsync(s->d_counter.p, 0, 2 * sizeof(unsigned), s->stream);
+  WorkList *dw = (WorkList *)s->d_work.p + b;
+  WorkList *dww = (WorkList *)s->d_work_w.p + b;
+  unsigned *ctr = (unsigned *)s->d_counter.p + 2 * b;
+  cudaMemcpyAsync(dw, s->h_work[b], sizeof(WorkList), cudaMemcpyHostToDevice,
+                  st);
+  cudaMemcpyAsync(dww, s->h_work_w[b], sizeof(WorkList),
+                  cudaMemcpyHostToDevice, st);
+  cudaMemsetAsync(ctr, 0, 2 * sizeof(unsigned), st);
   void (*kern)(nbgb::SpotArgs, const SlotParams *, const WorkList *,
                unsigned *, double *) =
       s->interp ? nbgb::serve_kernel<1> : nbgb::serve_kernel<0>;
-  kern<<<s->blocks, nbgb::kTileThreads, 0, s->stream>>>(
-      s->base, (const SlotParams *)s->d_slots.p, (const WorkList *)s->d_work.p,
-      (unsigned *)s->d_counter.p, (double *)s->d_pool.p);
+  kern<<<s->blocks, nbgb::kTileThreads, 0, st>>>(
+      s->base, (const SlotParams *)s->d_slots.p, dw, ctr,
+      (double *)s->d_pool.p);
   if (s->interp == NB_INTERP_TRICUBIC) {
     nbgb::serve_warp_kernel<1><<<s->blocks_w, nbgb::kSplitThreads, s->smem_w,
-                                 s->stream>>>(
-        s->base, (const SlotParams *)s->d_slots.p,
-        (const WorkList *)s->d_work_w.p, (unsigned *)s->d_counter.p + 1,
+                                 st>>>(
+        s->base, (const SlotParams *)s->d_slots.p, dww, ctr + 1,
         (double *)s->d_pool.p);
   }
   cudaGraph_t g = nullptr;
-  e = cudaStreamEndCapture(s->stream, &g);
+  e = cudaStreamEndCapture(st, &g);
   if (e != cudaSuccess) return sfail(s, NB_ECUDA, "graph capture end");
   e = cudaGraphInstantiate(&s->graph[b], g, 0);
   cudaGraphDestroy(g);
@@ -416,9 +428,9 @@ int nb_server_create(nb_server **out, int device, void *cuda_stream,
             cudaSuccess ||
         s->d_pool.alloc((size_t)s->pool_elems * sizeof(double)) !=
             cudaSuccess ||
-        s->d_work.alloc(sizeof(WorkList)) != cudaSuccess ||
-        s->d_work_w.alloc(sizeof(WorkList)) != cudaSuccess ||
-        s->d_counter.alloc(2 * sizeof(unsigned)) != cudaSuccess ||
+        s->d_work.alloc(2 * sizeof(WorkList)) != cudaSuccess ||
+        s->d_work_w.alloc(2 * sizeof(WorkList)) != cudaSuccess ||
+        s->d_counter.alloc(4 * sizeof(unsigned)) != cudaSuccess ||
         cudaHostAlloc((void **)&s->h_work[0], sizeof(WorkList),
                       cudaHostAllocDefault) != cudaSuccess ||
         cudaHostAlloc((void **)&s->h_work_w[0], sizeof(WorkList),
@@ -543,6 +555,12 @@ int nb_server_create(nb_server **out, int device, void *cuda_stream,
         cudaEventCreateWithFlags(&s->done_ev[1], cudaEventDisableTiming) !=
             cudaSuccess ||
         cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking) !=
+            cudaSuccess ||
+        cudaStreamCreateWithFlags(&s->stream2, cudaStreamNonBlocking) !=
+            cudaSuccess ||
+        cudaEventCreateWithFlags(&s->up_ev[0], cudaEventDisableTiming) !=
+            cudaSuccess ||
+        cudaEventCreateWithFlags(&s->up_ev[1], cudaEventDisableTiming) !=
             cudaSuccess) {
       rc = NB_ECUDA;
       break;
@@ -566,6 +584,10 @@ int nb_server_free(nb_server *s) {
   cudaGetDevice(&prev);
   cudaSetDevice(s->device);
   if (s->stream) cudaStreamSynchronize(s->stream);
+  if (s->stream2) {
+    cudaStreamSynchronize(s->stream2);
+    cudaStreamDestroy(s->stream2);
+  }
   if (s->copy_stream) {
     cudaStreamSynchronize(s->copy_stream);
     cudaStreamDestroy(s->copy_stream);
@@ -573,6 +595,7 @@ int nb_server_free(nb_server *s) {
   for (int b = 0; b < 2; ++b) {
     if (s->graph[b]) cudaGraphExecDestroy(s->graph[b]);
     if (s->done_ev[b]) cudaEventDestroy(s->done_ev[b]);
+    if (s->up_ev[b]) cudaEventDestroy(s->up_ev[b]);
     if (s->h_work[b]) cudaFreeHost(s->h_work[b]);
     if (s->h_work_w[b]) cudaFreeHost(s->h_work_w[b]);
   }
@@ -680,7 +703,8 @@ static int admit(nb_server *s) {
     r.state = NB_REQ_RUNNING;
     cudaError_t e = cudaMemcpyAsync((SlotParams *)s->d_slots.p + r.slot,
                                     &r.params, sizeof(SlotParams),
-                                    cudaMemcpyHostToDevice, s->stream);
+                                    cudaMemcpyHostToDevice,
+                                    stream_of(s, s->cur));
     if (e != cudaSuccess) return sfail(s, NB_ECUDA, "slot upload");
     it = s->queue.erase(it);
   }
@@ -782,8 +806,13 @@ int nb_server_step(nb_server *s, double timeout_s, int *n_active) {
     ww->n = nw;
     if (nt + nw > 0) {
       const int b = s->cur;
-      cudaError_t e = cudaGraphLaunch(s->graph[b], s->stream);
-      if (e == cudaSuccess) e = cudaEventRecord(s->done_ev[b], s->stream);
+      cudaStream_t st = stream_of(s, b);
+      // this step's slot uploads are on st; those of the previous build
+      // are on the other stream: wait for them (not for its kernels)
+      cudaError_t e = cudaEventRecord(s->up_ev[b], st);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(st, s->up_ev[b ^ 1], 0);
+      if (e == cudaSuccess) e = cudaGraphLaunch(s->graph[b], st);
+      if (e == cudaSuccess) e = cudaEventRecord(s->done_ev[b], st);
       if (e != cudaSuccess) {
         for (size_t j = 0; j < act.size(); ++j) act[j]->next = next0[j];
         rc = sfail(s, NB_ECUDA, "graph launch");

@@ -216,9 +216,12 @@ __device__ __forceinline__ float term_value(const SpotArgs &a, bool hit,
         const int src = __ffs(miss) - 1;
         const int sp = __shfl_sync(0xffffffffu, c.par, src);
         const int sci = __shfl_sync(0xffffffffu, c.ci, src);
-        const float2 v = __ldg(reinterpret_cast<const float2 *>(
-                                   a.C4 + (size_t)sci * kCellChunks) +
-                               lane);
+        const float2 v = __ldg(
+            reinterpret_cast<const float2 *>(
+                a.C4 + (size_t)nb_idx(a.check, NB_SITE_CELL, sci,
+                                      cell_count(a)) *
+                           kCellChunks) +
+            lane);
         reinterpret_cast<float2 *>(
             cache)[((lane >> 1) * kCellSlots + sp) * 2 + (lane & 1)] = v;
         __syncwarp();
@@ -235,7 +238,10 @@ __device__ __forceinline__ float term_value(const SpotArgs &a, bool hit,
   if (cached) {
     fc = cell_horner<true>(cache + c.par, kCellSlots, c.x);
   } else if (c.tri) {
-    fc = cell_horner<false>(a.C4 + (size_t)c.ci * kCellChunks, 1, c.x);
+    fc = cell_horner<false>(
+        a.C4 + (size_t)nb_idx(a.check, NB_SITE_CELL, c.ci, cell_count(a)) *
+                   kCellChunks,
+        1, c.x);
   } else if (hit) {
     fc = fcell_f32<INTERP>(a, n, fr);
   }
@@ -514,7 +520,10 @@ __device__ __forceinline__ unsigned sum_pairs(
   const unsigned done =
       __ballot_sync(0xffffffffu, ov && mm.z + mm.y <= pq.ch + np);
   const bool valid = lane < np;
-  const int k = valid ? k1 + (pq.ch + lane - pos) : 0;
+  const int k =
+      valid ? (int)nb_idx(a.check, NB_SITE_SOURCE, k1 + (pq.ch + lane - pos),
+                          b.S)
+            : 0;
   const SplitEntry &E = ring[(pq.e0 + j) & (kEntries - 1)];
   const float4 A = E.a, B = E.b, C = E.c, D = E.d;
   const float Gh[3] = {A.x, A.y, C.x}, r[3] = {A.z, A.w, C.y};

@@ -71,11 +71,18 @@ __device__ __forceinline__ double fcell_f64(const SpotArgs &a,
         w[c][3] = (t + 1.0) * t * (t - 1.0) / 6.0;
       }
       double sum = 0.0;
+      long long off =
+          ((long long)(fl[0] - 1) * a.hn[1] + (fl[1] - 1)) * a.hn[2] +
+          (fl[2] - 1);
+      {
+        const long long last = off + (3ll * a.hn[1] + 3) * a.hn[2] + 3;
+        if (nb_idx(a.check, NB_SITE_STENCIL, last, table_size(a)) != last)
+          off = 0;
+      }
       for (int i = 0; i < 4; ++i)
         for (int j = 0; j < 4; ++j) {
           const float *row =
-              a.F + ((fl[0] - 1 + i) * a.hn[1] + (fl[1] - 1 + j)) * a.hn[2] +
-              (fl[2] - 1);
+              a.F + off + ((long long)i * a.hn[1] + j) * a.hn[2];
 #pragma unroll
           for (int k = 0; k < 4; ++k)
             sum += w[0][i] * w[1][j] * w[2][k] * (double)__ldg(row + k);
@@ -86,7 +93,9 @@ __device__ __forceinline__ double fcell_f64(const SpotArgs &a,
   long long i = (long long)n[0] - a.hmin[0], j = (long long)n[1] - a.hmin[1],
             k = (long long)n[2] - a.hmin[2];
   if (in_table(a, i, j, k))
-    return (double)__ldg(a.F + (i * a.hn[1] + j) * a.hn[2] + k);
+    return (double)__ldg(a.F + nb_idx(a.check, NB_SITE_F,
+                                      (i * a.hn[1] + j) * a.hn[2] + k,
+                                      table_size(a)));
   return a.defF64;
 }
 
@@ -153,7 +162,7 @@ __global__ void __launch_bounds__(kTileThreads, 4)
       }
     }
   }
-  a.image[gp] += a.prefactor * acc;
+  a.image[nb_idx(a.check, NB_SITE_IMAGE, gp, a.npix)] += a.prefactor * acc;
 }
 
 cudaError_t launch_spots_f64(const SpotArgs &a, cudaStream_t st) {

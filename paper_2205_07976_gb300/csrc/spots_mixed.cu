@@ -34,6 +34,13 @@ __global__ void __launch_bounds__(kTileThreads, 4)
   }
   for (int i = threadIdx.x; i < a.S * SRC32_STRIDE; i += blockDim.x)
     s_src[i] = a.src32[i];
+  // the sinc fast path's grid table after the source rows
+  float *s_srcq = nullptr;
+  if (SHAPE == 0 && MODE == 0 && !HASDIV && a.srcq) {
+    s_srcq = s_src + a.S * SRC32_STRIDE;
+    for (int i = threadIdx.x; i < 2 * a.S; i += blockDim.x)
+      s_srcq[i] = a.srcq[i];
+  }
   __syncthreads();
 
   long long item = a.pixlist ? (long long)blockIdx.x * blockDim.x + threadIdx.x
@@ -45,8 +52,8 @@ __global__ void __launch_bounds__(kTileThreads, 4)
   const PixelView v{a.PM, a.S, a.u0h, a.u0l};
   unsigned evals = 0;  // terms evaluated (not skipped by the underflow cut)
   double total = mixed_pixel<SHAPE, INTERP, MODE, HASDIV>(
-      a, v, s_axh, s_axl, s_src, P, s, f, evals);
-  a.image[gp] += a.prefactor * total;
+      a, v, s_axh, s_axl, s_src, P, s, f, evals, s_srcq);
+  a.image[nb_idx(a.check, NB_SITE_IMAGE, gp, a.npix)] += a.prefactor * total;
   if (a.stats) warp_count(a.stats, evals);
 }
 
@@ -157,7 +164,9 @@ cudaError_t build_cell_polynomials(const float *F, const int hn[3], float4 *C4,
 
 cudaError_t launch_spots_mixed(const SpotArgs &a, int precision,
                                cudaStream_t st) {
-  size_t smem = (size_t)(2 * a.PM * 9 + a.S * SRC32_STRIDE) * sizeof(float);
+  size_t smem = (size_t)(2 * a.PM * 9 + a.S * SRC32_STRIDE +
+                         (a.srcq ? 2 * a.S : 0)) *
+                sizeof(float);
   long long blocks = a.pixlist ? (a.n_list + kTileThreads - 1) / kTileThreads
                                : a.n_tiles;
   if (blocks <= 0) return cudaSuccess;

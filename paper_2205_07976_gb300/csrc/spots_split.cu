@@ -78,7 +78,8 @@ __global__ void __launch_bounds__(kSplitThreads, 5)
     // pixels, consecutive in the image, in one coalesced access
     if (lane < nb) {
       const long long gp = a.pixlist ? a.pixlist[first + lane] : first + lane;
-      a.image[gp] += a.prefactor * mine;
+      a.image[nb_idx(a.check, NB_SITE_IMAGE, gp, a.npix)] +=
+          a.prefactor * mine;
     }
     __syncwarp();  // the next batch rewrites the units
   }

@@ -112,8 +112,14 @@ SIGNATURES = {
 }
 
 
+def variant() -> str:
+    """The library build to load: "release", or "check" (the bounds-checked
+    debug build) when the environment variable NBGB_VARIANT says so."""
+    return os.environ.get("NBGB_VARIANT", "release")
+
+
 def library_path() -> str:
-    return _build.LIB
+    return _build.lib_path(variant())
 
 
 def load(build: bool = True):
@@ -121,7 +127,8 @@ def load(build: bool = True):
     global _LIB
     with _LOCK:
         if _LIB is None:
-            path = _build.build() if build else _build.LIB
+            path = (_build.build(variant=variant()) if build
+                    else _build.lib_path(variant()))
             if not os.path.exists(path):
                 raise RuntimeError(f"libnbgb.so not found at {path}")
             lib = ctypes.CDLL(path)

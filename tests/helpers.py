@@ -11,6 +11,16 @@ def masked_rel_err(got, ref, floor_frac):
     return float(np.max(np.abs(got[m] - ref[m]) / ref[m])), int(m.sum())
 
 
+def rel_err_above(got, ref, floor_abs):
+    """max |got - ref| / ref over pixels with ref > floor_abs (absolute)."""
+    got = np.asarray(got, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    m = ref > floor_abs
+    if not m.any():
+        return 0.0, 0
+    return float(np.max(np.abs(got[m] - ref[m]) / ref[m])), int(m.sum())
+
+
 def abs_err_frac(got, ref):
     """max |got - ref| over all pixels, as a fraction of max(ref)."""
     got = np.asarray(got, dtype=np.float64)

@@ -65,3 +65,18 @@ def test_create_without_gpu_fails_cleanly():
     rc = lib.nb_fp64_peak_tflops(0, ctypes.byref(x))
     assert rc in (nbgb.NB_ECUDA, nbgb.NB_EINVAL)
     assert x.value == 0.0
+
+
+def test_bounds_checked_build_exports_the_same_symbols():
+    """The debug build (-DNB_CHECK=1) compiles, exports every declared
+    symbol and says so in its version string."""
+    path = _build.build(variant="check")
+    assert path != _build.lib_path("release")
+    lib = ctypes.CDLL(path)
+    for name in sorted(declared_symbols()):
+        assert hasattr(lib, name), name
+    lib.nb_version.restype = ctypes.c_char_p
+    assert lib.nb_version().decode().endswith("+check")
+    rel = ctypes.CDLL(_build.lib_path("release"))
+    rel.nb_version.restype = ctypes.c_char_p
+    assert not rel.nb_version().decode().endswith("+check")

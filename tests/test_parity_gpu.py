@@ -1,8 +1,9 @@
 """GPU images vs the FP64 CPU oracle, element by element, through the C ABI.
 
 Tolerances (max relative error per pixel):
-  NB_F64    1e-12 on pixels above 1e-6 of the image maximum, and 1e-12 of
-            the maximum in absolute terms everywhere;
+  NB_F64    1e-12 on every pixel above 1e-250 photons (no floor relative
+            to the maximum), and 1e-12 of the maximum in absolute terms
+            everywhere;
   NB_MIXED  1e-5 on pixels above 1e-3 of the image maximum;
   NB_F32    reported only (the precision sweep's naive arm).
 Windows are chosen with odd sizes so that every launch has ragged 16x8
@@ -14,7 +15,7 @@ import pytest
 import oracle
 from paper_2205_07976_gb300 import nbgb
 from paper_2205_07976_gb300 import workloads as W
-from tests.helpers import abs_err_frac, masked_rel_err
+from tests.helpers import abs_err_frac, masked_rel_err, rel_err_above
 
 pytestmark = pytest.mark.gpu
 
@@ -22,8 +23,14 @@ F64_TOL = 1e-12
 MIXED_TOL = 1e-5
 
 
+# Relative error is taken on every pixel above 1e-250 photons: far below
+# any intensity, but above the range where a sum of terms of exp(-700)
+# and less depends on how each libm rounds into the subnormal doubles
+F64_FLOOR = 1e-250
+
+
 def check_f64(got, ref):
-    rel, n = masked_rel_err(got, ref, 1e-6)
+    rel, n = rel_err_above(got, ref, F64_FLOOR)
     assert rel <= F64_TOL, (rel, n)
     assert abs_err_frac(got, ref) <= F64_TOL
 
@@ -94,10 +101,9 @@ def test_large_shot_window_mixed(c1win, variant):
 def test_precision_window(N):
     s = W.shrink(W.precision_shot(N), 45, 35, 600, 640)
     ref = oracle.image(s)
-    f64 = run(s, "f64")
-    rel, _ = masked_rel_err(f64, ref, 1e-6)
-    # the sinc's phase pi N f carries the FP64 rounding of h times N
-    assert rel <= (F64_TOL if N <= 50 else 1e-10), rel
+    # FP64 within 1e-12 on every pixel at every N: the kernel forms the
+    # fractional offset before the sinc, as the oracle's reduced form does
+    check_f64(run(s, "f64"), ref)
     check_mixed(run(s, "mixed"), ref)
     assert np.isfinite(run(s, "f32")).all()
 
