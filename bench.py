@@ -50,14 +50,15 @@ WORKLOAD = ("large shot 3072x3072, oversample 2, 2 layers (0.5 mm, atten "
 FP32_LANES_PER_SM = 128
 MAX_SM_MHZ = 2070.0  # GB300's maximum SM clock
 # DRAM bytes (read + write) of one full-size launch of the warp-per-pixel
-# kernel, from one ncu capture (profiles/spots_split_large_shot_dram.txt);
+# kernel, from one ncu capture (profiles/spots_split_large_shot_dram.txt:
+# the mean of two launches);
 # valid only while the kernel sources hash to the value they had then
-TRAFFIC_CAPTURE = {"bytes": 79148288 + 25847296,
+TRAFFIC_CAPTURE = {"bytes": (80208384 + 22526464 + 79908608 + 23491072) // 2,
                    "sources": ["paper_2205_07976_gb300/csrc/spots_split.cu",
                                "paper_2205_07976_gb300/csrc/split_pixel.cuh",
                                "paper_2205_07976_gb300/csrc/mixed_common.cuh",
                                "paper_2205_07976_gb300/csrc/nbgb_internal.cuh"],
-                   "sha256_16": "b5326d9b4b0ec590"}
+                   "sha256_16": "c15f8a79666a519f"}
 
 
 def captured_traffic():
@@ -71,10 +72,16 @@ def captured_traffic():
     return TRAFFIC_CAPTURE["bytes"]
 
 
-# FP32-pipe utilisation of the warp-per-pixel kernel from one ncu --set full
-# capture on a 512x512 window of the large shot
+# Pipe utilisation (% of active cycles) of the warp-per-pixel kernel from
+# one ncu --set full capture on a 512x512 window of the large shot
 # (profiles/spots_split_window512_full.txt), keyed like the traffic figure
-PIPES_CAPTURE = None
+PIPES_CAPTURE = {"sm__pipe_fma_cycles_active_pct": 35.0,
+                 "sm__pipe_alu_cycles_active_pct": 41.2,
+                 "sm__inst_executed_pipe_lsu_pct": 41.2,
+                 "smsp__issue_active_pct": 74.1,
+                 "l1tex__data_pipe_lsu_wavefronts_pct": 53.8,
+                 "window": "512x512 centred on the large shot",
+                 "sha256_16": "c15f8a79666a519f"}
 
 
 def captured_pipes():

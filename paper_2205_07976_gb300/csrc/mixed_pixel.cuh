@@ -133,17 +133,44 @@ __device__ __forceinline__ double mixed_pixel(const SpotArgs &a,
             for (int k = 0; k < v.S; ++k) {
               const float2 dq =
                   reinterpret_cast<const float2 *>(s_srcq)[k];
-              float fh[3], fl[3];
+              float fh[3], fl[3], nfx[3];
+              // axes h and k in packed two-lane operations (the same
+              // roundings lane by lane), l in scalar ones
+              {
+                const float2 d2 = make_float2(dq.x, dq.x),
+                             e2 = make_float2(dq.y, dq.y);
+                const float2 Gq2 = make_float2(Gq[0], Gq[1]),
+                             Gr2 = make_float2(Gr[0], Gr[1]),
+                             rq22 = make_float2(rq2[0], rq2[1]);
+                const float2 t = ffma2(Gq2, d2, rq22);
+                const float2 nf = make_float2(rintf(t.x), rintf(t.y));
+                const float2 sx = ffma2(Gq2, d2, fsub2(rq22, nf));
+                const float2 lo = ffma2(
+                    Gr2, d2,
+                    ffma2(Gq2, e2,
+                          ffma2(Gr2, e2, make_float2(rr2[0], rr2[1]))));
+                const float2 h2 = fadd2(sx, lo);
+                const float2 l2 = fsub2(lo, fsub2(h2, sx));
+                fh[0] = h2.x;
+                fh[1] = h2.y;
+                fl[0] = l2.x;
+                fl[1] = l2.y;
+                nfx[0] = nf.x;
+                nfx[1] = nf.y;
+              }
+              {
+                const float nf = rintf(fmaf(Gq[2], dq.x, rq2[2]));
+                const float sx = fmaf(Gq[2], dq.x, __fsub_rn(rq2[2], nf));
+                const float lo =
+                    fmaf(Gr[2], dq.x, fmaf(Gq[2], dq.y, fmaf(Gr[2], dq.y,
+                                                             rr2[2])));
+                fh[2] = __fadd_rn(sx, lo);
+                fl[2] = __fsub_rn(lo, __fsub_rn(fh[2], sx));
+                nfx[2] = nf;
+              }
               int n[3];
 #pragma unroll
               for (int x = 0; x < 3; ++x) {
-                const float nf = rintf(fmaf(Gq[x], dq.x, rq2[x]));
-                const float sx = fmaf(Gq[x], dq.x, __fsub_rn(rq2[x], nf));
-                const float lo =
-                    fmaf(Gr[x], dq.x, fmaf(Gq[x], dq.y, fmaf(Gr[x], dq.y,
-                                                             rr2[x])));
-                fh[x] = __fadd_rn(sx, lo);
-                fl[x] = __fsub_rn(lo, __fsub_rn(fh[x], sx));
                 // nf was rounded from the grid values, which differ from h
                 // by up to |lo|: for an offset beyond 1/2, n moves to h's
                 // nearest lattice point, as the table lookup needs (the
@@ -151,7 +178,7 @@ __device__ __forceinline__ double mixed_pixel(const SpotArgs &a,
                 // the tricubic cell coordinates move with n)
                 const int adj = (fh[x] > 0.5f) - (fh[x] < -0.5f);
                 if (INTERP == 1) fh[x] = __fsub_rn(fh[x], (float)adj);
-                n[x] = __float2int_rn(n0[x] + nf) - a.hmin[x] + adj;
+                n[x] = __float2int_rn(n0[x] + nfx[x]) - a.hmin[x] + adj;
               }
               const float2 yr2 =
                   sinc_arg2(make_float2(a.N[0], a.N[1]),

@@ -40,9 +40,10 @@ struct SplitEntry {
 };
 constexpr int kIntervalEntry = 1 << 31;
 static_assert(sizeof(SplitEntry) % 16 == 0, "entries stay 16-byte aligned");
-static_assert(SRC32_DL % 2 == 0 && SRC32_W == SRC32_DL + 1 &&
-                  SRC32_STRIDE % 2 == 0 && kUnitFloats % 2 == 0,
-              "float2 reads of (delta_lo, w) and of the unit rows");
+static_assert(SRC32_DL == 0 && SRC32_W == 1 && SRC32_DH == 2 &&
+                  SRC32_STRIDE % 4 == 0 && kUnitFloats % 2 == 0,
+              "one float4 read of (delta_lo, w, delta_hi, .) per source "
+              "and float2 reads of the unit rows");
 
 // ff_dot3 (mixed_common.cuh) with the double-float row stored as
 // interleaved (hi, lo) pairs: the same operations, half the shared loads
@@ -265,9 +266,13 @@ struct SplitBlock {
 
 // Bytes of dynamic shared memory split_stage lays out for PM orientations
 // and S sources.
+__host__ __device__ inline int split_axes_floats(int PM) {
+  return (2 * PM * 9 + 3) & ~3;  // the source rows after it 16-byte aligned
+}
+
 __host__ __device__ inline size_t split_smem_layout(int PM, int S) {
   const int nblk = (S + kSrcBlock - 1) / kSrcBlock;
-  size_t off = (size_t)(2 * PM * 9 + S * SRC32_STRIDE +
+  size_t off = (size_t)(split_axes_floats(PM) + S * SRC32_STRIDE +
                         kSplitWarps * kMaxUnits * kUnitFloats) *
                sizeof(float);
   off = (off + 15) & ~(size_t)15;
@@ -288,7 +293,7 @@ __device__ __forceinline__ void split_stage(SplitBlock &b, float *sms,
                                             const float *src32, int PM, int S,
                                             float u0h, float u0l) {
   float2 *s_ax2 = reinterpret_cast<float2 *>(sms);
-  float *s_src = sms + 2 * PM * 9;
+  float *s_src = sms + split_axes_floats(PM);
   float *s_unit = s_src + S * SRC32_STRIDE;  // [warp][unit][kUnitFloats]
   // entries and cache hold float4s: 16-byte aligned base
   const size_t ent_off =
@@ -529,9 +534,10 @@ __device__ __forceinline__ unsigned sum_pairs(
   const float Gh[3] = {A.x, A.y, C.x}, r[3] = {A.z, A.w, C.y};
   const float Gl[3] = {B.x, B.y, C.z}, rl[3] = {B.z, B.w, C.w};
   const float *src = b.src + k * SRC32_STRIDE;
-  const float dh = b.dh[k];
-  // (delta_lo, w) of source k in one load
-  const float2 dlw = *reinterpret_cast<const float2 *>(src + SRC32_DL);
+  // (delta_lo, w, delta_hi) of source k in one load
+  const float4 sw = *reinterpret_cast<const float4 *>(src);
+  const float dh = sw.z;
+  const float2 dlw = make_float2(sw.x, sw.y);
   float fr[3];
   int n[3];
   if (!HASDIV && (aux & kIntervalEntry)) {
