@@ -130,6 +130,10 @@ __device__ __forceinline__ double mixed_pixel(const SpotArgs &a,
           }
           if (fastq) {
             float blk = 0.f;  // plain sum of up to 8 sources' terms
+            const float hnf[3] = {(float)a.hn[0], (float)a.hn[1],
+                                  (float)a.hn[2]};
+            const bool fidx_float =
+                (long long)a.hn[0] * a.hn[1] * a.hn[2] <= (1ll << 24);
             for (int k = 0; k < v.S; ++k) {
               const float2 dq =
                   reinterpret_cast<const float2 *>(s_srcq)[k];
@@ -168,17 +172,18 @@ __device__ __forceinline__ double mixed_pixel(const SpotArgs &a,
                 fl[2] = __fsub_rn(lo, __fsub_rn(fh[2], sx));
                 nfx[2] = nf;
               }
-              int n[3];
+              // nf was rounded from the grid values, which differ from h
+              // by up to |lo|: h's nearest lattice point is nf plus the
+              // rounding of the offset (-+1 beyond 1/2), as the table
+              // lookup needs (the sinc ratio is the same for f and f -+ 1
+              // up to its sign; the tricubic cell coordinates move with
+              // it).  Table-relative, in FP32 (small integers, exact).
+              float nt[3];
 #pragma unroll
               for (int x = 0; x < 3; ++x) {
-                // nf was rounded from the grid values, which differ from h
-                // by up to |lo|: for an offset beyond 1/2, n moves to h's
-                // nearest lattice point, as the table lookup needs (the
-                // sinc ratio is the same for f and f -+ 1 up to its sign;
-                // the tricubic cell coordinates move with n)
-                const int adj = (fh[x] > 0.5f) - (fh[x] < -0.5f);
-                if (INTERP == 1) fh[x] = __fsub_rn(fh[x], (float)adj);
-                n[x] = __float2int_rn(n0[x] + nfx[x]) - a.hmin[x] + adj;
+                const float adj = rintf(fh[x]);
+                if (INTERP == 1) fh[x] = __fsub_rn(fh[x], adj);
+                nt[x] = (n0[x] - (float)a.hmin[x]) + (nfx[x] + adj);
               }
               const float2 yr2 =
                   sinc_arg2(make_float2(a.N[0], a.N[1]),
@@ -191,15 +196,37 @@ __device__ __forceinline__ double mixed_pixel(const SpotArgs &a,
               const float2 nh = sinpi_reduced2_d4(yr2);
               const float2 dk = sinpi_reduced2_d4(make_float2(fh[0], fh[1]));
               const float2 sl = sinpi_reduced2_d4(make_float2(yzr, fh[2]));
-              const bool z0 = fabsf(fh[0]) < 1e-9f, z1 = fabsf(fh[1]) < 1e-9f,
-                         z2 = fabsf(fh[2]) < 1e-9f;
-              const float num = (z0 ? a.N[0] : nh.x) * (z1 ? a.N[1] : nh.y) *
-                                (z2 ? a.N[2] : sl.x);
-              const float den = (z0 ? 1.f : dk.x) * (z1 ? 1.f : dk.y) *
-                                (z2 ? 1.f : sl.y);
+              float num = nh.x * nh.y * sl.x, den = dk.x * dk.y * sl.y;
+              if (den == 0.f) {
+                // an offset exactly 0: that axis's ratio is N (f -> 0)
+                const bool z0 = fh[0] == 0.f, z1 = fh[1] == 0.f,
+                           z2 = fh[2] == 0.f;
+                num = (z0 ? a.N[0] : nh.x) * (z1 ? a.N[1] : nh.y) *
+                      (z2 ? a.N[2] : sl.x);
+                den = (z0 ? 1.f : dk.x) * (z1 ? 1.f : dk.y) *
+                      (z2 ? 1.f : sl.y);
+              }
               const float ratio = __fdividef(num, den);
               ++evals;
-              const float fc = fcell_f32<INTERP>(a, n, fh);
+              float fc;
+              if (INTERP == 0 && fidx_float) {
+                // nearest lookup with the index formed in FP32 (exact: the
+                // table has at most 2^24 entries)
+                const bool inside = nt[0] >= 0.f && nt[0] < hnf[0] &&
+                                    nt[1] >= 0.f && nt[1] < hnf[1] &&
+                                    nt[2] >= 0.f && nt[2] < hnf[2];
+                fc = inside
+                         ? __ldg(a.F + nb_idx(a.check, NB_SITE_F,
+                                              (long long)fmaf(
+                                                  fmaf(nt[0], hnf[1], nt[1]),
+                                                  hnf[2], nt[2]),
+                                              table_size(a)))
+                         : a.defF;
+              } else {
+                const int n[3] = {__float2int_rn(nt[0]), __float2int_rn(nt[1]),
+                                  __float2int_rn(nt[2])};
+                fc = fcell_f32<INTERP>(a, n, fh);
+              }
               blk += fc * fc * (ratio * ratio) * s_src[k * SRC32_STRIDE +
                                                        SRC32_W];
               if ((k & 7) == 7 || k == v.S - 1) {
