@@ -709,7 +709,11 @@ __device__ __forceinline__ double split_sum(const SpotArgs &a,
       // sorted delta table
       const int maxc = (int)__reduce_max_sync(0xffffffffu, (unsigned)ncomb);
       if (COUNT) nivals += __reduce_add_sync(0xffffffffu, (unsigned)ncomb);
-      // the lattice points ml + (d0, d1, d2), d_x < nm_x, in odometer order
+      // the lattice points ml + (d0, d1, d2), d_x < nm_x, in odometer order;
+      // A of the quadratic depends on the item only
+      float A = N2[0] * Gh[0] * Gh[0];
+      A = fmaf(N2[1] * Gh[1], Gh[1], A);
+      A = fmaf(N2[2] * Gh[2], Gh[2], A);
       int dg[3] = {0, 0, 0};
       for (int c = 0; c < maxc; ++c) {
         int k1 = 0, k2 = 0;
@@ -730,9 +734,6 @@ __device__ __forceinline__ double split_sum(const SpotArgs &a,
               ++dg[2];
             }
           }
-          float A = N2[0] * Gh[0] * Gh[0];
-          A = fmaf(N2[1] * Gh[1], Gh[1], A);
-          A = fmaf(N2[2] * Gh[2], Gh[2], A);
           float B = N2[0] * Gh[0] * dx[0];
           B = fmaf(N2[1] * Gh[1], dx[1], B);
           B = fmaf(N2[2] * Gh[2], dx[2], B);
@@ -766,13 +767,15 @@ __device__ __forceinline__ double split_sum(const SpotArgs &a,
             k2 = S;  // the sweep does not move: all or nothing
           }
         }
+        // no lane has an entry for this lattice point: nothing to push
+        if (!__any_sync(0xffffffffu, k2 > k1)) continue;
         float4 d4;
         if (INTERP == 1 && a.C4) {
           // the lattice point's cell data once per entry; the index packed
           // (clamped to [-1, hn]: any index outside the table looks up
           // default_F, and cell tables exist only for hn < 1024)
           int ci0 = 0, pk = 0, npk = 0;
-          if (c < ncomb) {
+          if (k2 > k1) {
             entry_cell_data(a, nt, ci0, pk);
 #pragma unroll
             for (int x = 0; x < 3; ++x)
