@@ -114,6 +114,10 @@ __device__ __forceinline__ float cell_horner(const float4 *cp, int stride,
   return fmaf(fmaf(fmaf(q[1].y, x[0], q[1].x), x[0], q[0].y), x[0], q[0].x);
 }
 
+// n[2] of a term whose index is still packed (interval entries with cell
+// polynomials): n[0] then holds the packed index of SplitEntry::d.y
+constexpr int kPackedIndex = -0x40000000;
+
 // The cell of a tricubic term: whether its 4x4x4 stencil lies inside the
 // table (tri), the cell's index in the polynomial table (ci), its parity
 // slot in the cache (par) and the coordinates x in [0, 1) within the cell.
@@ -244,7 +248,13 @@ __device__ __forceinline__ float term_value(const SpotArgs &a, bool hit,
                    kCellChunks,
         1, c.x);
   } else if (hit) {
-    fc = fcell_f32<INTERP>(a, n, fr);
+    int nn[3] = {n[0], n[1], n[2]};
+    if (n[2] == kPackedIndex) {
+      nn[0] = (n[0] & 1023) - 1;
+      nn[1] = ((n[0] >> 10) & 1023) - 1;
+      nn[2] = ((n[0] >> 20) & 1023) - 1;
+    }
+    fc = fcell_f32<INTERP>(a, nn, fr);
   }
   return fc * fc * fl2 * w;
 }
@@ -553,10 +563,10 @@ __device__ __forceinline__ unsigned sum_pairs(
     fr[1] = f01.y;
     fr[2] = fmaf(Gh[2], dh, r[2]) + fmaf(Gh[2], dlw.x, fmaf(Gl[2], dh, rl[2]));
     if (INTERP == 1 && a.C4) {
-      const int npk = __float_as_int(D.y);
-      n[0] = (npk & 1023) - 1;
-      n[1] = ((npk >> 10) & 1023) - 1;
-      n[2] = ((npk >> 20) & 1023) - 1;
+      // the packed index; unpacked only where a term needs the table
+      // itself (term_value's fallback)
+      n[0] = __float_as_int(D.y);
+      n[1] = n[2] = kPackedIndex;
     } else {
       n[0] = __float_as_int(D.x);
       n[1] = __float_as_int(D.y);
