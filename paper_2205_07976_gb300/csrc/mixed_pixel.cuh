@@ -17,8 +17,142 @@ struct PixelView {
   float u0h, u0l;
 };
 
-// s_srcq: the sources' (delta on the grid qD, rest) pairs of the sinc fast
-// path in shared memory, or null.
+// Lookups of the sinc fast path: the general one (fcell_f32: tricubic, or
+// nearest with its bounds test per step), and the nearest lookup with the
+// index formed in FP32 and no test, for an item whose every step lands in
+// the table.
+enum { kLookupTable = 0, kLookupInside = 1 };
+
+// Whether every step of an item of the sinc fast path has its nearest
+// lattice point inside the table.  Along the sources h - n0 = Gq delta_q +
+// rq + (a rest below ~2e-3), with delta_q in [sinc_dq[0], sinc_dq[1]] (the
+// products are exact), so the step's lattice offset lies in [floor(lo),
+// ceil(hi)] of the range widened by 0.01.
+__device__ __forceinline__ bool sinc_item_inside(const SpotArgs &a,
+                                                 const float Gq[3],
+                                                 const float rq[3],
+                                                 const float n0[3]) {
+  bool in = true;
+#pragma unroll
+  for (int x = 0; x < 3; ++x) {
+    const float e0 = Gq[x] * a.sinc_dq[0], e1 = Gq[x] * a.sinc_dq[1];
+    const float lo = floorf(fminf(e0, e1) + rq[x] - 0.01f),
+                hi = ceilf(fmaxf(e0, e1) + rq[x] + 0.01f);
+    const float c = n0[x] - (float)a.hmin[x];
+    in = in && c + lo >= 0.f && c + hi <= (float)a.hn[x] - 1.f;
+  }
+  return in;
+}
+
+// One item (subpixel, phi x mosaic) of the sinc fast path over the S
+// sources, added to acc in blocks of 8 (a plain FP32 sum per block).  The
+// item's G and r are on their grids (Gq, on qG; rq, on 2^-21) with the
+// rests Gr and rr; n0 is its lattice point; q4 holds the sources' (delta
+// on the grid qD, the rest of delta, w, 0).  Gq delta_q is exact in FP32
+// (qG qD = 2^-21, at most 11 and 12 significant bits), and so is
+// Gq delta_q + (rq - n); the offset of the step is that value plus the
+// small terms Gr delta_q + Gq delta_rest + Gr delta_rest + rr (|.| below
+// ~2e-3, good to ~1e-10), kept as a double-float pair.
+template <int INTERP, int LOOKUP>
+__device__ __forceinline__ void sinc_fast_item(
+    const SpotArgs &a, const float4 *q4, int S, const float Gq[3],
+    const float Gr[3], const float rq[3], const float rr[3],
+    const float n0[3], Kahan &acc, unsigned &evals) {
+  const float hnf[3] = {(float)a.hn[0], (float)a.hn[1], (float)a.hn[2]};
+  // the item's lattice point relative to the table, and its flat index
+  // (integers below 2^24 in magnitude: exact in FP32)
+  const float c[3] = {n0[0] - (float)a.hmin[0], n0[1] - (float)a.hmin[1],
+                      n0[2] - (float)a.hmin[2]};
+  const float H12 = hnf[1] * hnf[2];
+  const float cidx = fmaf(c[0], H12, fmaf(c[1], hnf[2], c[2]));
+  for (int k0 = 0; k0 < S; k0 += 8) {
+    const int kend = min(k0 + 8, S);
+    float blk = 0.f;
+    for (int k = k0; k < kend; ++k) {
+      const float4 dq = q4[k];
+      float fh[3], fl[3], nfx[3];
+      // axes h and k in packed two-lane operations (the same roundings
+      // lane by lane), l in scalar ones
+      {
+        const float2 d2 = make_float2(dq.x, dq.x), e2 = make_float2(dq.y, dq.y);
+        const float2 Gq2 = make_float2(Gq[0], Gq[1]),
+                     Gr2 = make_float2(Gr[0], Gr[1]),
+                     rq22 = make_float2(rq[0], rq[1]);
+        const float2 t = ffma2(Gq2, d2, rq22);
+        const float2 nf = make_float2(rintf(t.x), rintf(t.y));
+        const float2 sx = ffma2(Gq2, d2, fsub2(rq22, nf));
+        const float2 lo = ffma2(
+            Gr2, d2,
+            ffma2(Gq2, e2, ffma2(Gr2, e2, make_float2(rr[0], rr[1]))));
+        const float2 h2 = fadd2(sx, lo);
+        const float2 l2 = fsub2(lo, fsub2(h2, sx));
+        fh[0] = h2.x;
+        fh[1] = h2.y;
+        fl[0] = l2.x;
+        fl[1] = l2.y;
+        nfx[0] = nf.x;
+        nfx[1] = nf.y;
+      }
+      {
+        const float nf = rintf(fmaf(Gq[2], dq.x, rq[2]));
+        const float sx = fmaf(Gq[2], dq.x, __fsub_rn(rq[2], nf));
+        const float lo =
+            fmaf(Gr[2], dq.x, fmaf(Gq[2], dq.y, fmaf(Gr[2], dq.y, rr[2])));
+        fh[2] = __fadd_rn(sx, lo);
+        fl[2] = __fsub_rn(lo, __fsub_rn(fh[2], sx));
+        nfx[2] = nf;
+      }
+      // nf was rounded from the grid values, which differ from h by up to
+      // |lo|: h's nearest lattice point is n0 + nf plus the rounding of the
+      // offset (-+1 beyond 1/2), as the table lookup needs (the sinc ratio
+      // is the same for f and f -+ 1 up to its sign; the tricubic cell
+      // coordinates move with it)
+      float m[3];
+#pragma unroll
+      for (int x = 0; x < 3; ++x) {
+        const float adj = rintf(fh[x]);
+        if (INTERP == 1) fh[x] = __fsub_rn(fh[x], adj);
+        m[x] = nfx[x] + adj;
+      }
+      const float2 yr2 = sinc_arg2(make_float2(a.N[0], a.N[1]),
+                                   make_float2(fh[0], fh[1]),
+                                   make_float2(fl[0], fl[1]));
+      float yzh, yze;
+      two_prod(a.N[2], fh[2], yzh, yze);
+      const float yzl = fmaf(a.N[2], fl[2], yze);
+      const float yzr = __fsub_rn(yzh, rintf(yzh)) + yzl;
+      const float2 nh = sinpi_reduced2_d4(yr2);
+      const float2 dk = sinpi_reduced2_d4(make_float2(fh[0], fh[1]));
+      const float2 sl = sinpi_reduced2_d4(make_float2(yzr, fh[2]));
+      float num = nh.x * nh.y * sl.x, den = dk.x * dk.y * sl.y;
+      if (den == 0.f) {
+        // an offset exactly 0: that axis's ratio is N (f -> 0)
+        const bool z0 = fh[0] == 0.f, z1 = fh[1] == 0.f, z2 = fh[2] == 0.f;
+        num = (z0 ? a.N[0] : nh.x) * (z1 ? a.N[1] : nh.y) *
+              (z2 ? a.N[2] : sl.x);
+        den = (z0 ? 1.f : dk.x) * (z1 ? 1.f : dk.y) * (z2 ? 1.f : sl.y);
+      }
+      const float ratio = __fdividef(num, den);
+      ++evals;
+      float fc;
+      if (LOOKUP == kLookupInside) {
+        const float idx = fmaf(m[0], H12, fmaf(m[1], hnf[2], m[2] + cidx));
+        fc = __ldg(a.F +
+                   nb_idx(a.check, NB_SITE_F, (long long)idx, table_size(a)));
+      } else {
+        const int n[3] = {__float2int_rn(c[0] + m[0]),
+                          __float2int_rn(c[1] + m[1]),
+                          __float2int_rn(c[2] + m[2])};
+        fc = fcell_f32<INTERP>(a, n, fh);
+      }
+      blk += fc * fc * (ratio * ratio) * dq.z;
+    }
+    acc.add(blk);
+  }
+}
+
+// s_srcq: the sinc fast path's source rows in shared memory (float4: delta
+// on the grid qD, the rest of delta, w, 0), or null.
 template <int SHAPE, int INTERP, int MODE, int HASDIV>
 __device__ __forceinline__ double mixed_pixel(const SpotArgs &a,
                                               const PixelView &v,
@@ -104,15 +238,9 @@ __device__ __forceinline__ double mixed_pixel(const SpotArgs &a,
               rh[x] = rl[x] = n0[x] = 0.f;
             }
           }
-          // sinc in NB_MIXED, fast path: G rounded to the grid qG and
-          // delta to qD (qG qD = 2^-21, each with at most 11 and 12
-          // significant bits), r to the grid 2^-21.  Then G_q delta_q is
-          // exact in FP32, and so is G_q delta_q + (r_q - n): the offset
-          // of the step is that exact value plus the small terms
-          // G_rest delta_q + G_q delta_rest + G_rest delta_rest + r_rest
-          // (|.| < ~2e-3, good to ~1e-10), kept as a double-float pair.
-          // Taken per item when |G| < 2^11 qG on every axis, otherwise the
-          // general path below.
+          // sinc in NB_MIXED, fast path (sinc_fast_item): G rounded to the
+          // grid qG, r to the grid 2^-21.  Taken per item when |G| < 2^11 qG
+          // on every axis, otherwise the general path below.
           bool fastq = false;
           float Gq[3], Gr[3], rq2[3], rr2[3];
           if (MODE == 0 && SHAPE == 0 && !HASDIV && s_srcq) {
@@ -129,111 +257,17 @@ __device__ __forceinline__ double mixed_pixel(const SpotArgs &a,
             }
           }
           if (fastq) {
-            float blk = 0.f;  // plain sum of up to 8 sources' terms
-            const float hnf[3] = {(float)a.hn[0], (float)a.hn[1],
-                                  (float)a.hn[2]};
-            const bool fidx_float =
-                (long long)a.hn[0] * a.hn[1] * a.hn[2] <= (1ll << 24);
-            for (int k = 0; k < v.S; ++k) {
-              const float2 dq =
-                  reinterpret_cast<const float2 *>(s_srcq)[k];
-              float fh[3], fl[3], nfx[3];
-              // axes h and k in packed two-lane operations (the same
-              // roundings lane by lane), l in scalar ones
-              {
-                const float2 d2 = make_float2(dq.x, dq.x),
-                             e2 = make_float2(dq.y, dq.y);
-                const float2 Gq2 = make_float2(Gq[0], Gq[1]),
-                             Gr2 = make_float2(Gr[0], Gr[1]),
-                             rq22 = make_float2(rq2[0], rq2[1]);
-                const float2 t = ffma2(Gq2, d2, rq22);
-                const float2 nf = make_float2(rintf(t.x), rintf(t.y));
-                const float2 sx = ffma2(Gq2, d2, fsub2(rq22, nf));
-                const float2 lo = ffma2(
-                    Gr2, d2,
-                    ffma2(Gq2, e2,
-                          ffma2(Gr2, e2, make_float2(rr2[0], rr2[1]))));
-                const float2 h2 = fadd2(sx, lo);
-                const float2 l2 = fsub2(lo, fsub2(h2, sx));
-                fh[0] = h2.x;
-                fh[1] = h2.y;
-                fl[0] = l2.x;
-                fl[1] = l2.y;
-                nfx[0] = nf.x;
-                nfx[1] = nf.y;
-              }
-              {
-                const float nf = rintf(fmaf(Gq[2], dq.x, rq2[2]));
-                const float sx = fmaf(Gq[2], dq.x, __fsub_rn(rq2[2], nf));
-                const float lo =
-                    fmaf(Gr[2], dq.x, fmaf(Gq[2], dq.y, fmaf(Gr[2], dq.y,
-                                                             rr2[2])));
-                fh[2] = __fadd_rn(sx, lo);
-                fl[2] = __fsub_rn(lo, __fsub_rn(fh[2], sx));
-                nfx[2] = nf;
-              }
-              // nf was rounded from the grid values, which differ from h
-              // by up to |lo|: h's nearest lattice point is nf plus the
-              // rounding of the offset (-+1 beyond 1/2), as the table
-              // lookup needs (the sinc ratio is the same for f and f -+ 1
-              // up to its sign; the tricubic cell coordinates move with
-              // it).  Table-relative, in FP32 (small integers, exact).
-              float nt[3];
-#pragma unroll
-              for (int x = 0; x < 3; ++x) {
-                const float adj = rintf(fh[x]);
-                if (INTERP == 1) fh[x] = __fsub_rn(fh[x], adj);
-                nt[x] = (n0[x] - (float)a.hmin[x]) + (nfx[x] + adj);
-              }
-              const float2 yr2 =
-                  sinc_arg2(make_float2(a.N[0], a.N[1]),
-                            make_float2(fh[0], fh[1]),
-                            make_float2(fl[0], fl[1]));
-              float yzh, yze;
-              two_prod(a.N[2], fh[2], yzh, yze);
-              const float yzl = fmaf(a.N[2], fl[2], yze);
-              const float yzr = __fsub_rn(yzh, rintf(yzh)) + yzl;
-              const float2 nh = sinpi_reduced2_d4(yr2);
-              const float2 dk = sinpi_reduced2_d4(make_float2(fh[0], fh[1]));
-              const float2 sl = sinpi_reduced2_d4(make_float2(yzr, fh[2]));
-              float num = nh.x * nh.y * sl.x, den = dk.x * dk.y * sl.y;
-              if (den == 0.f) {
-                // an offset exactly 0: that axis's ratio is N (f -> 0)
-                const bool z0 = fh[0] == 0.f, z1 = fh[1] == 0.f,
-                           z2 = fh[2] == 0.f;
-                num = (z0 ? a.N[0] : nh.x) * (z1 ? a.N[1] : nh.y) *
-                      (z2 ? a.N[2] : sl.x);
-                den = (z0 ? 1.f : dk.x) * (z1 ? 1.f : dk.y) *
-                      (z2 ? 1.f : sl.y);
-              }
-              const float ratio = __fdividef(num, den);
-              ++evals;
-              float fc;
-              if (INTERP == 0 && fidx_float) {
-                // nearest lookup with the index formed in FP32 (exact: the
-                // table has at most 2^24 entries)
-                const bool inside = nt[0] >= 0.f && nt[0] < hnf[0] &&
-                                    nt[1] >= 0.f && nt[1] < hnf[1] &&
-                                    nt[2] >= 0.f && nt[2] < hnf[2];
-                fc = inside
-                         ? __ldg(a.F + nb_idx(a.check, NB_SITE_F,
-                                              (long long)fmaf(
-                                                  fmaf(nt[0], hnf[1], nt[1]),
-                                                  hnf[2], nt[2]),
-                                              table_size(a)))
-                         : a.defF;
-              } else {
-                const int n[3] = {__float2int_rn(nt[0]), __float2int_rn(nt[1]),
-                                  __float2int_rn(nt[2])};
-                fc = fcell_f32<INTERP>(a, n, fh);
-              }
-              blk += fc * fc * (ratio * ratio) * s_src[k * SRC32_STRIDE +
-                                                       SRC32_W];
-              if ((k & 7) == 7 || k == v.S - 1) {
-                acc.add(blk);
-                blk = 0.f;
-              }
-            }
+            const float4 *q4 = reinterpret_cast<const float4 *>(s_srcq);
+            // the nearest lookup's index in FP32 for an item whose steps all
+            // land in the table: a table below 2^23 entries with hn_h >= 16
+            // keeps every partial sum of the index below 2^24
+            if (INTERP == 0 && table_size(a) <= (1ll << 23) && a.hn[0] >= 16 &&
+                sinc_item_inside(a, Gq, rq2, n0))
+              sinc_fast_item<INTERP, kLookupInside>(a, q4, v.S, Gq, Gr, rq2,
+                                                    rr2, n0, acc, evals);
+            else
+              sinc_fast_item<INTERP, kLookupTable>(a, q4, v.S, Gq, Gr, rq2,
+                                                   rr2, n0, acc, evals);
             continue;
           }
           if (MODE == 0 && SHAPE == 0 && !HASDIV) {

@@ -87,6 +87,7 @@ struct nb_sim {
   DevBuf d_panels, d_ax64, d_axh, d_axl, d_src64, d_src32, d_divh, d_divl,
       d_F, d_image, d_list, d_tmp, d_stats, d_work, d_srcq, d_check;
   float sinc_qG = 0.f;  // grid of G for the sinc fast path (0: off)
+  float sinc_dq[2] = {0.f, 0.f};  // range of the sources' delta on its grid
   int variant = NB_VARIANT_AUTO;
   int sm_count = 0;
   long long last_pixel_steps = 0, last_pixels = 0;
@@ -381,12 +382,16 @@ static int upload_tables(nb_sim *s) {
       m = std::max(m, std::fabs(1.0 / s->lam[k] - s->u0));
     const int e = m > 0.0 ? (int)std::ceil(std::log2(m)) : -20;
     const double qD = std::ldexp(1.0, e - 12);
-    srcq.resize((size_t)2 * S);
+    srcq.resize((size_t)4 * S);
     for (int k = 0; k < S; ++k) {
       const double d = 1.0 / s->lam[k] - s->u0;
       const double dq = std::nearbyint(d / qD) * qD;
-      srcq[2 * k] = (float)dq;  // exact: at most 13 bits on a power-of-2 grid
-      srcq[2 * k + 1] = (float)(d - dq);
+      srcq[4 * k] = (float)dq;  // exact: at most 13 bits on a power-of-2 grid
+      srcq[4 * k + 1] = (float)(d - dq);
+      srcq[4 * k + 2] = src32[(size_t)k * nbgb::SRC32_STRIDE + nbgb::SRC32_W];
+      srcq[4 * k + 3] = 0.f;
+      s->sinc_dq[0] = k ? std::min(s->sinc_dq[0], srcq[4 * k]) : srcq[4 * k];
+      s->sinc_dq[1] = k ? std::max(s->sinc_dq[1], srcq[4 * k]) : srcq[4 * k];
     }
     s->sinc_qG = (float)std::ldexp(1.0, -21 - (e - 12));
   }
@@ -507,6 +512,8 @@ static void fill_args(const nb_sim *s, SpotArgs &a) {
   a.divl = (const float *)s->d_divl.p;
   a.srcq = s->sinc_qG > 0.f ? (const float *)s->d_srcq.p : nullptr;
   a.sinc_qG = a.srcq ? s->sinc_qG : 0.f;
+  a.sinc_dq[0] = s->sinc_dq[0];
+  a.sinc_dq[1] = s->sinc_dq[1];
   a.prefactor = nbgb::kElectronRadius * nbgb::kElectronRadius * s->fluence *
                 s->scale / ((double)s->os * s->os * s->n_mosaic * s->n_phi);
   a.image = (double *)s->d_image.p;
@@ -903,12 +910,18 @@ static int launch(nb_sim *s, const long long *dev_list, long long n_list) {
   size_t smem_need =
       s->precision == NB_F64
           ? (size_t)(a.PM * 9 + a.S * nbgb::SRC64_STRIDE) * sizeof(double)
-          : (size_t)(2 * a.PM * 9 + a.S * (nbgb::SRC32_STRIDE + 2)) *
+          : (size_t)(2 * a.PM * 9 + a.S * nbgb::SRC32_STRIDE) *
                 sizeof(float);
   if (smem_need > 200 * 1024)
     return fail(s, NB_EINVAL,
                 "phi x mosaic and source tables exceed 200 KB of shared "
                 "memory");
+  // the sinc fast path stages 4 more floats per source; where they do not
+  // fit as well, the kernels take the general path
+  if (a.srcq && smem_need + (size_t)a.S * 4 * sizeof(float) > 200 * 1024) {
+    a.srcq = nullptr;
+    a.sinc_qG = 0.f;
+  }
   // counters: [0] evaluated terms, [1..3] the warp kernel's pairs,
   // intervals and source blocks
   cudaError_t e = s->d_stats.ensure(4 * sizeof(unsigned long long));

@@ -150,10 +150,11 @@ struct SpotArgs {
   int has_div;
   const float *divh, *divl;
   // sinc fast path of NB_MIXED: per source delta split on a fixed grid qD
-  // (srcq[S][2] = (delta on the grid, the rest)), and the grid qG of the
+  // (srcq[S][4] = (delta on the grid, the rest, w, 0)), and the grid qG of the
   // items' G, with qG qD = 2^-21; sinc_qG = 0: no fast path
   const float *srcq;
   float sinc_qG;
+  float sinc_dq[2];  // the least and the largest delta on the grid qD
   double prefactor;  // r_e^2 fluence scale / (os^2 M Phi)
   double *image;
   // statistics of the launch: [0] terms evaluated (the FP32 forms skip

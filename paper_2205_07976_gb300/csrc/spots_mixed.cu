@@ -24,23 +24,23 @@ namespace nbgb {
 template <int SHAPE, int INTERP, int MODE, int HASDIV>
 __global__ void __launch_bounds__(kTileThreads, 4)
     spots_mixed_kernel(SpotArgs a) {
-  extern __shared__ float smf[];
-  float *s_axh = smf;
-  float *s_axl = smf + a.PM * 9;
-  float *s_src = smf + 2 * a.PM * 9;
+  extern __shared__ __align__(16) float smf[];
+  // the sinc fast path's rows (float4: delta on its grid, the rest, w)
+  // first, 16-byte aligned; then the axes and the source rows
+  const bool fastq = SHAPE == 0 && MODE == 0 && !HASDIV && a.srcq;
+  float *s_srcq = fastq ? smf : nullptr;
+  float *s_axh = smf + (fastq ? 4 * a.S : 0);
+  float *s_axl = s_axh + a.PM * 9;
+  float *s_src = s_axh + 2 * a.PM * 9;
   for (int i = threadIdx.x; i < a.PM * 9; i += blockDim.x) {
     s_axh[i] = a.axh[i];
     s_axl[i] = a.axl[i];
   }
   for (int i = threadIdx.x; i < a.S * SRC32_STRIDE; i += blockDim.x)
     s_src[i] = a.src32[i];
-  // the sinc fast path's grid table after the source rows
-  float *s_srcq = nullptr;
-  if (SHAPE == 0 && MODE == 0 && !HASDIV && a.srcq) {
-    s_srcq = s_src + a.S * SRC32_STRIDE;
-    for (int i = threadIdx.x; i < 2 * a.S; i += blockDim.x)
+  if (fastq)
+    for (int i = threadIdx.x; i < 4 * a.S; i += blockDim.x)
       s_srcq[i] = a.srcq[i];
-  }
   __syncthreads();
 
   long long item = a.pixlist ? (long long)blockIdx.x * blockDim.x + threadIdx.x
@@ -164,8 +164,11 @@ cudaError_t build_cell_polynomials(const float *F, const int hn[3], float4 *C4,
 
 cudaError_t launch_spots_mixed(const SpotArgs &a, int precision,
                                cudaStream_t st) {
+  // the sinc fast path's table (NB_MIXED, sinc, one beam direction)
+  const bool fastq =
+      a.srcq && a.shape == 0 && precision != 2 && !a.has_div;
   size_t smem = (size_t)(2 * a.PM * 9 + a.S * SRC32_STRIDE +
-                         (a.srcq ? 2 * a.S : 0)) *
+                         (fastq ? 4 * a.S : 0)) *
                 sizeof(float);
   long long blocks = a.pixlist ? (a.n_list + kTileThreads - 1) / kTileThreads
                                : a.n_tiles;

@@ -108,6 +108,35 @@ def test_precision_window(N):
     assert np.isfinite(run(s, "f32")).all()
 
 
+@pytest.mark.parametrize("hmax,interp", [(20, W.INTERP_NEAREST),
+                                         (6, W.INTERP_NEAREST),
+                                         (20, W.INTERP_TRICUBIC)])
+def test_sinc_table_edges(hmax, interp):
+    """The sinc shape with one beam direction (the kernels' fixed-grid
+    path) on a table of hkl in [-hmax, hmax]^3 that the detector's h
+    exceeds (|h| reaches ~37 at its corners), with default_F = 35: a
+    lattice point outside the table looks up default_F.  With hmax = 20
+    some items have every step in the table, some a few steps outside and
+    some every step outside; hmax = 6 is below the size at which the
+    nearest lookup forms its index in FP32.  The whole 1024^2 image,
+    compared on a grid of 4096 sampled pixels."""
+    s = W.precision_shot(10, n_mosaic=4)
+    s.F = W.structure_factors(np.random.default_rng(21), hmax)
+    s.hkl_min = np.array([-hmax] * 3, dtype=np.int32)
+    s.default_F = 35.0
+    s.interp = interp
+    pix = (np.arange(0, 1024, 32)[:, None] * 1024 +
+           np.arange(0, 1024, 8)[None, :]).ravel().astype(np.int64)
+    ref = oracle.image(s, pixels=pix)
+    check_mixed(run(s, "mixed")[pix], ref)
+    # the sample holds pixels whose terms all come from the table and
+    # pixels with terms from default_F
+    s0 = s.copy()
+    s0.default_F = 0.0
+    differ = oracle.image(s0, pixels=pix) != ref
+    assert differ.any() and not differ.all()
+
+
 # ---------------------------------------------- multi-panel (c3 forward)
 
 
