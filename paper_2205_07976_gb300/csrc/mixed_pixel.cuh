@@ -44,15 +44,34 @@ __device__ __forceinline__ bool sinc_item_inside(const SpotArgs &a,
   return in;
 }
 
-// One item (subpixel, phi x mosaic) of the sinc fast path over the S
-// sources, added to acc in blocks of 8 (a plain FP32 sum per block).  The
-// item's G and r are on their grids (Gq, on qG; rq, on 2^-21) with the
-// rests Gr and rr; n0 is its lattice point; q4 holds the sources' (delta
-// on the grid qD, the rest of delta, w, 0).  Gq delta_q is exact in FP32
-// (qG qD = 2^-21, at most 11 and 12 significant bits), and so is
-// Gq delta_q + (rq - n); the offset of the step is that value plus the
-// small terms Gr delta_q + Gq delta_rest + Gr delta_rest + rr (|.| below
-// ~2e-3, good to ~1e-10), kept as a double-float pair.
+// h - n = sx + lo of one axis of two sources at once (the lanes), in the
+// roundings of the scalar form: t = Gq dq + rq rounded to nf, sx = Gq dq +
+// (rq - nf) exact, lo the small terms; returns (fh, fl) = sx + lo as a
+// double-float pair and nf
+__device__ __forceinline__ void sinc_offset2(float2 Gq, float2 Gr, float2 rq,
+                                             float2 rr, float2 d, float2 e,
+                                             float2 &fh, float2 &fl,
+                                             float2 &nf) {
+  const float2 t = ffma2(Gq, d, rq);
+  nf = make_float2(rintf(t.x), rintf(t.y));
+  const float2 sx = ffma2(Gq, d, fsub2(rq, nf));
+  const float2 lo = ffma2(Gr, d, ffma2(Gq, e, ffma2(Gr, e, rr)));
+  fh = fadd2(sx, lo);
+  fl = fsub2(lo, fsub2(fh, sx));
+}
+
+// One item (subpixel, phi x mosaic) of the sinc fast path over the
+// sources, two at a time, added to acc in blocks of 8 sources (a plain
+// FP32 sum per block).  The item's G and r are on their grids (Gq, on qG;
+// rq, on 2^-21) with the rests Gr and rr; n0 is its lattice point.  q4
+// holds two float4 per pair of sources 2j, 2j + 1: (delta_q, delta_q,
+// delta_rest, delta_rest) and (w, w, 0, 0); a pair that completes an odd
+// count has w = 0.  Gq delta_q is exact in FP32 (qG qD = 2^-21, at most 11
+// and 12 significant bits), and so is Gq delta_q + (rq - n); the offset of
+// the step is that value plus the small terms Gr delta_q + Gq delta_rest +
+// Gr delta_rest + rr (|.| below ~2e-3, good to ~1e-10), kept as a
+// double-float pair.  Axes h and k of one source share packed two-lane
+// operations, and so do axis l, the products and the sums of the pair.
 template <int INTERP, int LOOKUP>
 __device__ __forceinline__ void sinc_fast_item(
     const SpotArgs &a, const float4 *q4, int S, const float Gq[3],
@@ -65,94 +84,105 @@ __device__ __forceinline__ void sinc_fast_item(
                       n0[2] - (float)a.hmin[2]};
   const float H12 = hnf[1] * hnf[2];
   const float cidx = fmaf(c[0], H12, fmaf(c[1], hnf[2], c[2]));
-  for (int k0 = 0; k0 < S; k0 += 8) {
-    const int kend = min(k0 + 8, S);
-    float blk = 0.f;
-    for (int k = k0; k < kend; ++k) {
-      const float4 dq = q4[k];
-      float fh[3], fl[3], nfx[3];
-      // axes h and k in packed two-lane operations (the same roundings
-      // lane by lane), l in scalar ones
-      {
-        const float2 d2 = make_float2(dq.x, dq.x), e2 = make_float2(dq.y, dq.y);
-        const float2 Gq2 = make_float2(Gq[0], Gq[1]),
-                     Gr2 = make_float2(Gr[0], Gr[1]),
-                     rq22 = make_float2(rq[0], rq[1]);
-        const float2 t = ffma2(Gq2, d2, rq22);
-        const float2 nf = make_float2(rintf(t.x), rintf(t.y));
-        const float2 sx = ffma2(Gq2, d2, fsub2(rq22, nf));
-        const float2 lo = ffma2(
-            Gr2, d2,
-            ffma2(Gq2, e2, ffma2(Gr2, e2, make_float2(rr[0], rr[1]))));
-        const float2 h2 = fadd2(sx, lo);
-        const float2 l2 = fsub2(lo, fsub2(h2, sx));
-        fh[0] = h2.x;
-        fh[1] = h2.y;
-        fl[0] = l2.x;
-        fl[1] = l2.y;
-        nfx[0] = nf.x;
-        nfx[1] = nf.y;
-      }
-      {
-        const float nf = rintf(fmaf(Gq[2], dq.x, rq[2]));
-        const float sx = fmaf(Gq[2], dq.x, __fsub_rn(rq[2], nf));
-        const float lo =
-            fmaf(Gr[2], dq.x, fmaf(Gq[2], dq.y, fmaf(Gr[2], dq.y, rr[2])));
-        fh[2] = __fadd_rn(sx, lo);
-        fl[2] = __fsub_rn(lo, __fsub_rn(fh[2], sx));
-        nfx[2] = nf;
-      }
+  const float2 Ghk = make_float2(Gq[0], Gq[1]), Grhk = make_float2(Gr[0], Gr[1]),
+               rqhk = make_float2(rq[0], rq[1]), rrhk = make_float2(rr[0], rr[1]);
+  const float2 Gll = make_float2(Gq[2], Gq[2]), Grll = make_float2(Gr[2], Gr[2]),
+               rqll = make_float2(rq[2], rq[2]), rrll = make_float2(rr[2], rr[2]);
+  const float2 Nhk = make_float2(a.N[0], a.N[1]),
+               Nll = make_float2(a.N[2], a.N[2]);
+  const int P = (S + 1) >> 1;  // pairs
+  for (int j0 = 0; j0 < P; j0 += 4) {
+    const int jend = min(j0 + 4, P);
+    float2 blk = make_float2(0.f, 0.f);
+    for (int j = j0; j < jend; ++j) {
+      const float4 D = q4[2 * j], Wp = q4[2 * j + 1];
+      // fh[s], fl[s]: (h, k) of source s; fhl, fll: l of both sources
+      float2 fh[2], fl[2], nf[2], fhl, fll, nfl;
+      sinc_offset2(Ghk, Grhk, rqhk, rrhk, make_float2(D.x, D.x),
+                   make_float2(D.z, D.z), fh[0], fl[0], nf[0]);
+      sinc_offset2(Ghk, Grhk, rqhk, rrhk, make_float2(D.y, D.y),
+                   make_float2(D.w, D.w), fh[1], fl[1], nf[1]);
+      sinc_offset2(Gll, Grll, rqll, rrll, make_float2(D.x, D.y),
+                   make_float2(D.z, D.w), fhl, fll, nfl);
       // nf was rounded from the grid values, which differ from h by up to
       // |lo|: h's nearest lattice point is n0 + nf plus the rounding of the
       // offset (-+1 beyond 1/2), as the table lookup needs (the sinc ratio
       // is the same for f and f -+ 1 up to its sign; the tricubic cell
       // coordinates move with it)
-      float m[3];
+      float m[2][3], fr[2][3];
 #pragma unroll
-      for (int x = 0; x < 3; ++x) {
-        const float adj = rintf(fh[x]);
-        if (INTERP == 1) fh[x] = __fsub_rn(fh[x], adj);
-        m[x] = nfx[x] + adj;
+      for (int q = 0; q < 2; ++q) {
+        const float fx[3] = {q ? fh[1].x : fh[0].x, q ? fh[1].y : fh[0].y,
+                             q ? fhl.y : fhl.x};
+        const float nx[3] = {q ? nf[1].x : nf[0].x, q ? nf[1].y : nf[0].y,
+                             q ? nfl.y : nfl.x};
+#pragma unroll
+        for (int x = 0; x < 3; ++x) {
+          const float adj = rintf(fx[x]);
+          fr[q][x] = INTERP == 1 ? __fsub_rn(fx[x], adj) : fx[x];
+          m[q][x] = nx[x] + adj;
+        }
       }
-      const float2 yr2 = sinc_arg2(make_float2(a.N[0], a.N[1]),
-                                   make_float2(fh[0], fh[1]),
-                                   make_float2(fl[0], fl[1]));
-      float yzh, yze;
-      two_prod(a.N[2], fh[2], yzh, yze);
-      const float yzl = fmaf(a.N[2], fl[2], yze);
-      const float yzr = __fsub_rn(yzh, rintf(yzh)) + yzl;
-      const float2 nh = sinpi_reduced2_d4(yr2);
-      const float2 dk = sinpi_reduced2_d4(make_float2(fh[0], fh[1]));
-      const float2 sl = sinpi_reduced2_d4(make_float2(yzr, fh[2]));
-      float num = nh.x * nh.y * sl.x, den = dk.x * dk.y * sl.y;
-      if (den == 0.f) {
+      // numerators sin(pi N f) and denominators sin(pi f): (h, k) of each
+      // source, l of both; their products per source in (x, y)
+      const float2 nh0 = sinpi_reduced2_d4(sinc_arg2(Nhk, fh[0], fl[0]));
+      const float2 nh1 = sinpi_reduced2_d4(sinc_arg2(Nhk, fh[1], fl[1]));
+      const float2 nl = sinpi_reduced2_d4(sinc_arg2(Nll, fhl, fll));
+      const float2 dh0 = sinpi_reduced2_d4(fh[0]);
+      const float2 dh1 = sinpi_reduced2_d4(fh[1]);
+      const float2 dl = sinpi_reduced2_d4(fhl);
+      float2 num = fmul2(make_float2(nh0.x * nh0.y, nh1.x * nh1.y), nl);
+      float2 den = fmul2(make_float2(dh0.x * dh0.y, dh1.x * dh1.y), dl);
+      if (den.x == 0.f || den.y == 0.f) {
         // an offset exactly 0: that axis's ratio is N (f -> 0)
-        const bool z0 = fh[0] == 0.f, z1 = fh[1] == 0.f, z2 = fh[2] == 0.f;
-        num = (z0 ? a.N[0] : nh.x) * (z1 ? a.N[1] : nh.y) *
-              (z2 ? a.N[2] : sl.x);
-        den = (z0 ? 1.f : dk.x) * (z1 ? 1.f : dk.y) * (z2 ? 1.f : sl.y);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const float2 fq = q ? fh[1] : fh[0], nq = q ? nh1 : nh0,
+                       dq = q ? dh1 : dh0;
+          const float fz = q ? fhl.y : fhl.x, nz = q ? nl.y : nl.x,
+                      dz = q ? dl.y : dl.x;
+          const bool z0 = fq.x == 0.f, z1 = fq.y == 0.f, z2 = fz == 0.f;
+          const float nu = (z0 ? a.N[0] : nq.x) * (z1 ? a.N[1] : nq.y) *
+                           (z2 ? a.N[2] : nz);
+          const float de = (z0 ? 1.f : dq.x) * (z1 ? 1.f : dq.y) *
+                           (z2 ? 1.f : dz);
+          if (q) {
+            num.y = nu;
+            den.y = de;
+          } else {
+            num.x = nu;
+            den.x = de;
+          }
+        }
       }
-      const float ratio = __fdividef(num, den);
-      ++evals;
-      float fc;
-      if (LOOKUP == kLookupInside) {
-        const float idx = fmaf(m[0], H12, fmaf(m[1], hnf[2], m[2] + cidx));
-        fc = __ldg(a.F +
-                   nb_idx(a.check, NB_SITE_F, (long long)idx, table_size(a)));
-      } else {
-        const int n[3] = {__float2int_rn(c[0] + m[0]),
-                          __float2int_rn(c[1] + m[1]),
-                          __float2int_rn(c[2] + m[2])};
-        fc = fcell_f32<INTERP>(a, n, fh);
+      const float2 ratio = make_float2(__fdividef(num.x, den.x),
+                                       __fdividef(num.y, den.y));
+      float fc[2];
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        if (LOOKUP == kLookupInside) {
+          const float idx =
+              fmaf(m[q][0], H12, fmaf(m[q][1], hnf[2], m[q][2] + cidx));
+          fc[q] = __ldg(a.F + nb_idx(a.check, NB_SITE_F, (long long)idx,
+                                     table_size(a)));
+        } else {
+          const int n[3] = {__float2int_rn(c[0] + m[q][0]),
+                            __float2int_rn(c[1] + m[q][1]),
+                            __float2int_rn(c[2] + m[q][2])};
+          fc[q] = fcell_f32<INTERP>(a, n, fr[q]);
+        }
       }
-      blk += fc * fc * (ratio * ratio) * dq.z;
+      const float2 f2 = make_float2(fc[0], fc[1]);
+      blk = ffma2(fmul2(fmul2(f2, f2), fmul2(ratio, ratio)),
+                  make_float2(Wp.x, Wp.y), blk);
     }
-    acc.add(blk);
+    acc.add(blk.x + blk.y);
   }
+  evals += S;
 }
 
-// s_srcq: the sinc fast path's source rows in shared memory (float4: delta
-// on the grid qD, the rest of delta, w, 0), or null.
+// s_srcq: the sinc fast path's source table in shared memory (two float4
+// per pair of sources, as sinc_fast_item reads it), or null.
 template <int SHAPE, int INTERP, int MODE, int HASDIV>
 __device__ __forceinline__ double mixed_pixel(const SpotArgs &a,
                                               const PixelView &v,

@@ -382,16 +382,22 @@ static int upload_tables(nb_sim *s) {
       m = std::max(m, std::fabs(1.0 / s->lam[k] - s->u0));
     const int e = m > 0.0 ? (int)std::ceil(std::log2(m)) : -20;
     const double qD = std::ldexp(1.0, e - 12);
-    srcq.resize((size_t)4 * S);
-    for (int k = 0; k < S; ++k) {
-      const double d = 1.0 / s->lam[k] - s->u0;
+    // two float4 per pair of sources 2j, 2j + 1: (delta_q, delta_q,
+    // rest, rest) and (w, w, 0, 0); an odd count ends with a copy of the
+    // last source of weight 0
+    const int P = (S + 1) / 2;
+    srcq.assign((size_t)8 * P, 0.f);
+    for (int k = 0; k < 2 * P; ++k) {
+      const int kk = std::min(k, S - 1), j = k / 2, q = k % 2;
+      const double d = 1.0 / s->lam[kk] - s->u0;
       const double dq = std::nearbyint(d / qD) * qD;
-      srcq[4 * k] = (float)dq;  // exact: at most 13 bits on a power-of-2 grid
-      srcq[4 * k + 1] = (float)(d - dq);
-      srcq[4 * k + 2] = src32[(size_t)k * nbgb::SRC32_STRIDE + nbgb::SRC32_W];
-      srcq[4 * k + 3] = 0.f;
-      s->sinc_dq[0] = k ? std::min(s->sinc_dq[0], srcq[4 * k]) : srcq[4 * k];
-      s->sinc_dq[1] = k ? std::max(s->sinc_dq[1], srcq[4 * k]) : srcq[4 * k];
+      float *r = srcq.data() + (size_t)8 * j;
+      r[q] = (float)dq;  // exact: at most 13 bits on a power-of-2 grid
+      r[2 + q] = (float)(d - dq);
+      r[4 + q] = k < S ? src32[(size_t)k * nbgb::SRC32_STRIDE + nbgb::SRC32_W]
+                       : 0.f;
+      s->sinc_dq[0] = k ? std::min(s->sinc_dq[0], r[q]) : r[q];
+      s->sinc_dq[1] = k ? std::max(s->sinc_dq[1], r[q]) : r[q];
     }
     s->sinc_qG = (float)std::ldexp(1.0, -21 - (e - 12));
   }
@@ -916,9 +922,10 @@ static int launch(nb_sim *s, const long long *dev_list, long long n_list) {
     return fail(s, NB_EINVAL,
                 "phi x mosaic and source tables exceed 200 KB of shared "
                 "memory");
-  // the sinc fast path stages 4 more floats per source; where they do not
-  // fit as well, the kernels take the general path
-  if (a.srcq && smem_need + (size_t)a.S * 4 * sizeof(float) > 200 * 1024) {
+  // the sinc fast path stages 8 more floats per pair of sources; where
+  // they do not fit as well, the kernels take the general path
+  if (a.srcq &&
+      smem_need + (size_t)8 * ((a.S + 1) / 2) * sizeof(float) > 200 * 1024) {
     a.srcq = nullptr;
     a.sinc_qG = 0.f;
   }

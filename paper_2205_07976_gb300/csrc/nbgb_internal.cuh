@@ -150,8 +150,9 @@ struct SpotArgs {
   int has_div;
   const float *divh, *divl;
   // sinc fast path of NB_MIXED: per source delta split on a fixed grid qD
-  // (srcq[S][4] = (delta on the grid, the rest, w, 0)), and the grid qG of the
-  // items' G, with qG qD = 2^-21; sinc_qG = 0: no fast path
+  // (srcq: per pair of sources (delta on the grid x2, the rest x2, w x2,
+  // 0, 0)), and the grid qG of the items' G, with qG qD = 2^-21;
+  // sinc_qG = 0: no fast path
   const float *srcq;
   float sinc_qG;
   float sinc_dq[2];  // the least and the largest delta on the grid qD

@@ -25,11 +25,12 @@ template <int SHAPE, int INTERP, int MODE, int HASDIV>
 __global__ void __launch_bounds__(kTileThreads, 4)
     spots_mixed_kernel(SpotArgs a) {
   extern __shared__ __align__(16) float smf[];
-  // the sinc fast path's rows (float4: delta on its grid, the rest, w)
-  // first, 16-byte aligned; then the axes and the source rows
+  // the sinc fast path's table (two float4 per pair of sources) first,
+  // 16-byte aligned; then the axes and the source rows
   const bool fastq = SHAPE == 0 && MODE == 0 && !HASDIV && a.srcq;
   float *s_srcq = fastq ? smf : nullptr;
-  float *s_axh = smf + (fastq ? 4 * a.S : 0);
+  const int nq = fastq ? 8 * ((a.S + 1) / 2) : 0;
+  float *s_axh = smf + nq;
   float *s_axl = s_axh + a.PM * 9;
   float *s_src = s_axh + 2 * a.PM * 9;
   for (int i = threadIdx.x; i < a.PM * 9; i += blockDim.x) {
@@ -39,7 +40,7 @@ __global__ void __launch_bounds__(kTileThreads, 4)
   for (int i = threadIdx.x; i < a.S * SRC32_STRIDE; i += blockDim.x)
     s_src[i] = a.src32[i];
   if (fastq)
-    for (int i = threadIdx.x; i < 4 * a.S; i += blockDim.x)
+    for (int i = threadIdx.x; i < nq; i += blockDim.x)
       s_srcq[i] = a.srcq[i];
   __syncthreads();
 
@@ -168,7 +169,7 @@ cudaError_t launch_spots_mixed(const SpotArgs &a, int precision,
   const bool fastq =
       a.srcq && a.shape == 0 && precision != 2 && !a.has_div;
   size_t smem = (size_t)(2 * a.PM * 9 + a.S * SRC32_STRIDE +
-                         (fastq ? 4 * a.S : 0)) *
+                         (fastq ? 8 * ((a.S + 1) / 2) : 0)) *
                 sizeof(float);
   long long blocks = a.pixlist ? (a.n_list + kTileThreads - 1) / kTileThreads
                                : a.n_tiles;
