@@ -46,16 +46,17 @@ __device__ __forceinline__ bool sinc_item_inside(const SpotArgs &a,
 
 // h - n = sx + lo of one axis of two sources at once (the lanes), in the
 // roundings of the scalar form: t = Gq dq + rq rounded to nf, sx = Gq dq +
-// (rq - nf) exact, lo the small terms; returns (fh, fl) = sx + lo as a
-// double-float pair and nf
+// (rq - nf) exact, lo = Gr delta + Gq dr + rr the small terms (dq, dr:
+// delta on its grid and the rest; delta in FP32); returns (fh, fl) =
+// sx + lo as a double-float pair and nf
 __device__ __forceinline__ void sinc_offset2(float2 Gq, float2 Gr, float2 rq,
-                                             float2 rr, float2 d, float2 e,
-                                             float2 &fh, float2 &fl,
+                                             float2 rr, float2 dq, float2 dr,
+                                             float2 dd, float2 &fh, float2 &fl,
                                              float2 &nf) {
-  const float2 t = ffma2(Gq, d, rq);
+  const float2 t = ffma2(Gq, dq, rq);
   nf = make_float2(rintf(t.x), rintf(t.y));
-  const float2 sx = ffma2(Gq, d, fsub2(rq, nf));
-  const float2 lo = ffma2(Gr, d, ffma2(Gq, e, ffma2(Gr, e, rr)));
+  const float2 sx = ffma2(Gq, dq, fsub2(rq, nf));
+  const float2 lo = ffma2(Gr, dd, ffma2(Gq, dr, rr));
   fh = fadd2(sx, lo);
   fl = fsub2(lo, fsub2(fh, sx));
 }
@@ -64,14 +65,14 @@ __device__ __forceinline__ void sinc_offset2(float2 Gq, float2 Gr, float2 rq,
 // sources, two at a time, added to acc in blocks of 8 sources (a plain
 // FP32 sum per block).  The item's G and r are on their grids (Gq, on qG;
 // rq, on 2^-21) with the rests Gr and rr; n0 is its lattice point.  q4
-// holds two float4 per pair of sources 2j, 2j + 1: (delta_q, delta_q,
-// delta_rest, delta_rest) and (w, w, 0, 0); a pair that completes an odd
-// count has w = 0.  Gq delta_q is exact in FP32 (qG qD = 2^-21, at most 11
-// and 12 significant bits), and so is Gq delta_q + (rq - n); the offset of
-// the step is that value plus the small terms Gr delta_q + Gq delta_rest +
-// Gr delta_rest + rr (|.| below ~2e-3, good to ~1e-10), kept as a
-// double-float pair.  Axes h and k of one source share packed two-lane
-// operations, and so do axis l, the products and the sums of the pair.
+// holds two float4 per pair of sources 2j, 2j + 1: (dq, dq, dr, dr) and
+// (w, w, delta, delta), dq = delta on the grid qD, dr the rest; a pair
+// that completes an odd count has w = 0.  Gq dq is exact in FP32 (qG qD =
+// 2^-21, at most 11 and 12 significant bits), and so is Gq dq + (rq - n);
+// the offset of the step is that value plus the small terms Gr delta +
+// Gq dr + rr (|.| below ~2e-3, good to ~2e-10), kept as a double-float
+// pair.  Axes h and k of one source share packed two-lane operations, and
+// so do axis l, the products and the sums of the pair.
 template <int INTERP, int LOOKUP>
 __device__ __forceinline__ void sinc_fast_item(
     const SpotArgs &a, const float4 *q4, int S, const float Gq[3],
@@ -99,17 +100,27 @@ __device__ __forceinline__ void sinc_fast_item(
       // fh[s], fl[s]: (h, k) of source s; fhl, fll: l of both sources
       float2 fh[2], fl[2], nf[2], fhl, fll, nfl;
       sinc_offset2(Ghk, Grhk, rqhk, rrhk, make_float2(D.x, D.x),
-                   make_float2(D.z, D.z), fh[0], fl[0], nf[0]);
+                   make_float2(D.z, D.z), make_float2(Wp.z, Wp.z), fh[0],
+                   fl[0], nf[0]);
       sinc_offset2(Ghk, Grhk, rqhk, rrhk, make_float2(D.y, D.y),
-                   make_float2(D.w, D.w), fh[1], fl[1], nf[1]);
+                   make_float2(D.w, D.w), make_float2(Wp.w, Wp.w), fh[1],
+                   fl[1], nf[1]);
       sinc_offset2(Gll, Grll, rqll, rrll, make_float2(D.x, D.y),
-                   make_float2(D.z, D.w), fhl, fll, nfl);
+                   make_float2(D.z, D.w), make_float2(Wp.z, Wp.w), fhl, fll,
+                   nfl);
       // nf was rounded from the grid values, which differ from h by up to
       // |lo|: h's nearest lattice point is n0 + nf plus the rounding of the
       // offset (-+1 beyond 1/2), as the table lookup needs (the sinc ratio
       // is the same for f and f -+ 1 up to its sign; the tricubic cell
-      // coordinates move with it)
+      // coordinates move with it).  m: that lattice point relative to n0;
+      // the lookup without bounds tests forms it only in the rare pair with
+      // an offset beyond 1/2
       float m[2][3], fr[2][3];
+      const bool beyond =
+          LOOKUP != kLookupInside ||
+          fmaxf(fmaxf(fmaxf(fabsf(fh[0].x), fabsf(fh[0].y)),
+                      fmaxf(fabsf(fh[1].x), fabsf(fh[1].y))),
+                fmaxf(fabsf(fhl.x), fabsf(fhl.y))) > 0.5f;
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
         const float fx[3] = {q ? fh[1].x : fh[0].x, q ? fh[1].y : fh[0].y,
@@ -118,9 +129,16 @@ __device__ __forceinline__ void sinc_fast_item(
                              q ? nfl.y : nfl.x};
 #pragma unroll
         for (int x = 0; x < 3; ++x) {
-          const float adj = rintf(fx[x]);
-          fr[q][x] = INTERP == 1 ? __fsub_rn(fx[x], adj) : fx[x];
-          m[q][x] = nx[x] + adj;
+          m[q][x] = nx[x];
+          fr[q][x] = fx[x];
+        }
+        if (beyond) {
+#pragma unroll
+          for (int x = 0; x < 3; ++x) {
+            const float adj = rintf(fx[x]);
+            if (INTERP == 1) fr[q][x] = __fsub_rn(fx[x], adj);
+            m[q][x] = nx[x] + adj;
+          }
         }
       }
       // numerators sin(pi N f) and denominators sin(pi f): (h, k) of each

@@ -383,8 +383,8 @@ static int upload_tables(nb_sim *s) {
     const int e = m > 0.0 ? (int)std::ceil(std::log2(m)) : -20;
     const double qD = std::ldexp(1.0, e - 12);
     // two float4 per pair of sources 2j, 2j + 1: (delta_q, delta_q,
-    // rest, rest) and (w, w, 0, 0); an odd count ends with a copy of the
-    // last source of weight 0
+    // rest, rest) and (w, w, delta, delta); an odd count ends with a copy
+    // of the last source of weight 0
     const int P = (S + 1) / 2;
     srcq.assign((size_t)8 * P, 0.f);
     for (int k = 0; k < 2 * P; ++k) {
@@ -396,6 +396,7 @@ static int upload_tables(nb_sim *s) {
       r[2 + q] = (float)(d - dq);
       r[4 + q] = k < S ? src32[(size_t)k * nbgb::SRC32_STRIDE + nbgb::SRC32_W]
                        : 0.f;
+      r[6 + q] = (float)d;
       s->sinc_dq[0] = k ? std::min(s->sinc_dq[0], r[q]) : r[q];
       s->sinc_dq[1] = k ? std::max(s->sinc_dq[1], r[q]) : r[q];
     }

@@ -151,7 +151,7 @@ struct SpotArgs {
   const float *divh, *divl;
   // sinc fast path of NB_MIXED: per source delta split on a fixed grid qD
   // (srcq: per pair of sources (delta on the grid x2, the rest x2, w x2,
-  // 0, 0)), and the grid qG of the items' G, with qG qD = 2^-21;
+  // delta x2)), and the grid qG of the items' G, with qG qD = 2^-21;
   // sinc_qG = 0: no fast path
   const float *srcq;
   float sinc_qG;
