@@ -45,17 +45,17 @@ __device__ __forceinline__ bool sinc_item_inside(const SpotArgs &a,
 }
 
 // h - n = sx + lo of one axis of two sources at once (the lanes), in the
-// roundings of the scalar form: t = Gq dq + rq rounded to nf, sx = Gq dq +
-// (rq - nf) exact, lo = Gr delta + Gq dr + rr the small terms (dq, dr:
-// delta on its grid and the rest; delta in FP32); returns (fh, fl) =
-// sx + lo as a double-float pair and nf
+// roundings of the scalar form: t = Gq dq + rq, exact (both on the 2^-21
+// grid and |t| < 4), rounded to nf, sx = t - nf exact, lo = Gr delta +
+// Gq dr + rr the small terms (dq, dr: delta on its grid and the rest;
+// delta in FP32); returns (fh, fl) = sx + lo as a double-float pair and nf
 __device__ __forceinline__ void sinc_offset2(float2 Gq, float2 Gr, float2 rq,
                                              float2 rr, float2 dq, float2 dr,
                                              float2 dd, float2 &fh, float2 &fl,
                                              float2 &nf) {
   const float2 t = ffma2(Gq, dq, rq);
   nf = make_float2(rintf(t.x), rintf(t.y));
-  const float2 sx = ffma2(Gq, dq, fsub2(rq, nf));
+  const float2 sx = fsub2(t, nf);
   const float2 lo = ffma2(Gr, dd, ffma2(Gq, dr, rr));
   fh = fadd2(sx, lo);
   fl = fsub2(lo, fsub2(fh, sx));
@@ -68,7 +68,8 @@ __device__ __forceinline__ void sinc_offset2(float2 Gq, float2 Gr, float2 rq,
 // holds two float4 per pair of sources 2j, 2j + 1: (dq, dq, dr, dr) and
 // (w, w, delta, delta), dq = delta on the grid qD, dr the rest; a pair
 // that completes an odd count has w = 0.  Gq dq is exact in FP32 (qG qD =
-// 2^-21, at most 11 and 12 significant bits), and so is Gq dq + (rq - n);
+// 2^-21, at most 11 and 12 significant bits), and so is Gq dq + rq (on the
+// 2^-21 grid, below 4 in magnitude) and its distance to the nearest n;
 // the offset of the step is that value plus the small terms Gr delta +
 // Gq dr + rr (|.| below ~2e-3, good to ~2e-10), kept as a double-float
 // pair.  Axes h and k of one source share packed two-lane operations, and
@@ -287,16 +288,22 @@ __device__ __forceinline__ double mixed_pixel(const SpotArgs &a,
             }
           }
           // sinc in NB_MIXED, fast path (sinc_fast_item): G rounded to the
-          // grid qG, r to the grid 2^-21.  Taken per item when |G| < 2^11 qG
-          // on every axis, otherwise the general path below.
+          // grid qG, r to the grid 2^-21.  Taken per item when every axis
+          // has |G| < 2^11 qG and |G| max|dq| <= 3, otherwise the general
+          // path below.
           bool fastq = false;
           float Gq[3], Gr[3], rq2[3], rr2[3];
           if (MODE == 0 && SHAPE == 0 && !HASDIV && s_srcq) {
             const float qG = a.sinc_qG, iqG = 1.f / qG;  // powers of 2
+            // |G| < 2^11 qG keeps Gq dq exact; |G dq| <= 3 keeps
+            // Gq dq + rq below 4, where the 2^-21 grid is exact in FP32
+            const float dqmax =
+                fmaxf(fabsf(a.sinc_dq[0]), fabsf(a.sinc_dq[1]));
             fastq = true;
 #pragma unroll
             for (int x = 0; x < 3; ++x) {
-              fastq = fastq && fabsf(Gh[x]) < 2048.f * qG;
+              fastq = fastq && fabsf(Gh[x]) < 2048.f * qG &&
+                      fabsf(Gh[x]) * dqmax <= 3.f;
               Gq[x] = __fmul_rn(rintf(__fmul_rn(Gh[x], iqG)), qG);
               Gr[x] = __fsub_rn(Gh[x], Gq[x]) + Gl[x];
               rq2[x] = __fmul_rn(rintf(__fmul_rn(rh[x], 2097152.f)),
