@@ -427,7 +427,7 @@ __host__ __device__ inline size_t adj_ring_smem_bytes(int PM, int S,
   const int warps = kTileThreads / 32;
   return adj_ring_floats(PM, S, f_cache) * sizeof(float) +
          (size_t)warps * kAdjRing * (sizeof(float4) + sizeof(int)) +
-         (size_t)warps * 32 * sizeof(float4);
+         (size_t)warps * 32 * (sizeof(float4) + sizeof(int));
 }
 
 template <int HASF, int INTERP>
@@ -455,6 +455,7 @@ __global__ void __launch_bounds__(kTileThreads, INTERP ? 3 : 4)
   int *s_recb = reinterpret_cast<int *>(s_rec + (kTileThreads / 32) * kAdjRing);
   float4 *s_unit =
       reinterpret_cast<float4 *>(s_recb + (kTileThreads / 32) * kAdjRing);
+  int *s_perm = reinterpret_cast<int *>(s_unit + (kTileThreads / 32) * 32);
   if (fcache)
     for (int e = 0; e < 125; ++e) s_facc[e][threadIdx.x] = 0.f;
   __syncthreads();
@@ -463,27 +464,45 @@ __global__ void __launch_bounds__(kTileThreads, INTERP ? 3 : 4)
   float4 *rec_a = s_rec + warp * kAdjRing;
   int *rec_b = s_recb + warp * kAdjRing;
   float4 *unit_w = s_unit + warp * 32;
+  int *perm = s_perm + warp * 32;
 
-  // structure-factor gradient state of this lane (as in the kernel above)
+  // structure-factor gradient state of this lane (as in the kernel above):
+  // the packed lattice point whose 5x5x5 column the lane holds (-1: none)
   long long near_idx = -1;
   double near_sum = 0.0;
-  int held[3] = {0, 0, 0};
-  bool holding = false;
-  auto flush_node = [&]() {
-    if (!holding) return;
-    for (int e = 0; e < 125; ++e) {
-      const float v = s_facc[e][threadIdx.x];
-      if (v == 0.f) continue;
-      s_facc[e][threadIdx.x] = 0.f;
-      const int i = e / 25, j = (e / 5) % 5, k = e % 5;
-      atomicAdd(g.gradF + nb_idx(a.check, NB_SITE_GRADF,
-                                 ((long long)(held[0] - 2 + i) * a.hn[1] +
-                                  (held[1] - 2 + j)) * a.hn[2] +
-                                     (held[2] - 2 + k),
-                                 table_size(a)),
-                (double)v);
+  int held_key = -1;
+  // Flushes, cooperatively, the columns of the lanes with `need`: lanes
+  // that hold the same lattice point are summed entry by entry (in FP32,
+  // in lane order) and each touched node gets one FP64 atomic; the 125
+  // entries of a group are split over the 32 lanes.  Called by all lanes.
+  auto flush_columns = [&](bool need) {
+    unsigned todo = __ballot_sync(0xffffffffu, need && held_key >= 0);
+    while (todo) {
+      const int key = __shfl_sync(0xffffffffu, held_key, __ffs(todo) - 1);
+      const unsigned grp =
+          __ballot_sync(0xffffffffu, need && held_key == key && key >= 0);
+      todo &= ~grp;
+      const int c0 = (key & 1023) - 1, c1 = ((key >> 10) & 1023) - 1,
+                c2 = ((key >> 20) & 1023) - 1;
+      for (int e = lane; e < 125; e += 32) {
+        float v = 0.f;
+        for (unsigned m = grp; m; m &= m - 1) {
+          const int t = warp * 32 + __ffs(m) - 1;
+          v += s_facc[e][t];
+          s_facc[e][t] = 0.f;
+        }
+        if (v != 0.f) {
+          const int i = e / 25, j = (e / 5) % 5, k = e % 5;
+          atomicAdd(g.gradF + nb_idx(a.check, NB_SITE_GRADF,
+                                     ((long long)(c0 - 2 + i) * a.hn[1] +
+                                      (c1 - 2 + j)) * a.hn[2] + (c2 - 2 + k),
+                                     table_size(a)),
+                    (double)v);
+        }
+      }
     }
-    holding = false;
+    if (need) held_key = -1;
+    __syncwarp();
   };
 
   const float N2[3] = {a.N[0] * a.N[0], a.N[1] * a.N[1], a.N[2] * a.N[2]};
@@ -510,7 +529,33 @@ __global__ void __launch_bounds__(kTileThreads, INTERP ? 3 : 4)
   // evaluates records head .. head + cnt - 1 (cnt <= 32), one per lane
   auto eval_pass = [&](int cnt) {
     const bool v = lane < cnt;
-    const int slot = (head + lane) & (kAdjRing - 1);
+    int slot = (head + lane) & (kAdjRing - 1);
+    if (HASF) {
+      // the pass's records in the order of their lattice points (ties in
+      // ring order): lanes then keep the node of their column across
+      // passes more often, and flush it less
+      const int key = v ? __float_as_int(rec_a[slot].w) : 0x7fffffff;
+      bool placed = !v;
+      int pos = 0, base = 0;
+      while (__any_sync(0xffffffffu, !placed)) {
+        const int kmin = __reduce_min_sync(0xffffffffu, placed ? 0x7fffffff : key);
+        const unsigned grp = __ballot_sync(0xffffffffu, !placed && key == kmin);
+        if (!placed && key == kmin) {
+          pos = base + __popc(grp & ((1u << lane) - 1u));
+          placed = true;
+        }
+        base += __popc(grp);
+      }
+      if (v) perm[pos] = slot;
+      __syncwarp();
+      if (v) slot = perm[lane];
+      __syncwarp();
+      // a lane whose record is at another lattice point than its column
+      // flushes the column first
+      if (INTERP)
+        flush_columns(v && held_key >= 0 &&
+                      __float_as_int(rec_a[slot].w) != held_key);
+    }
     head += cnt;
     if (v) {
       const float4 ra = rec_a[slot];
@@ -615,14 +660,7 @@ __global__ void __launch_bounds__(kTileThreads, INTERP ? 3 : 4)
       if (HASF) {
         const float gvf = Wt * scalef * (2.f * fc * fl2 * w);
         if (tri) {
-          if (!holding || n[0] != held[0] || n[1] != held[1] ||
-              n[2] != held[2]) {
-            flush_node();
-            held[0] = n[0];
-            held[1] = n[1];
-            held[2] = n[2];
-            holding = true;
-          }
+          held_key = npk;  // the column was flushed unless it holds npk
           const int o0 = fl[0] - n[0] + 1, o1 = fl[1] - n[1] + 1,
                     o2 = fl[2] - n[2] + 1;
 #pragma unroll
@@ -797,7 +835,7 @@ __global__ void __launch_bounds__(kTileThreads, INTERP ? 3 : 4)
       }
     }
   }
-  if (fcache) flush_node();
+  if (fcache) flush_columns(true);
   if (HASF && near_idx >= 0) atomicAdd(g.gradF + nb_idx(a.check, NB_SITE_GRADF, near_idx, table_size(a)), near_sum);
 }
 
