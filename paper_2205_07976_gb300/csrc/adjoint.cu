@@ -116,7 +116,7 @@ template <int HASF, int INTERP>
 __global__ void __launch_bounds__(kTileThreads, INTERP ? 3 : 4)
     spots_adjoint_kernel(AdjointArgs g) {
   const SpotArgs &a = g.a;
-  extern __shared__ float smf[];
+  extern __shared__ __align__(16) float smf[];
   float *s_axh = smf;
   float *s_axl = smf + a.PM * 9;
   float *s_src = smf + 2 * a.PM * 9;
@@ -417,8 +417,10 @@ constexpr int kAdjFold = 16;  // passes between folds into FP64
 
 __host__ __device__ inline size_t adj_ring_floats(int PM, int S,
                                                   bool f_cache) {
+  // the tables, then (F gradient) each thread's 5x5x4 column as 25 float4
+  // (16-byte aligned: 2 PM 9 + 12 S + 54 PM is a multiple of 4)
   size_t fl = (size_t)2 * PM * 9 + (size_t)S * SRC32_STRIDE + (size_t)PM * 54 +
-              (f_cache ? (size_t)125 * kTileThreads : 0);
+              (f_cache ? (size_t)100 * kTileThreads : 0);
   return (fl + 3) & ~(size_t)3;  // 16-byte aligned records after it
 }
 
@@ -434,7 +436,7 @@ template <int HASF, int INTERP>
 __global__ void __launch_bounds__(kTileThreads, INTERP ? 3 : 4)
     spots_adjoint_ring_kernel(AdjointArgs g) {
   const SpotArgs &a = g.a;
-  extern __shared__ float smf[];
+  extern __shared__ __align__(16) float smf[];
   float *s_axh = smf;
   float *s_axl = smf + a.PM * 9;
   float *s_src = smf + 2 * a.PM * 9;
@@ -448,8 +450,8 @@ __global__ void __launch_bounds__(kTileThreads, INTERP ? 3 : 4)
   for (int i = threadIdx.x; i < a.PM * 54; i += blockDim.x)
     s_dax[i] = g.dax[i];
   const bool fcache = INTERP && HASF;
-  float (*s_facc)[kTileThreads] =
-      reinterpret_cast<float (*)[kTileThreads]>(s_dax + a.PM * 54);
+  float4 (*s_col)[kTileThreads] =
+      reinterpret_cast<float4 (*)[kTileThreads]>(s_dax + a.PM * 54);
   float4 *s_rec = reinterpret_cast<float4 *>(
       smf + adj_ring_floats(a.PM, a.S, fcache));
   int *s_recb = reinterpret_cast<int *>(s_rec + (kTileThreads / 32) * kAdjRing);
@@ -457,7 +459,8 @@ __global__ void __launch_bounds__(kTileThreads, INTERP ? 3 : 4)
       reinterpret_cast<float4 *>(s_recb + (kTileThreads / 32) * kAdjRing);
   int *s_perm = reinterpret_cast<int *>(s_unit + (kTileThreads / 32) * 32);
   if (fcache)
-    for (int e = 0; e < 125; ++e) s_facc[e][threadIdx.x] = 0.f;
+    for (int r = 0; r < 25; ++r)
+      s_col[r][threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
   __syncthreads();
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -466,15 +469,19 @@ __global__ void __launch_bounds__(kTileThreads, INTERP ? 3 : 4)
   float4 *unit_w = s_unit + warp * 32;
   int *perm = s_perm + warp * 32;
 
-  // structure-factor gradient state of this lane (as in the kernel above):
-  // the packed lattice point whose 5x5x5 column the lane holds (-1: none)
+  // structure-factor gradient state of this lane.  A tricubic term near
+  // lattice point n with its cell starting at fl touches nodes
+  // fl - 1 .. fl + 2 on each axis: the lane sums them in a column of 5 x 5
+  // nodes around (n_h, n_k) by the 4 nodes fl_l - 1 .. fl_l + 2 along l (a
+  // float4 per (h, k) node), keyed by (n_h, n_k, fl_l) packed like a
+  // record's lattice point (-1: no column)
   long long near_idx = -1;
   double near_sum = 0.0;
   int held_key = -1;
   // Flushes, cooperatively, the columns of the lanes with `need`: lanes
-  // that hold the same lattice point are summed entry by entry (in FP32,
-  // in lane order) and each touched node gets one FP64 atomic; the 125
-  // entries of a group are split over the 32 lanes.  Called by all lanes.
+  // with the same key are summed entry by entry (in FP32, in lane order)
+  // and each touched node gets one FP64 atomic; the 100 entries of a group
+  // are split over the 32 lanes.  Called by all lanes.
   auto flush_columns = [&](bool need) {
     unsigned todo = __ballot_sync(0xffffffffu, need && held_key >= 0);
     while (todo) {
@@ -484,25 +491,33 @@ __global__ void __launch_bounds__(kTileThreads, INTERP ? 3 : 4)
       todo &= ~grp;
       const int c0 = (key & 1023) - 1, c1 = ((key >> 10) & 1023) - 1,
                 c2 = ((key >> 20) & 1023) - 1;
-      for (int e = lane; e < 125; e += 32) {
+      for (int e = lane; e < 100; e += 32) {
+        const int r = e >> 2, kk = e & 3;
         float v = 0.f;
         for (unsigned m = grp; m; m &= m - 1) {
-          const int t = warp * 32 + __ffs(m) - 1;
-          v += s_facc[e][t];
-          s_facc[e][t] = 0.f;
+          float *col = reinterpret_cast<float *>(
+              &s_col[r][warp * 32 + __ffs(m) - 1]);
+          v += col[kk];
+          col[kk] = 0.f;
         }
-        if (v != 0.f) {
-          const int i = e / 25, j = (e / 5) % 5, k = e % 5;
+        if (v != 0.f)
           atomicAdd(g.gradF + nb_idx(a.check, NB_SITE_GRADF,
-                                     ((long long)(c0 - 2 + i) * a.hn[1] +
-                                      (c1 - 2 + j)) * a.hn[2] + (c2 - 2 + k),
+                                     ((long long)(c0 - 2 + r / 5) * a.hn[1] +
+                                      (c1 - 2 + r % 5)) * a.hn[2] +
+                                         (c2 - 1 + kk),
                                      table_size(a)),
                     (double)v);
-        }
       }
     }
     if (need) held_key = -1;
     __syncwarp();
+  };
+  // a record's column key: its lattice point with l replaced by the start
+  // of its cell along l
+  auto column_key = [&](float4 ra) {
+    const int npk = __float_as_int(ra.w);
+    return (npk & 0xfffff) |
+           ((((npk >> 20) & 1023) - (ra.z < 0.f ? 1 : 0)) << 20);
   };
 
   const float N2[3] = {a.N[0] * a.N[0], a.N[1] * a.N[1], a.N[2] * a.N[2]};
@@ -534,7 +549,7 @@ __global__ void __launch_bounds__(kTileThreads, INTERP ? 3 : 4)
       // the pass's records in the order of their lattice points (ties in
       // ring order): lanes then keep the node of their column across
       // passes more often, and flush it less
-      const int key = v ? __float_as_int(rec_a[slot].w) : 0x7fffffff;
+      const int key = v ? column_key(rec_a[slot]) : 0x7fffffff;
       bool placed = !v;
       int pos = 0, base = 0;
       while (__any_sync(0xffffffffu, !placed)) {
@@ -550,11 +565,11 @@ __global__ void __launch_bounds__(kTileThreads, INTERP ? 3 : 4)
       __syncwarp();
       if (v) slot = perm[lane];
       __syncwarp();
-      // a lane whose record is at another lattice point than its column
+      // a lane whose record has another column key than its column
       // flushes the column first
       if (INTERP)
         flush_columns(v && held_key >= 0 &&
-                      __float_as_int(rec_a[slot].w) != held_key);
+                      column_key(rec_a[slot]) != held_key);
     }
     head += cnt;
     if (v) {
@@ -660,19 +675,21 @@ __global__ void __launch_bounds__(kTileThreads, INTERP ? 3 : 4)
       if (HASF) {
         const float gvf = Wt * scalef * (2.f * fc * fl2 * w);
         if (tri) {
-          held_key = npk;  // the column was flushed unless it holds npk
-          const int o0 = fl[0] - n[0] + 1, o1 = fl[1] - n[1] + 1,
-                    o2 = fl[2] - n[2] + 1;
+          // the column was flushed unless it holds this key
+          held_key = (npk & 0xfffff) | ((fl[2] + 1) << 20);
+          const int o0 = fl[0] - n[0] + 1, o1 = fl[1] - n[1] + 1;
+          float4 *col = &s_col[o0 * 5 + o1][threadIdx.x];
 #pragma unroll
           for (int i = 0; i < 4; ++i)
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
               const float wij = gvf * (wv[0][i] * wv[1][j]);
-              const int row = ((o0 + i) * 5 + (o1 + j)) * 5 + o2;
-#pragma unroll
-              for (int kk = 0; kk < 4; ++kk)
-                s_facc[row + kk][threadIdx.x] =
-                    fmaf(wij, wv[2][kk], s_facc[row + kk][threadIdx.x]);
+              float4 c = col[(i * 5 + j) * kTileThreads];
+              c.x = fmaf(wij, wv[2][0], c.x);
+              c.y = fmaf(wij, wv[2][1], c.y);
+              c.z = fmaf(wij, wv[2][2], c.z);
+              c.w = fmaf(wij, wv[2][3], c.w);
+              col[(i * 5 + j) * kTileThreads] = c;
             }
         } else if (inside) {
           if (fidx != near_idx) {
