@@ -53,12 +53,12 @@ MAX_SM_MHZ = 2070.0  # GB300's maximum SM clock
 # kernel, from one ncu capture (profiles/spots_split_large_shot_dram.txt:
 # the mean of two launches);
 # valid only while the kernel sources hash to the value they had then
-TRAFFIC_CAPTURE = {"bytes": (80208384 + 22526464 + 79908608 + 23491072) // 2,
+TRAFFIC_CAPTURE = {"bytes": (80041216 + 23120640 + 80218880 + 23527936) // 2,
                    "sources": ["paper_2205_07976_gb300/csrc/spots_split.cu",
                                "paper_2205_07976_gb300/csrc/split_pixel.cuh",
                                "paper_2205_07976_gb300/csrc/mixed_common.cuh",
                                "paper_2205_07976_gb300/csrc/nbgb_internal.cuh"],
-                   "sha256_16": "c15f8a79666a519f"}
+                   "sha256_16": "a8083c8e1426134c"}
 
 
 def captured_traffic():
@@ -75,13 +75,13 @@ def captured_traffic():
 # Pipe utilisation (% of active cycles) of the warp-per-pixel kernel from
 # one ncu --set full capture on a 512x512 window of the large shot
 # (profiles/spots_split_window512_full.txt), keyed like the traffic figure
-PIPES_CAPTURE = {"sm__pipe_fma_cycles_active_pct": 35.0,
-                 "sm__pipe_alu_cycles_active_pct": 41.2,
+PIPES_CAPTURE = {"sm__pipe_fma_cycles_active_pct": 36.2,
+                 "sm__pipe_alu_cycles_active_pct": 40.0,
                  "sm__inst_executed_pipe_lsu_pct": 41.2,
-                 "smsp__issue_active_pct": 74.1,
-                 "l1tex__data_pipe_lsu_wavefronts_pct": 53.8,
+                 "smsp__issue_active_pct": 73.9,
+                 "l1tex__data_pipe_lsu_wavefronts_pct": 55.2,
                  "window": "512x512 centred on the large shot",
-                 "sha256_16": "c15f8a79666a519f"}
+                 "sha256_16": "a8083c8e1426134c"}
 
 
 def captured_pipes():

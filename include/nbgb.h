@@ -437,10 +437,10 @@ int nb_set_option(nb_sim *sim, int key, long long value);
  * rewrites it (the counters are cleared before the kernel runs), so calls
  * whose work overlaps on the GPU race: serialise them.  The first call on a
  * device looks up the array's device address once (cudaGetSymbolAddress
- * with that device current).  The call waits for its table set-up on
- * `cuda_stream` (an 8-byte device-to-host read) and then queues the kernel
- * asynchronously; it blocks the host, and cannot be captured into a CUDA
- * graph.
+ * with that device current): make that first call before any stream
+ * capture.  Each call waits on the host for its table set-up on
+ * `cuda_stream` (an 8-byte device-to-host read), then queues the kernel
+ * asynchronously.
  * Errors: NB_EINVAL for NULL pointers, sizes outside the limits above, a
  * non-unit dir, e_vec parallel to dir, or bad geometry; NB_ECUDA if a CUDA
  * call fails. */

@@ -3,13 +3,23 @@
 // double accumulate of addArray (Listing 1).
 //
 // Loop nest per pixel: subpixel x sensor layer -> source -> phi x mosaic.
-// Everything is FP64, evaluated in the order the definition is written
-// (this file is compiled without FMA contraction), so that the result
-// differs from any other faithful FP64 evaluation only by the rounding of
-// the transcendental functions.  Only loop invariants are hoisted (pixel
-// position, solid angle, capture fraction per subpixel/layer; scattering
-// vector and polarization per source).  The rotated axes and the source
-// table are staged in shared memory per block.
+// Everything is FP64 and this file is compiled without FMA contraction.
+// The Miller indices, the fractional offsets and the sinc are evaluated in
+// the order the definition is written, so h and the sinc's phases are
+// bitwise those of any other uncontracted FP64 evaluation (the sinc at
+// N = 200 multiplies h's rounding by pi N).  Two parts that are not
+// sensitive to the last bits are arranged for the FP64 pipe, which on this
+// part issues at 1/64 of the FP32 rate and so sets the kernel's time:
+//   * the Gaussian exponent and the Lagrange weights multiply by 1/0.63
+//     and 1/6 instead of dividing (an IEEE division is a sequence of about
+//     ten FP64 instructions; the result moves by an ulp);
+//   * the tricubic sum is nested per axis, sum_i w_i sum_j w_j sum_k w_k
+//     F_ijk: 147 FP64 operations instead of 256 for the flat triple
+//     product sum (the rounding differs at the 1e-15 level).
+// Only loop invariants are hoisted (pixel position, solid angle, capture
+// fraction per subpixel/layer; scattering vector and polarization per
+// source).  The rotated axes and the source table are staged in shared
+// memory per block.
 #include "nbgb_internal.cuh"
 
 namespace nbgb {
@@ -34,7 +44,8 @@ __device__ __forceinline__ double flatt_f64(const SpotArgs &a,
       rad2 += a.N64[x] * a.N64[x] * fr * fr;
     }
   }
-  if (SHAPE == 1) r = a.N64[0] * a.N64[1] * a.N64[2] * exp(-rad2 / 0.63);
+  if (SHAPE == 1)
+    r = a.N64[0] * a.N64[1] * a.N64[2] * exp(-rad2 * (1.0 / 0.63));
   return r;
 }
 
@@ -60,17 +71,18 @@ __device__ __forceinline__ double fcell_f64(const SpotArgs &a,
     }
     if (in_table(a, fl[0] - 1, fl[1] - 1, fl[2] - 1) &&
         in_table(a, fl[0] + 2, fl[1] + 2, fl[2] + 2)) {
-      // 4-point Lagrange weights on nodes -1, 0, 1, 2
+      // 4-point Lagrange weights on nodes -1, 0, 1, 2, from the shared
+      // products t (t - 1) and (t + 1)(t - 2)
       double w[3][4];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        double t = x[c];
-        w[c][0] = -t * (t - 1.0) * (t - 2.0) / 6.0;
-        w[c][1] = (t + 1.0) * (t - 1.0) * (t - 2.0) / 2.0;
-        w[c][2] = -(t + 1.0) * t * (t - 2.0) / 2.0;
-        w[c][3] = (t + 1.0) * t * (t - 1.0) / 6.0;
+        const double t = x[c], tm1 = t - 1.0, tm2 = t - 2.0, tp1 = t + 1.0;
+        const double p = t * tm1, q = tp1 * tm2;
+        w[c][0] = p * tm2 * (-1.0 / 6.0);
+        w[c][1] = q * tm1 * 0.5;
+        w[c][2] = q * t * -0.5;
+        w[c][3] = p * tp1 * (1.0 / 6.0);
       }
-      double sum = 0.0;
       long long off =
           ((long long)(fl[0] - 1) * a.hn[1] + (fl[1] - 1)) * a.hn[2] +
           (fl[2] - 1);
@@ -79,14 +91,22 @@ __device__ __forceinline__ double fcell_f64(const SpotArgs &a,
         if (nb_idx(a.check, NB_SITE_STENCIL, last, table_size(a)) != last)
           off = 0;
       }
-      for (int i = 0; i < 4; ++i)
+      double sum = 0.0;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        double si = 0.0;
+#pragma unroll
         for (int j = 0; j < 4; ++j) {
           const float *row =
               a.F + off + ((long long)i * a.hn[1] + j) * a.hn[2];
-#pragma unroll
-          for (int k = 0; k < 4; ++k)
-            sum += w[0][i] * w[1][j] * w[2][k] * (double)__ldg(row + k);
+          const double sj = w[2][0] * (double)__ldg(row) +
+                            w[2][1] * (double)__ldg(row + 1) +
+                            w[2][2] * (double)__ldg(row + 2) +
+                            w[2][3] * (double)__ldg(row + 3);
+          si += w[1][j] * sj;
         }
+        sum += w[0][i] * si;
+      }
       return sum;
     }
   }
