@@ -98,8 +98,8 @@ struct nb_sim {
   bool have_params = false;
   double pU[9] = {0}, pcell[3] = {0}, prot[3] = {0};
   double daxes[6][9];  // d(lab axes)/d(tx, ty, tz, a, b, c)
-  DevBuf d_dax, d_part, d_grad, d_F4, d_C4;
-  bool F4_valid = false, C4_valid = false;
+  DevBuf d_dax, d_part, d_grad, d_F4, d_C4, d_F64t;
+  bool F4_valid = false, C4_valid = false, F64_valid = false;
   int has_div = 0;
   double u0 = 0;
   bool tables_dirty = true;
@@ -504,6 +504,7 @@ static void fill_args(const nb_sim *s, SpotArgs &a) {
   a.F = (const float *)s->d_F.p;
   a.F4 = s->F4_valid ? (const float4 *)s->d_F4.p : nullptr;
   a.C4 = s->C4_valid ? (const float4 *)s->d_C4.p : nullptr;
+  a.F64t = s->F64_valid ? (const double *)s->d_F64t.p : nullptr;
   a.defF = (float)s->defF;
   a.defF64 = s->defF;
   a.S = s->n_src;
@@ -616,8 +617,8 @@ int nb_free(nb_sim *sim) {
                       &sim->d_image,  &sim->d_list,  &sim->d_tmp,
                       &sim->d_stats,  &sim->d_work,  &sim->d_srcq,  &sim->d_check,  &sim->d_dax,
                       &sim->d_part,   &sim->d_grad,  &sim->d_F4,
-                      &sim->d_C4,     &sim->d_bg64,  &sim->d_bg32,
-                      &sim->d_bgrng};
+                      &sim->d_C4,     &sim->d_F64t,  &sim->d_bg64,
+                      &sim->d_bg32,   &sim->d_bgrng};
     for (DevBuf *b : bufs) b->release();
   }
   delete sim;
@@ -687,6 +688,7 @@ int nb_set_crystal(nb_sim *s, const double axes[9], const double *umats,
     s->have_F = true;
     s->F4_valid = false;
     s->C4_valid = false;
+    s->F64_valid = false;
   } else {
     if (interp == NB_INTERP_NEAREST || interp == NB_INTERP_TRICUBIC)
       s->interp = interp;
@@ -713,6 +715,7 @@ int nb_set_fcell_device(nb_sim *s, const float *F, size_t n_elems) {
   // the derived tables are rebuilt from the new values at the next launch
   s->F4_valid = false;
   s->C4_valid = false;
+  s->F64_valid = false;
   return NB_OK;
 }
 
@@ -881,6 +884,21 @@ static void ensure_sliding_table(nb_sim *s) {
     s->F4_valid = true;
 }
 
+// F in FP64 for the NB_F64 kernel: its reads then need no conversion, each
+// of which costs an FP64-pipe instruction (2x the table's memory; skipped,
+// and the kernel converts, if that allocation fails)
+static void ensure_f64_table(nb_sim *s) {
+  if (s->F64_valid || s->precision != NB_F64) return;
+  const long long n = (long long)s->hn[0] * s->hn[1] * s->hn[2];
+  if (s->d_F64t.ensure((size_t)n * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  if (nbgb::build_f64_table((const float *)s->d_F.p, n,
+                            (double *)s->d_F64t.p, s->stream) == cudaSuccess)
+    s->F64_valid = true;
+}
+
 // the tricubic polynomial of every table cell (64 floats per cell) for the
 // warp-per-pixel kernel; skipped above 2 GB, for an axis longer than 1000
 // nodes, or if the allocation fails
@@ -910,6 +928,7 @@ static int launch(nb_sim *s, const long long *dev_list, long long n_list) {
   int rc = upload_tables(s);
   if (rc != NB_OK) return rc;
   ensure_sliding_table(s);
+  ensure_f64_table(s);
   SpotArgs a;
   fill_args(s, a);
   a.pixlist = dev_list;

@@ -122,6 +122,9 @@ struct SpotArgs {
   float N6;  // (Na Nb Nc)^2
   int shape, interp;
   const float *F;
+  // optional copy of F in FP64 for the NB_F64 kernel (null: each read
+  // converts F's float)
+  const double *F64t;
   // optional copy of F for tricubic lookups: F4[i][j][l] holds
   // F[i][j][l..l+3] (zero past the end), one 16-byte load per stencil row
   const float4 *F4;
@@ -353,6 +356,8 @@ void rotated_axes_table(const double *lab, const double *umats, int n_mosaic,
                         const double *spindle, std::vector<double> &ax);
 
 cudaError_t launch_spots_f64(const SpotArgs &a, cudaStream_t st);
+cudaError_t build_f64_table(const float *F, long long n, double *F64t,
+                            cudaStream_t st);
 cudaError_t build_sliding_table(const float *F, const int hn[3], float4 *F4,
                                 cudaStream_t st);
 cudaError_t build_cell_polynomials(const float *F, const int hn[3], float4 *C4,

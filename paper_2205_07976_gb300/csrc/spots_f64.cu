@@ -13,13 +13,18 @@
 //   * the Gaussian exponent and the Lagrange weights multiply by 1/0.63
 //     and 1/6 instead of dividing (an IEEE division is a sequence of about
 //     ten FP64 instructions; the result moves by an ulp);
-//   * the tricubic sum is nested per axis, sum_i w_i sum_j w_j sum_k w_k
-//     F_ijk: 147 FP64 operations instead of 256 for the flat triple
-//     product sum (the rounding differs at the 1e-15 level).
+//   * the tricubic sum is nested per axis in explicit FMAs, sum_i w_i
+//     sum_j w_j sum_k w_k F_ijk: 84 FP64 operations instead of 256 for the
+//     flat triple product sum (the rounding differs at the 1e-15 level);
+//   * the table is read from an FP64 copy (a float-to-double conversion
+//     is an FP64-pipe instruction too), and the cell's first node comes
+//     from the nearest lattice point instead of a floor;
+//   * the step's weight, capture, polarization and solid angle are one
+//     factor per source.
 // Only loop invariants are hoisted (pixel position, solid angle, capture
-// fraction per subpixel/layer; scattering vector and polarization per
-// source).  The rotated axes and the source table are staged in shared
-// memory per block.
+// fraction per subpixel/layer; scattering vector, polarization and that
+// factor per source).  The rotated axes and the source table are staged in
+// shared memory per block.
 #include "nbgb_internal.cuh"
 
 namespace nbgb {
@@ -56,18 +61,53 @@ __device__ __forceinline__ bool in_table(const SpotArgs &a, long long i,
          (unsigned long long)k < (unsigned long long)a.hn[2];
 }
 
+// The tricubic sum over the 4x4x4 stencil whose first node has flat index
+// off: nested per axis in explicit FMAs, sum_i w_i sum_j w_j sum_k w_k
+// F_ijk (84 FP64 operations; a flat triple-product sum takes 256).  T is
+// double (the FP64 copy of the table) or float (each read converted).
+template <typename T>
+__device__ __forceinline__ double tricubic_sum(const SpotArgs &a,
+                                               const T *tab, long long off,
+                                               const double w[3][4]) {
+  double sum = 0.0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    double si = 0.0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const T *row = tab + off + ((long long)i * a.hn[1] + j) * a.hn[2];
+      double sj = w[2][0] * (double)__ldg(row);
+      sj = fma(w[2][1], (double)__ldg(row + 1), sj);
+      sj = fma(w[2][2], (double)__ldg(row + 2), sj);
+      sj = fma(w[2][3], (double)__ldg(row + 3), sj);
+      si = j ? fma(w[1][j], sj, si) : w[1][0] * sj;
+    }
+    sum = i ? fma(w[0][i], si, sum) : w[0][0] * si;
+  }
+  return sum;
+}
+
+// F_cell at h, whose nearest lattice point is n (ties down, flatt_f64):
+// the cell's first node is floor(h) = n - 1 where h < n, else n, so no
+// floor and no second float-to-integer conversion per axis are needed
 template <int INTERP>
 __device__ __forceinline__ double fcell_f64(const SpotArgs &a,
                                             const double h[3],
                                             const double n[3]) {
+  long long nn[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) nn[c] = (long long)n[c] - a.hmin[c];
   if (INTERP == 1) {
     long long fl[3];
     double x[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      double f = floor(h[c]);
-      fl[c] = (long long)f - a.hmin[c];
-      x[c] = h[c] - f;
+      // h - n is exact (h and n lie within 1/2), and so is h - floor(h)
+      // for h < n: (h - n) + 1 holds no bit below h's last one
+      const double fr = h[c] - n[c];
+      const bool below = fr < 0.0;
+      fl[c] = nn[c] - (below ? 1 : 0);
+      x[c] = below ? fr + 1.0 : fr;
     }
     if (in_table(a, fl[0] - 1, fl[1] - 1, fl[2] - 1) &&
         in_table(a, fl[0] + 2, fl[1] + 2, fl[2] + 2)) {
@@ -91,32 +131,31 @@ __device__ __forceinline__ double fcell_f64(const SpotArgs &a,
         if (nb_idx(a.check, NB_SITE_STENCIL, last, table_size(a)) != last)
           off = 0;
       }
-      double sum = 0.0;
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        double si = 0.0;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const float *row =
-              a.F + off + ((long long)i * a.hn[1] + j) * a.hn[2];
-          const double sj = w[2][0] * (double)__ldg(row) +
-                            w[2][1] * (double)__ldg(row + 1) +
-                            w[2][2] * (double)__ldg(row + 2) +
-                            w[2][3] * (double)__ldg(row + 3);
-          si += w[1][j] * sj;
-        }
-        sum += w[0][i] * si;
-      }
-      return sum;
+      return a.F64t ? tricubic_sum(a, a.F64t, off, w)
+                    : tricubic_sum(a, a.F, off, w);
     }
   }
-  long long i = (long long)n[0] - a.hmin[0], j = (long long)n[1] - a.hmin[1],
-            k = (long long)n[2] - a.hmin[2];
-  if (in_table(a, i, j, k))
-    return (double)__ldg(a.F + nb_idx(a.check, NB_SITE_F,
-                                      (i * a.hn[1] + j) * a.hn[2] + k,
-                                      table_size(a)));
+  if (in_table(a, nn[0], nn[1], nn[2])) {
+    const long long idx = nb_idx(a.check, NB_SITE_F,
+                                 (nn[0] * a.hn[1] + nn[1]) * a.hn[2] + nn[2],
+                                 table_size(a));
+    return a.F64t ? __ldg(a.F64t + idx) : (double)__ldg(a.F + idx);
+  }
   return a.defF64;
+}
+
+// F as doubles, for the NB_F64 kernel's reads
+__global__ void f64_table_kernel(const float *F, long long n, double *F64t) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    F64t[i] = (double)F[i];
+}
+
+cudaError_t build_f64_table(const float *F, long long n, double *F64t,
+                            cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  f64_table_kernel<<<1216, 256, 0, st>>>(F, n, F64t);
+  return cudaGetLastError();
 }
 
 template <int SHAPE, int INTERP>
@@ -169,14 +208,15 @@ __global__ void __launch_bounds__(kTileThreads, 4)
           double c2 = dot3d(d, dir), x = dot3d(d, src + SRC64_E),
                  y = dot3d(d, src + SRC64_B);
           double pol = 0.5 * (1.0 + c2 * c2 - a.kahn64 * (x * x - y * y));
-          double wfac = src[SRC64_W];
+          // the step's factors that do not depend on phi x mosaic
+          const double wcpo = src[SRC64_W] * cap * pol * omega;
           for (int pm = 0; pm < a.PM; ++pm) {
             const double *A = s_ax + pm * 9;
             double h[3] = {dot3d(A, Sv), dot3d(A + 3, Sv), dot3d(A + 6, Sv)};
             double n[3];
             double fl = flatt_f64<SHAPE>(a, h, n);
             double fc = fcell_f64<INTERP>(a, h, n);
-            acc += fc * fc * fl * fl * wfac * cap * pol * omega;
+            acc += fc * fc * fl * fl * wcpo;
           }
         }
       }
