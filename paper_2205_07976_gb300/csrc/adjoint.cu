@@ -140,7 +140,9 @@ __global__ void __launch_bounds__(kTileThreads, INTERP ? 3 : 4)
   float (*s_facc)[kTileThreads] =
       reinterpret_cast<float (*)[kTileThreads]>(s_dax + a.PM * 54);
   long long near_idx = -1;  // nearest lookup: the entry being summed
-  double near_sum = 0.0;
+  // its run of terms, summed in FP32 (an FP64 instruction per term would
+  // cost 64 FP32 ones on this part) and added to the FP64 gradient once
+  float near_sum = 0.f;
   int held[3] = {0, 0, 0};  // the lattice point held (table-relative)
   bool holding = false;
   auto flush_node = [&]() {
@@ -201,7 +203,7 @@ __global__ void __launch_bounds__(kTileThreads, INTERP ? 3 : 4)
                 ye = df[0] * a.b0f[0] + df[1] * a.b0f[1] + df[2] * a.b0f[2];
           float scal = omega * cap * 0.5f *
                        (1.f + c2 * c2 - kahn * (xe * xe - ye * ye));
-          const double fscal = wks * (double)scal;  // for the F scatter
+          const float fscal = (float)(wks * (double)scal);  // F scatter
           Kahan acc0;
           float acc[9];
 #pragma unroll
@@ -331,7 +333,7 @@ __global__ void __launch_bounds__(kTileThreads, INTERP ? 3 : 4)
                                           (1.f / 0.63f),
                                   acc[6 + x]);
               if (HASF) {
-                double gv = fscal * (double)(2.f * fc * fl2 * w);
+                const float gvf = fscal * (2.f * fc * fl2 * w);
                 if (tri) {
                   if (!holding || n[0] != held[0] || n[1] != held[1] ||
                       n[2] != held[2]) {
@@ -344,7 +346,6 @@ __global__ void __launch_bounds__(kTileThreads, INTERP ? 3 : 4)
                   // the stencil starts at fl - 1 = n - 2 + o, o = 0 or 1
                   const int o0 = fl[0] - n[0] + 1, o1 = fl[1] - n[1] + 1,
                             o2 = fl[2] - n[2] + 1;
-                  const float gvf = (float)gv;
 #pragma unroll
                   for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -360,11 +361,11 @@ __global__ void __launch_bounds__(kTileThreads, INTERP ? 3 : 4)
                   // consecutive terms mostly hit the same entry: add up
                   // in a register, one atomic per run of equal entries
                   if (fidx != near_idx) {
-                    if (near_idx >= 0) atomicAdd(g.gradF + nb_idx(a.check, NB_SITE_GRADF, near_idx, table_size(a)), near_sum);
+                    if (near_idx >= 0) atomicAdd(g.gradF + nb_idx(a.check, NB_SITE_GRADF, near_idx, table_size(a)), (double)near_sum);
                     near_idx = fidx;
-                    near_sum = 0.0;
+                    near_sum = 0.f;
                   }
-                  near_sum += gv;
+                  near_sum += gvf;
                 }
               }
             }
@@ -378,7 +379,7 @@ __global__ void __launch_bounds__(kTileThreads, INTERP ? 3 : 4)
     gsum[9] = wp * g.kc * tot[9];  // dI/dscale = I / scale
   }
   if (INTERP && HASF) flush_node();
-  if (HASF && near_idx >= 0) atomicAdd(g.gradF + nb_idx(a.check, NB_SITE_GRADF, near_idx, table_size(a)), near_sum);
+  if (HASF && near_idx >= 0) atomicAdd(g.gradF + nb_idx(a.check, NB_SITE_GRADF, near_idx, table_size(a)), (double)near_sum);
   // block reduction in FP64, fixed order
   __shared__ double red[kTileThreads / 32][kGradN];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
