@@ -53,12 +53,12 @@ MAX_SM_MHZ = 2070.0  # GB300's maximum SM clock
 # kernel, from one ncu capture (profiles/spots_split_large_shot_dram.txt:
 # the mean of two launches);
 # valid only while the kernel sources hash to the value they had then
-TRAFFIC_CAPTURE = {"bytes": (80041216 + 23120640 + 80218880 + 23527936) // 2,
+TRAFFIC_CAPTURE = {"bytes": (80408320 + 22961920 + 80121344 + 23371520) // 2,
                    "sources": ["paper_2205_07976_gb300/csrc/spots_split.cu",
                                "paper_2205_07976_gb300/csrc/split_pixel.cuh",
                                "paper_2205_07976_gb300/csrc/mixed_common.cuh",
                                "paper_2205_07976_gb300/csrc/nbgb_internal.cuh"],
-                   "sha256_16": "a8083c8e1426134c"}
+                   "sha256_16": "068389bc3a988e15"}
 
 
 def captured_traffic():
@@ -81,7 +81,7 @@ PIPES_CAPTURE = {"sm__pipe_fma_cycles_active_pct": 36.2,
                  "smsp__issue_active_pct": 73.9,
                  "l1tex__data_pipe_lsu_wavefronts_pct": 55.2,
                  "window": "512x512 centred on the large shot",
-                 "sha256_16": "a8083c8e1426134c"}
+                 "sha256_16": "068389bc3a988e15"}
 
 
 def captured_pipes():
