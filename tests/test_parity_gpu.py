@@ -291,11 +291,13 @@ def test_work_counts_of_each_kernel():
             assert ev <= w["pairs"] < ps
 
 
-def test_fcell_device_upload_equals_host_upload():
+@pytest.mark.parametrize("precision", ["mixed", "f64"])
+def test_fcell_device_upload_equals_host_upload(precision):
     """nb_set_fcell_device replaces the table's values from device memory:
     the image equals the one with the same table given on the host, for the
-    nearest and the tricubic (cell polynomial) lookups; a wrong size is
-    rejected."""
+    nearest and the tricubic lookups and for the tables derived from F (the
+    cell polynomials of NB_MIXED, the FP64 copy of NB_F64), which a launch
+    before the replacement has built; a wrong size is rejected."""
     torch = pytest.importorskip("torch")
     for interp in (W.INTERP_NEAREST, W.INTERP_TRICUBIC):
         s = W.shrink(W.large_shot(), 24, 16, 2500, 700)
@@ -303,8 +305,9 @@ def test_fcell_device_upload_equals_host_upload():
         F2 = (s.F * np.float32(1.25) + np.float32(3.0)).astype(np.float32)
         t = s.copy()
         t.F = F2
-        ref = nbgb.simulate(t, "mixed", variant="warp")
-        sim = nbgb.Sim("mixed").set_shot(s).set_variant("warp")
+        variant = "warp" if precision == "mixed" else "auto"
+        ref = nbgb.simulate(t, precision, variant=variant)
+        sim = nbgb.Sim(precision).set_shot(s).set_variant(variant)
         sim.add_spots()  # builds the derived tables of the first table
         dF = torch.from_numpy(F2).cuda()
         torch.cuda.synchronize()
@@ -315,8 +318,16 @@ def test_fcell_device_upload_equals_host_upload():
         with pytest.raises(nbgb.NbError) as e:
             sim.set_fcell_device(dF.data_ptr(), dF.numel() - 1)
         assert e.value.code == nbgb.NB_EINVAL
+        # the host route (nb_set_crystal with a new table) as well
+        sim.upload_F(s.F)
+        sim.zero()
+        sim.add_spots()
+        back = sim.image()
         sim.close()
         np.testing.assert_array_equal(got, ref)
+        np.testing.assert_array_equal(
+            back, nbgb.simulate(s, precision, variant=variant))
+        assert back.max() > 0 and not np.array_equal(back, got)
 
 
 def test_single_pixel_and_empty_list():
