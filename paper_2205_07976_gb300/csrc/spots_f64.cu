@@ -11,8 +11,9 @@
 // sensitive to the last bits are arranged for the FP64 pipe, which on this
 // part issues at 1/64 of the FP32 rate and so sets the kernel's time:
 //   * the Gaussian exponent and the Lagrange weights multiply by 1/0.63
-//     and 1/6 instead of dividing (an IEEE division is a sequence of about
-//     ten FP64 instructions; the result moves by an ulp);
+//     and 1/6 instead of dividing, and the sinc divides once per step, not
+//     once per axis (an IEEE division is a sequence of about ten FP64
+//     instructions; the result moves by an ulp or two);
 //   * the tricubic sum is nested per axis in explicit FMAs, sum_i w_i
 //     sum_j w_j sum_k w_k F_ijk: 84 FP64 operations instead of 256 for the
 //     flat triple product sum (the rounding differs at the 1e-15 level);
@@ -36,22 +37,31 @@ __device__ __forceinline__ double dot3d(const double *a, const double *b) {
 template <int SHAPE>
 __device__ __forceinline__ double flatt_f64(const SpotArgs &a,
                                             const double h[3], double n[3]) {
-  double r = 1.0, rad2 = 0.0;
+  // sinc: the three numerators and the three denominators multiplied
+  // separately and divided once (a division is a sequence of about ten
+  // FP64 instructions); an axis with |f| below 1e-100 (f = 0 in practice:
+  // h is a sum of products of order-one values) contributes its limit N,
+  // so the product of denominators cannot underflow
+  double num = 1.0, den = 1.0, rad2 = 0.0;
 #pragma unroll
   for (int x = 0; x < 3; ++x) {
     n[x] = ceil(h[x] - 0.5);  // nearest integer, ties down
     double fr = h[x] - n[x];
     if (SHAPE == 0) {
       // sin(pi N h)/sin(pi h) = +-sin(pi N f)/sin(pi f); the sign drops out
-      r *= (fr == 0.0) ? a.N64[x]
-                       : sin(M_PI * a.N64[x] * fr) / sin(M_PI * fr);
+      if (fabs(fr) < 1e-100) {
+        num *= a.N64[x];
+      } else {
+        num *= sin(M_PI * a.N64[x] * fr);
+        den *= sin(M_PI * fr);
+      }
     } else {
       rad2 += a.N64[x] * a.N64[x] * fr * fr;
     }
   }
   if (SHAPE == 1)
-    r = a.N64[0] * a.N64[1] * a.N64[2] * exp(-rad2 * (1.0 / 0.63));
-  return r;
+    return a.N64[0] * a.N64[1] * a.N64[2] * exp(-rad2 * (1.0 / 0.63));
+  return num / den;
 }
 
 __device__ __forceinline__ bool in_table(const SpotArgs &a, long long i,
