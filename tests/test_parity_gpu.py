@@ -9,6 +9,8 @@ Tolerances (max relative error per pixel):
 Windows are chosen with odd sizes so that every launch has ragged 16x8
 tiles at its right and bottom edges.
 """
+import math
+
 import numpy as np
 import pytest
 
@@ -16,6 +18,7 @@ import oracle
 from paper_2205_07976_gb300 import nbgb
 from paper_2205_07976_gb300 import workloads as W
 from tests.helpers import abs_err_frac, masked_rel_err, rel_err_above
+from tests.test_oracle_pins import bragg_pixel_shot
 
 pytestmark = pytest.mark.gpu
 
@@ -62,6 +65,25 @@ def test_single_shot_f64(c0):
 def test_single_shot_mixed(c0):
     s, ref = c0
     check_mixed(run(s, "mixed"), ref)
+
+
+@pytest.mark.parametrize("shape,interp", [
+    (W.SHAPE_SINC, W.INTERP_NEAREST), (W.SHAPE_GAUSS, W.INTERP_NEAREST),
+    (W.SHAPE_GAUSS, W.INTERP_TRICUBIC), (W.SHAPE_SINC, W.INTERP_TRICUBIC)])
+@pytest.mark.parametrize("hkl", [(1, 2, 3), (-4, 3, 2), (7, -1, -5)])
+def test_single_step_on_a_bragg_condition(shape, interp, hkl):
+    """One pixel whose centre sees reflection hkl exactly, one source, one
+    domain: the closed form r_e^2 fluence scale F_hkl^2 (Na Nb Nc)^2 pol
+    omega (the same case pins the oracle), from every kernel: the FP64
+    form to 1e-11 (h is exact to a few ulp, so the sinc sits at its limit
+    N), the FP32-mixed thread and warp kernels to 1e-5."""
+    s, expected = bragg_pixel_shot(shape, interp, hkl)
+    assert math.isclose(run(s, "f64")[0], expected, rel_tol=1e-11)
+    assert math.isclose(run(s, "mixed", variant="thread")[0], expected,
+                        rel_tol=MIXED_TOL)
+    if shape == W.SHAPE_GAUSS:
+        assert math.isclose(run(s, "mixed", variant="warp")[0], expected,
+                            rel_tol=MIXED_TOL)
 
 
 def test_single_shot_f32_is_finite_and_close(c0):
