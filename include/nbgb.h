@@ -96,6 +96,13 @@ int nb_sim_create(nb_sim **out, int device, int precision, void *cuda_stream);
  *   interp    NB_INTERP_NEAREST (F at the nearest node, default_F outside
  *             the table) or NB_INTERP_TRICUBIC (4-point Lagrange per axis;
  *             nearest where the 4x4x4 stencil leaves the table).
+ * The table is copied to the device.  The first launch after a new table
+ * derives from it what its kernels read: for NB_F64 a copy in doubles (2x
+ * the table's memory), for the FP32 forms with tricubic lookup 16-byte
+ * stencil rows (4x) and, for NB_MIXED's warp-per-pixel kernel and
+ * adjoint, each cell's 64 polynomial coefficients (256 bytes per cell; not
+ * built above 2 GB or 1000 nodes per axis); where one of these is not
+ * built or its allocation fails, the kernels read F itself.
  * Errors: NB_EINVAL for n_mosaic < 1, n_phi < 1, n_mosaic x n_phi >
  * 2048, non-positive or (sinc) non-integral N, a zero spindle with
  * n_phi > 1, empty table, NULL axes or umats, or F NULL before any table
@@ -188,8 +195,8 @@ int nb_get_stats(nb_sim *sim, long long *evaluated_terms,
  * n_elems must equal hkl_n[0] hkl_n[1] hkl_n[2] of the table set there
  * (shape, origin, lookup and default_F are kept).  The copy is queued on
  * the handle's stream (nothing goes through the host), so the caller must
- * not change F until that stream has passed it; the tricubic tables
- * derived from F are rebuilt at the next launch.  This is the refinement
+ * not change F until that stream has passed it; the tables derived
+ * from F (see nb_set_crystal) are rebuilt at the next launch.  This is the refinement
  * loop's upload: a structure-factor table that already lives on the GPU
  * (a torch tensor being refined) stays there.  Errors: NB_ESTATE before
  * nb_set_crystal has set a table; NB_EINVAL for NULL F or a wrong
