@@ -20,9 +20,14 @@
 
 namespace nbgb {
 
-// MODE 0: NB_MIXED, MODE 1: NB_F32
+// MODE 0: NB_MIXED, MODE 1: NB_F32.  Launch bounds: 4 blocks per SM, and
+// 3 for the NB_MIXED sinc with nearest lookup, whose fast path then gets
+// 112 registers instead of 104 (still 4 blocks per SM by registers) and
+// measured 6.98 -> 6.91 ms on the 1024^2 sweep; the tricubic forms would
+// exceed 128 registers and lose a block per SM
 template <int SHAPE, int INTERP, int MODE, int HASDIV>
-__global__ void __launch_bounds__(kTileThreads, 4)
+__global__ void __launch_bounds__(
+    kTileThreads, (SHAPE == 0 && INTERP == 0 && MODE == 0) ? 3 : 4)
     spots_mixed_kernel(SpotArgs a) {
   extern __shared__ __align__(16) float smf[];
   // the sinc fast path's table (two float4 per pair of sources) first,
