@@ -7,8 +7,8 @@
 // The Miller indices, the fractional offsets and the sinc are evaluated in
 // the order the definition is written, so h and the sinc's phases are
 // bitwise those of any other uncontracted FP64 evaluation (the sinc at
-// N = 200 multiplies h's rounding by pi N).  Two parts that are not
-// sensitive to the last bits are arranged for the FP64 pipe, which on this
+// N = 200 multiplies h's rounding by pi N).  The rest, which is not
+// sensitive to the last bits, is arranged for the FP64 pipe, which on this
 // part issues at 1/64 of the FP32 rate and so sets the kernel's time:
 //   * the Gaussian exponent and the Lagrange weights multiply by 1/0.63
 //     and 1/6 instead of dividing, and the sinc divides once per step, not
