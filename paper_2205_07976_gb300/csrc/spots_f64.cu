@@ -10,10 +10,11 @@
 // N = 200 multiplies h's rounding by pi N).  The rest, which is not
 // sensitive to the last bits, is arranged for the FP64 pipe, which on this
 // part issues at 1/64 of the FP32 rate and so sets the kernel's time:
-//   * the Gaussian exponent and the Lagrange weights multiply by 1/0.63
-//     and 1/6 instead of dividing, and the sinc divides once per step, not
-//     once per axis (an IEEE division is a sequence of about ten FP64
-//     instructions; the result moves by an ulp or two);
+//   * the Gaussian exponent (summed in explicit FMAs) and the Lagrange
+//     weights multiply by 1/0.63 and 1/6 instead of dividing, and the sinc
+//     divides once per step, not once per axis (an IEEE division is a
+//     sequence of about ten FP64 instructions; the result moves by an ulp
+//     or two);
 //   * the tricubic sum is nested per axis in explicit FMAs, sum_i w_i
 //     sum_j w_j sum_k w_k F_ijk: 84 FP64 operations instead of 256 for the
 //     flat triple product sum (the rounding differs at the 1e-15 level);
@@ -56,11 +57,11 @@ __device__ __forceinline__ double flatt_f64(const SpotArgs &a,
         den *= sin(M_PI * fr);
       }
     } else {
-      rad2 += a.N64[x] * a.N64[x] * fr * fr;
+      // sum N^2 f^2 / 0.63 in explicit FMAs (N^2 / 0.63 is loop-invariant)
+      rad2 = fma(a.N64[x] * a.N64[x] * (1.0 / 0.63) * fr, fr, rad2);
     }
   }
-  if (SHAPE == 1)
-    return a.N64[0] * a.N64[1] * a.N64[2] * exp(-rad2 * (1.0 / 0.63));
+  if (SHAPE == 1) return a.N64[0] * a.N64[1] * a.N64[2] * exp(-rad2);
   return num / den;
 }
 
@@ -122,16 +123,17 @@ __device__ __forceinline__ double fcell_f64(const SpotArgs &a,
     if (in_table(a, fl[0] - 1, fl[1] - 1, fl[2] - 1) &&
         in_table(a, fl[0] + 2, fl[1] + 2, fl[2] + 2)) {
       // 4-point Lagrange weights on nodes -1, 0, 1, 2, from the shared
-      // products t (t - 1) and (t + 1)(t - 2)
+      // products t (t - 1) / 6 and (t + 1)(t - 2) / 2 (11 operations per
+      // axis; the negations are free operand modifiers)
       double w[3][4];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         const double t = x[c], tm1 = t - 1.0, tm2 = t - 2.0, tp1 = t + 1.0;
-        const double p = t * tm1, q = tp1 * tm2;
-        w[c][0] = p * tm2 * (-1.0 / 6.0);
-        w[c][1] = q * tm1 * 0.5;
-        w[c][2] = q * t * -0.5;
-        w[c][3] = p * tp1 * (1.0 / 6.0);
+        const double p6 = t * tm1 * (1.0 / 6.0), q2 = tp1 * tm2 * 0.5;
+        w[c][0] = -(p6 * tm2);
+        w[c][1] = q2 * tm1;
+        w[c][2] = -(q2 * t);
+        w[c][3] = p6 * tp1;
       }
       long long off =
           ((long long)(fl[0] - 1) * a.hn[1] + (fl[1] - 1)) * a.hn[2] +
