@@ -10,6 +10,9 @@
 // N = 200 multiplies h's rounding by pi N).  The rest, which is not
 // sensitive to the last bits, is arranged for the FP64 pipe, which on this
 // part issues at 1/64 of the FP32 rate and so sets the kernel's time:
+//   * the sinc's denominators sin(pi f), |pi f| <= pi/2, come from a
+//     truncated Taylor series (sin_half_period) instead of the general
+//     sine with its range reduction; their argument is unchanged;
 //   * the Gaussian exponent (summed in explicit FMAs) and the Lagrange
 //     weights multiply by 1/0.63 and 1/6 instead of dividing, and the sinc
 //     divides once per step, not once per axis (an IEEE division is a
@@ -35,6 +38,27 @@ __device__ __forceinline__ double dot3d(const double *a, const double *b) {
   return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
 }
 
+// sin(x) for |x| <= pi/2 from its Taylor series through x^21/21!: the
+// remainder is below (pi/2)^23/23! < 2e-18, the coefficients are the
+// reciprocal factorials rounded once (every factorial up to 21! is exact
+// in FP64), and x + x^3 p with p by Horner in x^2 keeps the error to a few
+// ulp; 12 FP64 operations, no range reduction (the sinc's denominators
+// have |pi f| <= pi/2)
+__device__ __forceinline__ double sin_half_period(double x) {
+  const double x2 = x * x;
+  double p = 1.0 / 51090942171709440000.0;  // 1/21!
+  p = fma(p, x2, -1.0 / 121645100408832000.0);
+  p = fma(p, x2, 1.0 / 355687428096000.0);
+  p = fma(p, x2, -1.0 / 1307674368000.0);
+  p = fma(p, x2, 1.0 / 6227020800.0);
+  p = fma(p, x2, -1.0 / 39916800.0);
+  p = fma(p, x2, 1.0 / 362880.0);
+  p = fma(p, x2, -1.0 / 5040.0);
+  p = fma(p, x2, 1.0 / 120.0);
+  p = fma(p, x2, -1.0 / 6.0);
+  return fma(x * x2, p, x);
+}
+
 template <int SHAPE>
 __device__ __forceinline__ double flatt_f64(const SpotArgs &a,
                                             const double h[3], double n[3]) {
@@ -54,7 +78,7 @@ __device__ __forceinline__ double flatt_f64(const SpotArgs &a,
         num *= a.N64[x];
       } else {
         num *= sin(M_PI * a.N64[x] * fr);
-        den *= sin(M_PI * fr);
+        den *= sin_half_period(M_PI * fr);
       }
     } else {
       // sum N^2 f^2 / 0.63 in explicit FMAs (N^2 / 0.63 is loop-invariant)
