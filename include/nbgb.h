@@ -403,7 +403,17 @@ enum {
     /* 1: launches of the warp-per-pixel kernel also count the work
      * nb_get_work reports (pairs, intervals, block tests); 0 (default):
      * they do not, and run the instantiation without the counters */
-    NB_OPT_COUNT_WORK = 2
+    NB_OPT_COUNT_WORK = 2,
+    /* a test hook for the failure paths, not part of the method: the next
+     * `value` device allocations made for simulation handles (any nb_sim
+     * of the process; the server and the FP64 peak probe allocate on their
+     * own) fail as if the device were out of memory (0, the default, turns
+     * it off).  A call whose own buffer is refused returns
+     * NB_ENOMEM and leaves the handle usable (the same call succeeds once
+     * memory is there); a launch whose table derived from F is refused
+     * (nb_set_crystal lists them) reads F itself and gives the same
+     * result. */
+    NB_OPT_FAIL_ALLOCS = 3
 };
 enum { NB_VARIANT_AUTO = 0, NB_VARIANT_THREAD = 1, NB_VARIANT_WARP = 2 };
 

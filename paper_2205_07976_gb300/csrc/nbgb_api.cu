@@ -3,6 +3,7 @@
 // step and mosaic domain, source tables, panel offsets) and the launches.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <algorithm>
@@ -18,6 +19,17 @@ using nbgb::SpotArgs;
 
 namespace {
 
+// NB_OPT_FAIL_ALLOCS: how many of the library's next device allocations
+// fail as if the device were out of memory (a test hook, process-wide)
+std::atomic<long long> g_fail_allocs{0};
+
+bool inject_alloc_failure() {
+  long long left = g_fail_allocs.load();
+  while (left > 0)
+    if (g_fail_allocs.compare_exchange_weak(left, left - 1)) return true;
+  return false;
+}
+
 struct DevBuf {
   void *p = nullptr;
   size_t n = 0;
@@ -27,6 +39,7 @@ struct DevBuf {
     p = nullptr;
     n = 0;
     if (bytes == 0) return cudaSuccess;
+    if (inject_alloc_failure()) return cudaErrorMemoryAllocation;
     cudaError_t e = cudaMalloc(&p, bytes);
     if (e == cudaSuccess) n = bytes;
     return e;
@@ -1156,6 +1169,11 @@ int nb_set_option(nb_sim *s, int key, long long value) {
   if (key == NB_OPT_COUNT_WORK) {
     if (value != 0 && value != 1) return fail(s, NB_EINVAL, "bad value");
     s->count_work = value != 0;
+    return NB_OK;
+  }
+  if (key == NB_OPT_FAIL_ALLOCS) {
+    if (value < 0) return fail(s, NB_EINVAL, "bad value");
+    g_fail_allocs.store(value);
     return NB_OK;
   }
   return fail(s, NB_EINVAL, "unknown option");

@@ -24,6 +24,7 @@ NB_DTYPE_F32, NB_DTYPE_F64 = 0, 1
 PRECISIONS = {"f64": NB_F64, "mixed": NB_MIXED, "f32": NB_F32}
 NB_OPT_VARIANT = 1
 NB_OPT_COUNT_WORK = 2
+NB_OPT_FAIL_ALLOCS = 3
 WORK_NAMES = ("pixel_steps", "units", "items", "intervals", "blocks",
               "pairs", "terms")
 VARIANTS = {"auto": 0, "thread": 1, "warp": 2}
@@ -320,6 +321,13 @@ class Sim:
         _check(self.lib.nb_get_stats(self.h, ctypes.byref(ev),
                                      ctypes.byref(ps)), self.h)
         return int(ev.value), int(ps.value)
+
+    def fail_allocations(self, n: int):
+        """Test hook: the library's next n device allocations (any handle)
+        fail as if the device were out of memory; 0 turns it off."""
+        _check(self.lib.nb_set_option(self.h, NB_OPT_FAIL_ALLOCS, int(n)),
+               self.h)
+        return self
 
     def count_work(self, on: bool = True):
         """Make the following launches count the work work() reports."""

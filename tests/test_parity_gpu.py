@@ -352,6 +352,43 @@ def test_fcell_device_upload_equals_host_upload(precision):
         assert back.max() > 0 and not np.array_equal(back, got)
 
 
+def test_refused_allocations_fail_cleanly_and_leave_the_handle_usable():
+    """Failure detection with the allocation-failure hook (no GPU fault): a
+    call whose buffer is refused returns NB_ENOMEM and the handle works
+    once memory is there; a refused table derived from F (the FP64 copy)
+    makes the launch read F itself, with the same image."""
+    base = W.shrink(W.large_shot(), 24, 16, 2500, 700)
+    ref = nbgb.simulate(base, "f64")
+    sim = nbgb.Sim("f64")
+    try:
+        sim.fail_allocations(1)
+        with pytest.raises(nbgb.NbError) as e:
+            sim.set_shot(base)  # the F table's buffer is the first
+        assert e.value.code == nbgb.NB_ENOMEM
+        sim.fail_allocations(0)
+        sim.set_shot(base)
+        sim.add_spots()
+        np.testing.assert_array_equal(sim.image(), ref)
+        # a larger table: its FP64 copy is the launch's only new buffer
+        big = base.copy()
+        big.F = W.structure_factors(np.random.default_rng(1), 62)
+        big.hkl_min = np.array([-62, -62, -62], dtype=np.int32)
+        ref_big = nbgb.simulate(big, "f64")
+        sim.set_crystal(big)
+        sim.fail_allocations(1)
+        sim.zero()
+        sim.add_spots()
+        got = sim.image()
+        # the refusal was spent on the FP64 copy: a new handle's buffers
+        # are all granted
+        probe = nbgb.Sim("f64").set_shot(base)
+        probe.close()
+        np.testing.assert_array_equal(got, ref_big)
+    finally:
+        sim.fail_allocations(0)
+        sim.close()
+
+
 def test_single_pixel_and_empty_list():
     s = W.shrink(W.single_shot_small(), 1, 1, 200, 170)
     ref = oracle.image(s)
