@@ -75,11 +75,11 @@ def captured_traffic():
 # Pipe utilisation (% of active cycles) of the warp-per-pixel kernel from
 # one ncu --set full capture on a 512x512 window of the large shot
 # (profiles/spots_split_window512_full.txt), keyed like the traffic figure
-PIPES_CAPTURE = {"sm__pipe_fma_cycles_active_pct": 36.2,
-                 "sm__pipe_alu_cycles_active_pct": 40.0,
-                 "sm__inst_executed_pipe_lsu_pct": 41.2,
-                 "smsp__issue_active_pct": 73.9,
-                 "l1tex__data_pipe_lsu_wavefronts_pct": 55.2,
+PIPES_CAPTURE = {"sm__pipe_fma_cycles_active_pct": 36.3,
+                 "sm__pipe_alu_cycles_active_pct": 40.1,
+                 "sm__inst_executed_pipe_lsu_pct": 41.3,
+                 "smsp__issue_active_pct": 74.1,
+                 "l1tex__data_pipe_lsu_wavefronts_pct": 54.5,
                  "window": "512x512 centred on the large shot",
                  "sha256_16": "068389bc3a988e15"}
 
