@@ -74,7 +74,11 @@ __device__ __forceinline__ double flatt_f64(const SpotArgs &a,
     double fr = h[x] - n[x];
     if (SHAPE == 0) {
       // sin(pi N h)/sin(pi h) = +-sin(pi N f)/sin(pi f); the sign drops out
-      if (fabs(fr) < 1e-100) {
+      // |f| < 1e-100 as an integer compare of the magnitudes' bit patterns
+      // (ordered like the values for non-negative doubles; a double
+      // compare is one more FP64-pipe instruction)
+      if ((__double_as_longlong(fr) & 0x7fffffffffffffffll) <
+          __double_as_longlong(1e-100)) {
         num *= a.N64[x];
       } else {
         num *= sin(M_PI * a.N64[x] * fr);
@@ -140,7 +144,8 @@ __device__ __forceinline__ double fcell_f64(const SpotArgs &a,
       // h - n is exact (h and n lie within 1/2), and so is h - floor(h)
       // for h < n: (h - n) + 1 holds no bit below h's last one
       const double fr = h[c] - n[c];
-      const bool below = fr < 0.0;
+      // f < 0 from the sign bit (an integer test; f = h - n is never -0)
+      const bool below = __double_as_longlong(fr) < 0;
       fl[c] = nn[c] - (below ? 1 : 0);
       x[c] = below ? fr + 1.0 : fr;
     }
@@ -252,7 +257,8 @@ __global__ void __launch_bounds__(kTileThreads, 4)
             double n[3];
             double fl = flatt_f64<SHAPE>(a, h, n);
             double fc = fcell_f64<INTERP>(a, h, n);
-            acc += fc * fc * fl * fl * wcpo;
+            const double a_ = fc * fl;
+            acc += a_ * a_ * wcpo;
           }
         }
       }
